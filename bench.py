@@ -1,0 +1,371 @@
+"""Benchmark of the DG Maxwell hot path: LSERK4 steps of the fused RK-stage kernel.
+
+One benchmark step = one LSERK4 time step = 5 RK stages, each a full right-
+hand side (volume derivative + curl, face gather + upwind flux, LIFT) fused
+with the stage update; the timed region also ends with one energy evaluation.
+Metric: DOF-updates/s = 6 * K * Np per stage (six fields counted separately,
+as in the paper's Fig. dofs-per-sec) / time.
+
+Workload (default): N = 4 (Np = 35) on [-1,1]^3 cut into 24^3 hexes x 6 Kuhn
+tetrahedra = 82 944 tets, interior vertices jittered by U[-0.15h, 0.15h]
+(seed 0), PEC walls, Gaussian E_z pulse of width 0.2 centred at a seeded point.
+Synthetic data.  u + res + the work copy are 209 MB > the 129 MB L2, so no L2
+flush is needed between iterations.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun (N > 1) every rank runs an independent replica of the
+workload (weak scaling, no collective in the data path); the time is the max
+over ranks.  `--impl reference` times the FP64 CPU oracle (the only reference
+this method has) on a bounded sample of the same workload, on rank 0 only.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import re
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from workloads import WORKLOADS, gaussian_pulse, kuhn_box_mesh, pulse_center, cavity_mode  # noqa: E402
+
+METRIC = "DOF-updates/s"
+FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+                  "sm_max_mhz": 2070.0}
+
+
+def workload_inputs(name):
+    w = WORKLOADS[name]
+    verts, tets = kuhn_box_mesh(w["n"], w["jitter"], w["seed"])
+    return w, verts, tets
+
+
+def initial_fields(w, x):
+    if w["init"] == "pulse":
+        return gaussian_pulse(x[0], x[1], x[2], w["width"], pulse_center(w["pulse_seed"]))
+    return cavity_mode(x[0], x[1], x[2], 0.0)
+
+
+def describe(name, w, K, Np):
+    return (f"{name}: N={w['N']} (Np={Np}), {w['n']}^3 hexes x 6 = {K} tets on [-1,1]^3, "
+            f"jitter {w['jitter']}h (seed {w['seed']}), PEC walls, upwind flux, "
+            f"{'Gaussian Ez pulse w=' + str(w['width']) if w['init'] == 'pulse' else 'cavity (1,1,1) mode'}")
+
+
+def stage_bytes_per_elem(Np):
+    # read u, read res, write res, write u (4 x 6 Np floats) + 132 B geometry/connectivity
+    return 96 * Np + 132
+
+
+def flops_per_elem_stage(N, Np, Nfp):
+    # additions + multiplications (the paper's counting): derivatives, chain rule + curl,
+    # flux, lifting, assembly, plus the LSERK4 update
+    return 36 * Np * Np + 66 * Np + 60 * 4 * Nfp + 12 * Np * 4 * Nfp + 6 * Np + 30 * Np
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d, "measured"
+    return dict(FALLBACK_PEAKS), "fallback"
+
+
+def kernel_source_digest():
+    h = hashlib.sha256()
+    for n in ("stage_kernel.cuh", "device.h"):
+        with open(os.path.join(ROOT, "paper_0901_1024_gb300", "csrc", n), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(workload):
+    """DRAM bytes per stage launch from the committed ncu summary, if it was
+    taken on the current kernel source (digest line), else None."""
+    p = os.path.join(ROOT, "profiles", f"stage_kernel_{workload}.md")
+    if not os.path.exists(p):
+        return None
+    text = open(p).read()
+    dg = re.search(r"kernel_source_digest:\s*([0-9a-f]+)", text)
+    tb = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", text)
+    if not dg or not tb or dg.group(1) != kernel_source_digest():
+        return None
+    return float(tb.group(1))
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons while running."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,utilization.gpu,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.samples = []
+        self.p = None
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={index}", f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "50"],
+                                      stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            return
+        self.t = threading.Thread(target=self._read, daemon=True)
+        self.t.start()
+
+    def _read(self):
+        for line in self.p.stdout:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 8:
+                self.samples.append((time.time(), parts))
+
+    def stop(self, t0, t1):
+        if not self.p:
+            return None
+        time.sleep(0.12)
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        rows = [(t, p) for t, p in self.samples]
+        inwin = [p for t, p in rows if t0 - 0.06 <= t <= t1 + 0.06]
+        busy = [p for t, p in rows if (num(p[3]) or 0) >= 50]
+        use = inwin or busy or [p for _, p in rows]
+        if not use:
+            return None
+        sm = [num(p[0]) for p in use if num(p[0]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for p in use for i in range(4) if p[4 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": num(use[0][1]), "reasons": reasons, "samples": len(use),
+                "window": "timed region" if inwin else ("busy samples" if busy else "all samples")}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def run_ours(args):
+    import torch
+    import paper_0901_1024_gb300 as dg
+
+    world, rank, local = dist_setup()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    w, verts, tets = workload_inputs(args.workload)
+    mesh = dg.Mesh(verts, tets, w["N"])
+    K, Np, Nfp = mesh.K, mesh.Np, mesh.Nfp
+    x = mesh.nodes()
+    u0 = initial_fields(w, x).astype(np.float32)
+    dt = mesh.dt_cfl
+    stream = torch.cuda.current_stream()
+    u = torch.from_numpy(u0).cuda()
+    res = torch.zeros_like(u)
+
+    sampler = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
+    # warm-up (also creates the work buffer and JIT-free kernels' attributes)
+    mesh.step(u, res, dt, args.warmup)
+    mesh.energy(u)
+    mesh.trace_enable(5 * args.steps + 4)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0 = time.time()
+    e0.record(stream)
+    mesh.step(u, res, dt, args.steps)
+    launches = mesh.last_launch_count()
+    energy = mesh.energy(u)
+    launches += mesh.last_launch_count()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t1 = time.time()
+    ms = e0.elapsed_time(e1)
+    trace_ms, trace_kind = mesh.trace_read()
+    mesh.trace_enable(0)
+    if dist:
+        tt = torch.tensor([ms], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms = float(tt.item())
+        dist.barrier()
+    clocks = sampler.stop(t0, t1) if sampler else None
+
+    dof_stage = 6 * K * Np
+    value = world * dof_stage * 5 * args.steps / (ms * 1e-3)
+    stage_ms = [t for t, k in zip(trace_ms, trace_kind) if k == 0]
+    avg_stage_s = statistics.fmean(stage_ms) * 1e-3
+    peaks, peaks_src = load_peaks()
+    algo_bytes = stage_bytes_per_elem(Np) * K
+    achieved = algo_bytes / avg_stage_s / 1e9
+    traffic = profiled_traffic(args.workload)
+    flops = flops_per_elem_stage(w["N"], Np, Nfp) * K
+    fp32_peak = 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12   # TFLOP/s, FP32 FMA
+
+    e2e = None
+    if not args.no_e2e:
+        uh = torch.from_numpy(u0.copy()).pin_memory()
+        rh = torch.zeros(u0.shape, dtype=torch.float32).pin_memory()
+        mesh.step_host(uh, rh, dt, 1)                      # warm the host-path buffers
+        n_e2e = max(1, min(args.steps, 20))
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        h0 = time.perf_counter()
+        for _ in range(n_e2e):
+            mesh.step_host(uh, rh, dt, 1, with_energy=True)
+        h1 = time.perf_counter()
+        el = h1 - h0
+        if dist:
+            tt = torch.tensor([el], device="cuda")
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            el = float(tt.item())
+        nbytes = u0.nbytes
+        e2e = {"value": world * dof_stage * 5 * n_e2e / el, "unit": METRIC,
+               "h2d_bytes_per_step": 2 * nbytes, "d2h_bytes_per_step": 2 * nbytes + 8,
+               "steps": n_e2e, "call": "dg_step_host (pinned host u, res; H2D, 5 stages, D2H, energy)"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = time_oracle(w, verts, tets, budget_s=args.cpu_budget)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": describe(args.workload, w, K, Np), "K": K, "N": w["N"], "Np": Np,
+                       "dt": dt, "stages_per_step": 5, "energy_evals_in_timed_region": 1,
+                       "l2": "inputs larger than L2 (u+res+work copy = %.0f MB > 129 MB)"
+                             % (3 * u0.nbytes / 1e6),
+                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                         "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
+                         "kernel": f"stage_kernel<N={w['N']},RK>",
+                         "algorithmic_bytes_per_launch": algo_bytes,
+                         "avg_launch_ms": avg_stage_s * 1e3, "launches_timed": len(stage_ms),
+                         "peak_source": f"{peaks_src} (MEASURED_PEAKS.json hbm_gbs)" if peaks_src == "measured"
+                         else "fallback 6.8 TB/s"},
+            "fp32_alu": {"achieved_tflops": flops / avg_stage_s / 1e12, "peak_tflops": fp32_peak,
+                         "frac": flops / avg_stage_s / 1e12 / fp32_peak,
+                         "peak_derivation": "152 SMs x 128 FP32 lanes x 2 flop x sm_max_mhz"},
+            "gflops": flops * 5 * args.steps / (ms * 1e-3) / 1e9 * world,
+            "energy": energy,
+            "clocks": clocks,
+            "e2e": e2e,
+            "gpu_launches": int(launches),
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def oracle_sample(w, verts, tets, layers):
+    """The first `layers` z-layers of hexes of the workload mesh (6*n*n*layers tets)."""
+    import oracle
+    n = w["n"]
+    Ks = 6 * n * n * layers
+    om = oracle.build_mesh(verts, tets[:Ks], w["N"])
+    u0 = initial_fields(w, np.stack([om.x, om.y, om.z]))
+    return om, u0
+
+
+def time_oracle(w, verts, tets, budget_s=15.0, layers=None, steps=None):
+    """Times the FP64 oracle's LSERK4 steps on a bounded sample of the workload."""
+    import oracle
+    layers = layers or 2
+    om, u = oracle_sample(w, verts, tets, layers)
+    dt = oracle.cfl_dt(om)
+    res = np.zeros_like(u)
+    t0 = time.perf_counter()
+    done = 0
+    while True:
+        u, res = oracle.lserk4_run(om, u, dt, 1, res)
+        done += 1
+        el = time.perf_counter() - t0
+        if (steps and done >= steps) or (not steps and (el >= budget_s or done >= 50)):
+            break
+    dof = 6 * om.K * om.Np * 5 * done
+    return {"value": dof / el, "unit": METRIC, "cores": 1, "kind": "oracle",
+            "sample": f"{done} LSERK4 step(s) on the first {layers} z-layer(s) of hexes "
+                      f"({om.K} of {len(tets)} tets) of the same mesh, FP64 NumPy oracle "
+                      f"(single-threaded einsum), {el:.1f} s"}
+
+
+def run_reference(args):
+    world, rank, _ = dist_setup()
+    if rank != 0:
+        return
+    w, verts, tets = workload_inputs(args.workload)
+    import oracle
+    layers = 1
+    om, u = oracle_sample(w, verts, tets, layers)
+    dt = oracle.cfl_dt(om)
+    res = np.zeros_like(u)
+    for _ in range(args.warmup):
+        u, res = oracle.lserk4_run(om, u, dt, 1, res)
+    t0 = time.perf_counter()
+    u, res = oracle.lserk4_run(om, u, dt, args.steps, res)
+    el = time.perf_counter() - t0
+    e = oracle.energy(om, u)
+    value = 6 * om.K * om.Np * 5 * args.steps / el
+    line = {"metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": el * 1e3 / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": describe(args.workload, w, len(tets), om.Np), "K": len(tets),
+                       "N": w["N"], "Np": om.Np,
+                       "sample": f"first {layers} z-layer of hexes ({om.K} tets)"},
+            "energy": e,
+            "cpu_baseline": {"value": value, "unit": METRIC, "cores": 1, "kind": "oracle",
+                             "sample": f"{args.steps} LSERK4 steps on {om.K} of {len(tets)} tets "
+                                       "(first z-layer of hexes), FP64 NumPy oracle"},
+            "e2e": {"value": value, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="pulse_n24_N4", choices=sorted(WORKLOADS))
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-budget", type=float, default=15.0)
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)          # at least 3 untimed warm-up steps
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,191 @@
+/*
+ * dg.h -- C ABI of the GB300 nodal discontinuous Galerkin Maxwell library.
+ *
+ * The library evaluates the semi-discrete nodal DG operator for Maxwell's
+ * equations on face-conforming tetrahedral meshes and advances it with the
+ * five-stage low-storage RK4 scheme, following Kloeckner, Warburton, Bridge &
+ * Hesthaven, "Nodal Discontinuous Galerkin Methods on Graphics Processors":
+ *   - problem statement: Section 2, Eq. claw / strong-dg (face-conforming
+ *     tetrahedra, order-N nodal Lagrange basis on Warburton's nodes);
+ *   - operator: Eq. semidiscrete-dg with the matrices of Eq.
+ *     dg-global-matrices, Eq. dg-reference-matrices and Fig. lifting-matrix;
+ *   - physics: Maxwell's equations of Section 6 (Eq. maxwells-claws) with
+ *     eps = mu = 1, no current, and the upwind flux of Section 6; every face
+ *     that is not shared by two tetrahedra is a perfectly conducting wall
+ *     (ghost state E+ = -E-, H+ = H-);
+ *   - time stepping: the LSERK4 scheme of Carpenter & Kennedy cited in
+ *     Section 6.
+ *
+ * Conventions shared by every call
+ *   - Return value: DG_OK (0) or one of the negative DG_ERR_* codes below;
+ *     dg_last_error() then returns a message (thread-local, valid until the
+ *     next failing call on the same thread).
+ *   - Fields are six FP32 arrays in structure-of-arrays order
+ *         u[c][k][i],  c = 0..5 (Ex, Ey, Ez, Hx, Hy, Hz), k = 0..K-1, i = 0..Np-1
+ *     i.e. a contiguous block of 6*K*Np floats.  Element numbering k is the
+ *     caller's tetrahedron order; node numbering i is the order returned by
+ *     dg_nodes().
+ *   - Ownership: the library owns the mesh, its operators and its device
+ *     geometry; the caller owns every field buffer it passes in.  Device
+ *     pointers must point to memory of the current CUDA device.
+ *   - Streams: `stream` is a cudaStream_t passed as void* (NULL = legacy
+ *     default stream).  Device calls are asynchronous on that stream unless
+ *     stated otherwise.  A mesh must not be used from two host threads at once.
+ *   - Orders: 1 <= N <= 9.
+ */
+#ifndef DG_GB300_H
+#define DG_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define DG_OK            0
+#define DG_ERR_ARG      -1   /* null pointer, bad size, bad value            */
+#define DG_ERR_MESH     -2   /* degenerate tetrahedron, bad index, face shared by >2 tets */
+#define DG_ERR_ORDER    -3   /* order outside 1..9                           */
+#define DG_ERR_CUDA     -4   /* a CUDA runtime call failed                   */
+#define DG_ERR_OOM      -5   /* host or device allocation failed             */
+#define DG_ERR_UNSTABLE -6   /* energy not finite (NaN/Inf): time step too large or bad data */
+#define DG_ERR_STATE    -7   /* call needs dg_set_order() first              */
+
+typedef struct dg_mesh dg_mesh;  /* opaque, library-owned */
+
+/*
+ * Build a mesh from vertex coordinates and tetrahedra (Section 2: a domain made
+ * of disjoint, face-conforming tetrahedra).
+ *   verts : host, [nv][3] doubles (x, y, z), read only, copied.
+ *   tets  : host, [K][4] int32 vertex indices (0-based), read only, copied.
+ *           A tetrahedron with negative orientation has its last two vertices
+ *           swapped internally; element numbering is unchanged.
+ *   out   : receives the new mesh; free it with dg_mesh_destroy().
+ * Faces are matched by their vertex triples; an unmatched face is a PEC wall.
+ * Errors: DG_ERR_ARG (null, nv < 4, K < 1, K*220 >= 2^31), DG_ERR_MESH
+ * (index out of range, zero-volume tetrahedron, face shared by more than two
+ * tetrahedra).  Host only; needs no GPU.
+ */
+int dg_mesh_create(const double* verts, int64_t nv, const int32_t* tets, int64_t K,
+                   dg_mesh** out);
+
+/*
+ * Set the polynomial order N (1..9) and build, on the host in FP64, the
+ * reference operators (Dr, Ds, Dt, M, LIFT of Eq. dg-global-matrices and Fig.
+ * lifting-matrix on Warp & Blend nodes), the face-node connectivity and the
+ * per-element geometry (Eq. dg-reference-matrices).  Device buffers are
+ * created lazily on the first device call.  May be called again to change N.
+ * Errors: DG_ERR_ARG, DG_ERR_ORDER.  Host only; needs no GPU.
+ */
+int dg_set_order(dg_mesh* mesh, int N);
+
+/* K, Np = (N+1)(N+2)(N+3)/6, Nfp = (N+1)(N+2)/2 and the CFL step
+ * dt = min_{k,f} (J_k / sJ_{k,f}) * 2/(N+1)^2.  Any output may be NULL. */
+int dg_info(const dg_mesh* mesh, int64_t* K, int* Np, int* Nfp, double* dt_cfl);
+
+/* Physical node coordinates, host [3][K][Np] doubles (x block, y block, z). */
+int dg_nodes(const dg_mesh* mesh, double* xyz);
+
+/*
+ * Face-node connectivity (the face index lists of Section 5.2), host int32
+ * arrays of K*4*Nfp entries ordered (k, face f, face node j):
+ *   vmapM[(k*4+f)*Nfp+j] = k*Np + (index of face node j of face f),
+ *   vmapP[...]           = global node id of the same point in the neighbour,
+ *                          or vmapM on a wall face.
+ * Faces: f0 = (v0 v1 v2), f1 = (v0 v1 v3), f2 = (v1 v2 v3), f3 = (v0 v2 v3)
+ * of the (orientation-corrected) tetrahedron; face nodes in ascending node order.
+ */
+int dg_get_connectivity(const dg_mesh* mesh, int32_t* vmapM, int32_t* vmapP);
+
+/* Reference operators in FP64, row-major: Dr, Ds, Dt, M are [Np][Np], LIFT is
+ * [Np][4*Nfp].  Any pointer may be NULL. */
+int dg_get_operators(const dg_mesh* mesh, double* Dr, double* Ds, double* Dt,
+                     double* M, double* LIFT);
+
+/* Per-element geometry in FP64: metric [9][K] (rx ry rz sx sy sz tx ty tz),
+ * J [K], normals [3][K][4], Fscale = sJ/J [K][4].  Any pointer may be NULL. */
+int dg_get_geometry(const dg_mesh* mesh, double* metric, double* J, double* normals,
+                    double* Fscale);
+
+/* Flux parameter alpha: 1 = upwind (default), 0 = central (energy conserving).
+ * Host only. */
+int dg_set_flux(dg_mesh* mesh, double alpha);
+
+/*
+ * One evaluation of the semi-discrete operator (Eq. semidiscrete-dg):
+ * rhs = curl terms (local differentiation, Alg. 4) + LIFT * flux (flux
+ * extraction, Alg. 2, and lifting, Alg. 1).
+ *   u   : device, [6][K][Np] FP32, read only.
+ *   rhs : device, [6][K][Np] FP32, written; must not overlap u.
+ * Asynchronous on `stream`.
+ */
+int dg_rhs(dg_mesh* mesh, const float* u, float* rhs, void* stream);
+
+/*
+ * Advance nsteps LSERK4 steps of size dt (5 stages each):
+ *   res <- a_i res + dt rhs(u);  u <- u + b_i res,  i = 0..4.
+ *   u   : device, [6][K][Np] FP32, in/out (state).
+ *   res : device, [6][K][Np] FP32, in/out (RK register; zero it at t = 0).
+ * The stage update is fused into the operator kernel; the library keeps one
+ * device work copy of u per mesh (allocated on first use).
+ * Asynchronous on `stream`.  Errors: DG_ERR_ARG (dt <= 0, nsteps < 0).
+ */
+int dg_step(dg_mesh* mesh, float* u, float* res, double dt, int nsteps, void* stream);
+
+/*
+ * Discrete energy 1/2 sum_k J_k sum_c u_kc^T M u_kc (FP32 products, FP64
+ * accumulation across elements) written to *out (host).
+ *   u : device, [6][K][Np] FP32.
+ * Synchronises `stream`.  Returns DG_ERR_UNSTABLE if the energy is not finite.
+ */
+int dg_energy(dg_mesh* mesh, const float* u, double* out, void* stream);
+
+/*
+ * End-to-end convenience: copy host fields to the device, advance nsteps
+ * LSERK4 steps, copy the fields back and (if energy != NULL) compute the
+ * energy of the result.
+ *   u, res : host, [6][K][Np] FP32, in/out (page-locked memory is fastest).
+ * Uses library-owned device buffers; synchronises `stream`.
+ */
+int dg_step_host(dg_mesh* mesh, float* u, float* res, double dt, int nsteps,
+                 double* energy, void* stream);
+
+/* Number of kernel launches the last dg_rhs / dg_step / dg_energy /
+ * dg_step_host call on this mesh issued (for launch accounting). */
+int64_t dg_last_launch_count(const dg_mesh* mesh);
+
+/*
+ * Per-launch tracing (the paper times its kernels with CUDA events, Section 6).
+ * dg_trace_enable(mesh, n) with n > 0 clears the record, reserves event pairs
+ * for n launches (more are created on demand) and turns tracing on; n = 0
+ * turns it off.  While on, dg_rhs, dg_step, dg_energy and dg_step_host record
+ * a CUDA event before and after every kernel launch, on the caller's stream,
+ * appending to the record.  The reservation happens on the current device,
+ * outside any later timed region.  Errors: DG_ERR_ARG (n < 0), DG_ERR_STATE
+ * (n > 0 before dg_set_order), DG_ERR_CUDA.
+ */
+int dg_trace_enable(dg_mesh* mesh, int n);
+
+/*
+ * Durations of the launches recorded since the last dg_trace_enable(), in
+ * launch order:
+ *   ms   : host, receives up to `cap` device durations in milliseconds;
+ *   kind : host, receives the kernel of each launch (0 = fused RK stage,
+ *          1 = right-hand side, 2 = energy partial sums, 3 = energy final sum);
+ *          may be NULL;
+ *   count: receives the number of recorded launches (may exceed cap).
+ * Waits for the last recorded event.  Errors: DG_ERR_STATE if nothing was traced.
+ */
+int dg_trace_read(dg_mesh* mesh, double* ms, int32_t* kind, int64_t cap, int64_t* count);
+
+/* Free the mesh and every device buffer it owns.  NULL is ignored. */
+void dg_mesh_destroy(dg_mesh* mesh);
+
+/* Message of the last failing call on this thread ("" if none). */
+const char* dg_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DG_GB300_H */

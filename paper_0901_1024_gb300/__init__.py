@@ -1,0 +1,157 @@
+"""GB300 nodal DG Maxwell solver: thin Python binding over libdg.so (include/dg.h).
+
+Every computation runs inside the C/CUDA library; this module only marshals
+arguments (NumPy arrays for host data, torch CUDA tensors or raw device
+pointers for fields) and turns error codes into exceptions.  There is no
+Python or CPU fallback: if libdg.so is missing, importing `Mesh` works but the
+first call raises ImportError.
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+
+from ._capi import DGError, check, library_path, load  # noqa: F401
+
+__all__ = ["Mesh", "DGError", "load", "library_path"]
+
+
+def _dptr(a: np.ndarray, dtype):
+    assert a.dtype == dtype and a.flags.c_contiguous
+    return a.ctypes.data_as(C.POINTER(np.ctypeslib.as_ctypes_type(dtype)))
+
+
+def _stream_handle(stream):
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+        except ImportError:
+            pass
+        return C.c_void_p(0)
+    if isinstance(stream, int):
+        return C.c_void_p(stream)
+    return C.c_void_p(stream.cuda_stream)
+
+
+def _devptr(x):
+    if isinstance(x, int):
+        return C.c_void_p(x)
+    assert x.is_cuda and x.is_contiguous(), "fields must be contiguous CUDA tensors"
+    import torch
+    assert x.dtype == torch.float32, "fields must be float32"
+    return C.c_void_p(x.data_ptr())
+
+
+class Mesh:
+    """A tetrahedral mesh with its DG operators (owns a dg_mesh*)."""
+
+    def __init__(self, verts, tets, N: int | None = None):
+        self._lib = load()
+        verts = np.ascontiguousarray(verts, dtype=np.float64)
+        tets = np.ascontiguousarray(tets, dtype=np.int32)
+        if verts.ndim != 2 or verts.shape[1] != 3 or tets.ndim != 2 or tets.shape[1] != 4:
+            raise ValueError("verts must be [nv,3] and tets [K,4]")
+        h = C.c_void_p()
+        check(self._lib.dg_mesh_create(_dptr(verts, np.float64), len(verts),
+                                       _dptr(tets, np.int32), len(tets), C.byref(h)),
+              "dg_mesh_create")
+        self._h = h
+        self.N = None
+        if N is not None:
+            self.set_order(N)
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            self._lib.dg_mesh_destroy(h)
+            self._h = None
+
+    close = __del__
+
+    # ---- host setup -------------------------------------------------------
+    def set_order(self, N: int):
+        check(self._lib.dg_set_order(self._h, int(N)), "dg_set_order")
+        self.N = int(N)
+        K, Np, Nfp, dt = C.c_int64(), C.c_int(), C.c_int(), C.c_double()
+        check(self._lib.dg_info(self._h, C.byref(K), C.byref(Np), C.byref(Nfp), C.byref(dt)),
+              "dg_info")
+        self.K, self.Np, self.Nfp, self.dt_cfl = K.value, Np.value, Nfp.value, dt.value
+        return self
+
+    def set_flux(self, alpha: float):
+        check(self._lib.dg_set_flux(self._h, float(alpha)), "dg_set_flux")
+
+    def nodes(self) -> np.ndarray:
+        out = np.empty((3, self.K, self.Np), np.float64)
+        check(self._lib.dg_nodes(self._h, _dptr(out, np.float64)), "dg_nodes")
+        return out
+
+    def connectivity(self):
+        n = self.K * 4 * self.Nfp
+        vM, vP = np.empty(n, np.int32), np.empty(n, np.int32)
+        check(self._lib.dg_get_connectivity(self._h, _dptr(vM, np.int32), _dptr(vP, np.int32)),
+              "dg_get_connectivity")
+        return vM, vP
+
+    def operators(self):
+        Np, NF = self.Np, 4 * self.Nfp
+        Dr, Ds, Dt, M = (np.empty((Np, Np)) for _ in range(4))
+        L = np.empty((Np, NF))
+        check(self._lib.dg_get_operators(self._h, *(_dptr(a, np.float64) for a in (Dr, Ds, Dt, M, L))),
+              "dg_get_operators")
+        return dict(Dr=Dr, Ds=Ds, Dt=Dt, M=M, LIFT=L)
+
+    def geometry(self):
+        K = self.K
+        metric, J, n, Fs = np.empty((9, K)), np.empty(K), np.empty((3, K, 4)), np.empty((K, 4))
+        check(self._lib.dg_get_geometry(self._h, *(_dptr(a, np.float64) for a in (metric, J, n, Fs))),
+              "dg_get_geometry")
+        return dict(metric=metric, J=J, normals=n, Fscale=Fs)
+
+    # ---- device calls -----------------------------------------------------
+    def rhs(self, u, out, stream=None):
+        check(self._lib.dg_rhs(self._h, _devptr(u), _devptr(out), _stream_handle(stream)), "dg_rhs")
+        return out
+
+    def step(self, u, res, dt: float, nsteps: int, stream=None):
+        check(self._lib.dg_step(self._h, _devptr(u), _devptr(res), float(dt), int(nsteps),
+                                _stream_handle(stream)), "dg_step")
+
+    def energy(self, u, stream=None) -> float:
+        out = C.c_double()
+        check(self._lib.dg_energy(self._h, _devptr(u), C.byref(out), _stream_handle(stream)),
+              "dg_energy")
+        return out.value
+
+    def step_host(self, u_host, res_host, dt: float, nsteps: int, with_energy=True, stream=None):
+        """u_host, res_host: host float32 buffers (NumPy arrays or pinned CPU tensors)."""
+        def hptr(a):
+            if isinstance(a, np.ndarray):
+                assert a.dtype == np.float32 and a.flags.c_contiguous
+                return C.c_void_p(a.ctypes.data)
+            assert (not a.is_cuda) and a.is_contiguous()
+            return C.c_void_p(a.data_ptr())
+        e = C.c_double()
+        check(self._lib.dg_step_host(self._h, hptr(u_host), hptr(res_host), float(dt), int(nsteps),
+                                     C.byref(e) if with_energy else None, _stream_handle(stream)),
+              "dg_step_host")
+        return e.value if with_energy else None
+
+    def last_launch_count(self) -> int:
+        return int(self._lib.dg_last_launch_count(self._h))
+
+    def trace_enable(self, n: int):
+        """Clear the launch trace and reserve n launches (n = 0: tracing off)."""
+        check(self._lib.dg_trace_enable(self._h, int(n)), "dg_trace_enable")
+
+    def trace_read(self):
+        """(durations in ms, kernel kinds) of the launches traced so far."""
+        cnt = C.c_int64()
+        check(self._lib.dg_trace_read(self._h, None, None, 0, C.byref(cnt)), "dg_trace_read")
+        ms, kind = np.empty(cnt.value), np.empty(cnt.value, np.int32)
+        check(self._lib.dg_trace_read(self._h, _dptr(ms, np.float64), _dptr(kind, np.int32),
+                                      cnt.value, C.byref(cnt)), "dg_trace_read")
+        return ms, kind

@@ -1,0 +1,220 @@
+// C ABI entry points (include/dg.h): argument checking, error reporting and
+// dispatch to the host setup (refelem.cpp, mesh.cpp) and device code (device.cu).
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "dg_internal.h"
+
+namespace {
+
+thread_local std::string g_error;
+
+int fail(int code, const std::string& msg) {
+  g_error = msg;
+  return code;
+}
+
+int check_mesh(const dg_mesh* m, bool need_order) {
+  if (!m) return fail(DG_ERR_ARG, "mesh is NULL");
+  if (need_order && m->N == 0) return fail(DG_ERR_STATE, "dg_set_order() has not been called");
+  return DG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* dg_last_error(void) { return g_error.c_str(); }
+
+int dg_mesh_create(const double* verts, int64_t nv, const int32_t* tets, int64_t K,
+                   dg_mesh** out) {
+  if (!out) return fail(DG_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (!verts || !tets) return fail(DG_ERR_ARG, "verts or tets is NULL");
+  if (nv < 4 || K < 1) return fail(DG_ERR_ARG, "need nv >= 4 and K >= 1");
+  if (K >= (int64_t(1) << 31) / 220) return fail(DG_ERR_ARG, "K too large for 32-bit node ids");
+  dg_mesh* m = new (std::nothrow) dg_mesh();
+  if (!m) return fail(DG_ERR_OOM, "host allocation failed");
+  std::string err;
+  int rc;
+  try {
+    rc = dg::mesh_build(m, verts, nv, tets, K, err);
+  } catch (const std::bad_alloc&) {
+    rc = DG_ERR_OOM;
+    err = "host allocation failed";
+  }
+  if (rc != DG_OK) {
+    delete m;
+    return fail(rc, err);
+  }
+  *out = m;
+  return DG_OK;
+}
+
+int dg_set_order(dg_mesh* m, int N) {
+  if (int rc = check_mesh(m, false)) return rc;
+  if (N < 1 || N > dg::kMaxOrder) return fail(DG_ERR_ORDER, "order N must be in 1..9");
+  std::string err;
+  dg::RefOps ops;
+  try {
+    if (!dg::build_ref_ops(N, ops, err)) return fail(DG_ERR_ORDER, err);
+  } catch (const std::bad_alloc&) {
+    return fail(DG_ERR_OOM, "host allocation failed");
+  }
+  m->ops = std::move(ops);
+  m->N = N;
+  double mn = INFINITY;
+  for (double f : m->Fscale) mn = std::fmin(mn, 1.0 / f);
+  m->dt_cfl = mn * 2.0 / ((N + 1.0) * (N + 1.0));
+  return DG_OK;
+}
+
+int dg_info(const dg_mesh* m, int64_t* K, int* Np, int* Nfp, double* dt_cfl) {
+  if (int rc = check_mesh(m, true)) return rc;
+  if (K) *K = m->K;
+  if (Np) *Np = m->ops.Np;
+  if (Nfp) *Nfp = m->ops.Nfp;
+  if (dt_cfl) *dt_cfl = m->dt_cfl;
+  return DG_OK;
+}
+
+int dg_nodes(const dg_mesh* m, double* xyz) {
+  if (int rc = check_mesh(m, true)) return rc;
+  if (!xyz) return fail(DG_ERR_ARG, "xyz is NULL");
+  const int64_t K = m->K;
+  const int Np = m->ops.Np;
+  for (int64_t k = 0; k < K; ++k) {
+    const int32_t* tv = &m->tets[4 * k];
+    for (int i = 0; i < Np; ++i) {
+      const double r = m->ops.r[i], s = m->ops.s[i], t = m->ops.t[i];
+      const double w[4] = {-(1 + r + s + t) / 2, (1 + r) / 2, (1 + s) / 2, (1 + t) / 2};
+      for (int d = 0; d < 3; ++d) {
+        double x = 0.0;
+        for (int a = 0; a < 4; ++a) x += w[a] * m->verts[3 * tv[a] + d];
+        xyz[(d * K + k) * Np + i] = x;
+      }
+    }
+  }
+  return DG_OK;
+}
+
+int dg_get_connectivity(const dg_mesh* m, int32_t* vmapM, int32_t* vmapP) {
+  if (int rc = check_mesh(m, true)) return rc;
+  if (!vmapM || !vmapP) return fail(DG_ERR_ARG, "vmapM or vmapP is NULL");
+  const int Np = m->ops.Np, Nfp = m->ops.Nfp;
+  for (int64_t k = 0; k < m->K; ++k)
+    for (int f = 0; f < 4; ++f)
+      for (int j = 0; j < Nfp; ++j) {
+        const int64_t idx = (k * 4 + f) * Nfp + j;
+        const int32_t me = static_cast<int32_t>(k * Np + m->ops.Fmask[f * Nfp + j]);
+        vmapM[idx] = me;
+        const int code = m->nbr_code[4 * k + f];
+        if (code < 0) {
+          vmapP[idx] = me;
+        } else {
+          const int64_t k2 = m->nbr_elem[4 * k + f];
+          vmapP[idx] = static_cast<int32_t>(k2 * Np + m->ops.perm[(f * 24 + code) * Nfp + j]);
+        }
+      }
+  return DG_OK;
+}
+
+int dg_get_operators(const dg_mesh* m, double* Dr, double* Ds, double* Dt, double* M,
+                     double* LIFT) {
+  if (int rc = check_mesh(m, true)) return rc;
+  const size_t nn = m->ops.Dr.size() * sizeof(double);
+  if (Dr) std::memcpy(Dr, m->ops.Dr.data(), nn);
+  if (Ds) std::memcpy(Ds, m->ops.Ds.data(), nn);
+  if (Dt) std::memcpy(Dt, m->ops.Dt.data(), nn);
+  if (M) std::memcpy(M, m->ops.M.data(), nn);
+  if (LIFT) std::memcpy(LIFT, m->ops.LIFT.data(), m->ops.LIFT.size() * sizeof(double));
+  return DG_OK;
+}
+
+int dg_get_geometry(const dg_mesh* m, double* metric, double* J, double* normals,
+                    double* Fscale) {
+  if (int rc = check_mesh(m, false)) return rc;
+  if (metric) std::memcpy(metric, m->metric.data(), m->metric.size() * sizeof(double));
+  if (J) std::memcpy(J, m->J.data(), m->J.size() * sizeof(double));
+  if (normals) std::memcpy(normals, m->normals.data(), m->normals.size() * sizeof(double));
+  if (Fscale) std::memcpy(Fscale, m->Fscale.data(), m->Fscale.size() * sizeof(double));
+  return DG_OK;
+}
+
+int dg_set_flux(dg_mesh* m, double alpha) {
+  if (int rc = check_mesh(m, false)) return rc;
+  if (!std::isfinite(alpha) || alpha < 0.0) return fail(DG_ERR_ARG, "alpha must be finite and >= 0");
+  m->alpha = alpha;
+  return DG_OK;
+}
+
+int dg_rhs(dg_mesh* m, const float* u, float* rhs, void* stream) {
+  if (int rc = check_mesh(m, true)) return rc;
+  if (!u || !rhs) return fail(DG_ERR_ARG, "u or rhs is NULL");
+  if (u == rhs) return fail(DG_ERR_ARG, "rhs must not alias u");
+  std::string err;
+  if (int rc = dg::device_rhs(m, u, rhs, stream, err)) return fail(rc, err);
+  return DG_OK;
+}
+
+int dg_step(dg_mesh* m, float* u, float* res, double dt, int nsteps, void* stream) {
+  if (int rc = check_mesh(m, true)) return rc;
+  if (!u || !res) return fail(DG_ERR_ARG, "u or res is NULL");
+  if (u == res) return fail(DG_ERR_ARG, "res must not alias u");
+  if (!(dt > 0.0) || !std::isfinite(dt)) return fail(DG_ERR_ARG, "dt must be positive and finite");
+  if (nsteps < 0) return fail(DG_ERR_ARG, "nsteps must be >= 0");
+  std::string err;
+  if (int rc = dg::device_step(m, u, res, dt, nsteps, stream, err)) return fail(rc, err);
+  return DG_OK;
+}
+
+int dg_energy(dg_mesh* m, const float* u, double* out, void* stream) {
+  if (int rc = check_mesh(m, true)) return rc;
+  if (!u || !out) return fail(DG_ERR_ARG, "u or out is NULL");
+  std::string err;
+  if (int rc = dg::device_energy(m, u, out, stream, err)) return fail(rc, err);
+  return DG_OK;
+}
+
+int dg_step_host(dg_mesh* m, float* u, float* res, double dt, int nsteps, double* energy,
+                 void* stream) {
+  if (int rc = check_mesh(m, true)) return rc;
+  if (!u || !res) return fail(DG_ERR_ARG, "u or res is NULL");
+  if (u == res) return fail(DG_ERR_ARG, "res must not alias u");
+  if (!(dt > 0.0) || !std::isfinite(dt)) return fail(DG_ERR_ARG, "dt must be positive and finite");
+  if (nsteps < 0) return fail(DG_ERR_ARG, "nsteps must be >= 0");
+  std::string err;
+  if (int rc = dg::device_step_host(m, u, res, dt, nsteps, energy, stream, err)) return fail(rc, err);
+  return DG_OK;
+}
+
+int64_t dg_last_launch_count(const dg_mesh* m) { return m ? m->last_launches : 0; }
+
+int dg_trace_enable(dg_mesh* m, int n) {
+  if (int rc = check_mesh(m, false)) return rc;
+  if (n < 0) return fail(DG_ERR_ARG, "n must be >= 0");
+  m->trace = n > 0;
+  if (n == 0) return DG_OK;
+  if (int rc = check_mesh(m, true)) return rc;
+  std::string err;
+  if (int rc = dg::device_trace_reset(m, n, err)) return fail(rc, err);
+  return DG_OK;
+}
+
+int dg_trace_read(dg_mesh* m, double* ms, int32_t* kind, int64_t cap, int64_t* count) {
+  if (int rc = check_mesh(m, false)) return rc;
+  if (!count || (cap > 0 && !ms) || cap < 0) return fail(DG_ERR_ARG, "bad output arguments");
+  std::string err;
+  if (int rc = dg::device_trace_read(m, ms, kind, cap, count, err)) return fail(rc, err);
+  return DG_OK;
+}
+
+void dg_mesh_destroy(dg_mesh* m) {
+  if (!m) return;
+  dgdev::destroy_device_state(m->dev);
+  delete m;
+}
+
+}  // extern "C"

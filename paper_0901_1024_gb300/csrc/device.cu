@@ -1,0 +1,402 @@
+// Device buffers of a mesh, kernel dispatch, the energy reduction and the
+// host-facing device operations behind the C ABI.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "device.h"
+#include "dg_internal.h"
+
+namespace dgdev {
+
+template <int N>
+cudaError_t launch_stage_n(bool rk, const StageArgs& a, int num_sms, cudaStream_t s);
+
+cudaError_t launch_stage(int N, bool rk, const StageArgs& a, int num_sms, cudaStream_t s) {
+  switch (N) {
+    case 1: return launch_stage_n<1>(rk, a, num_sms, s);
+    case 2: return launch_stage_n<2>(rk, a, num_sms, s);
+    case 3: return launch_stage_n<3>(rk, a, num_sms, s);
+    case 4: return launch_stage_n<4>(rk, a, num_sms, s);
+    case 5: return launch_stage_n<5>(rk, a, num_sms, s);
+    case 6: return launch_stage_n<6>(rk, a, num_sms, s);
+    case 7: return launch_stage_n<7>(rk, a, num_sms, s);
+    case 8: return launch_stage_n<8>(rk, a, num_sms, s);
+    case 9: return launch_stage_n<9>(rk, a, num_sms, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+// ------------------------------------------------------------- energy -----
+// E = 1/2 sum_k J_k sum_c u_kc^T M u_kc.  One warp per element: lane i forms
+// (M u_c)_i (M symmetric, read column-wise = coalesced) and u_i (M u_c)_i in
+// FP32; the per-element sum is scaled by J_k and accumulated in FP64.  Each
+// block writes one FP64 partial; a one-thread kernel adds the partials in a
+// fixed order, so the result is deterministic.
+constexpr int kEnergyThreads = 256;
+
+__global__ void __launch_bounds__(kEnergyThreads) energy_kernel(const EnergyArgs A) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  constexpr int nw = kEnergyThreads / 32;
+  double acc = 0.0;
+  for (int k = blockIdx.x * nw + warp; k < A.K; k += gridDim.x * nw) {
+    float ek = 0.f;
+    for (int c = 0; c < 6; ++c) {
+      const float* uk = A.u + (size_t(c) * A.K + k) * A.Np;
+      for (int i = lane; i < A.Np; i += 32) {
+        float s = 0.f;
+        for (int j = 0; j < A.Np; ++j) s = fmaf(__ldg(A.M + j * A.Np + i), __ldg(uk + j), s);
+        ek = fmaf(__ldg(uk + i), s, ek);
+      }
+    }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) ek += __shfl_xor_sync(0xffffffffu, ek, o);
+    const float J = reinterpret_cast<const float*>(A.geo)[size_t(k) * kGeoWords + 9];
+    acc += double(J) * double(ek);
+  }
+  __shared__ double sw[nw];
+  if (lane == 0) sw[warp] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < nw; ++w) t += sw[w];
+    A.partials[blockIdx.x] = t;
+  }
+}
+
+__global__ void energy_finalize(const double* partials, int n, double* result) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    double t = 0.0;
+    for (int i = 0; i < n; ++i) t += partials[i];
+    result[0] = 0.5 * t;
+  }
+}
+
+int energy_grid(int num_sms) { return 4 * num_sms; }
+
+cudaError_t launch_energy_partials(const EnergyArgs& a, int grid, cudaStream_t s) {
+  energy_kernel<<<grid, kEnergyThreads, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_energy_final(const EnergyArgs& a, int grid, cudaStream_t s) {
+  energy_finalize<<<1, 32, 0, s>>>(a.partials, grid, a.result);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------- device state -----
+struct DeviceState {
+  int device = -1;
+  int N = 0;
+  int64_t K = 0;
+  int Np = 0, Nfp = 0;
+  int num_sms = 0;
+  float4* geo = nullptr;
+  float4* D4 = nullptr;
+  float4* LIFT4 = nullptr;
+  float* M = nullptr;
+  unsigned char* fmask = nullptr;
+  unsigned char* perm = nullptr;
+  float* u_work = nullptr;      // second state buffer for the stage ping-pong
+  float* h_u = nullptr;         // device copies for dg_step_host
+  float* h_res = nullptr;
+  double* partials = nullptr;   // energy partials, one per block
+  double* result = nullptr;
+  int egrid = 0;
+  // per-launch tracing: event pair 2i, 2i+1 around launch i
+  std::vector<cudaEvent_t> ev;
+  std::vector<int> kind;
+  size_t nrec = 0;
+};
+
+void destroy_device_state(DeviceState* d) {
+  if (!d) return;
+  int cur = -1;
+  cudaGetDevice(&cur);
+  if (d->device >= 0) cudaSetDevice(d->device);
+  cudaFree(d->geo); cudaFree(d->D4); cudaFree(d->LIFT4); cudaFree(d->M);
+  cudaFree(d->fmask); cudaFree(d->perm); cudaFree(d->u_work); cudaFree(d->h_u);
+  cudaFree(d->h_res); cudaFree(d->partials); cudaFree(d->result);
+  for (cudaEvent_t e : d->ev) cudaEventDestroy(e);
+  if (cur >= 0) cudaSetDevice(cur);
+  delete d;
+}
+
+}  // namespace dgdev
+
+namespace dg {
+using dgdev::DeviceState;
+
+static int cuda_fail(cudaError_t e, const char* what, std::string& err) {
+  err = std::string(what) + ": " + cudaGetErrorString(e);
+  return e == cudaErrorMemoryAllocation ? DG_ERR_OOM : DG_ERR_CUDA;
+}
+
+#define DG_CUDA(call, what)                                        \
+  do {                                                             \
+    cudaError_t e_ = (call);                                       \
+    if (e_ != cudaSuccess) return cuda_fail(e_, what, err);        \
+  } while (0)
+
+template <class T>
+static int upload(T** dst, const std::vector<T>& src, std::string& err) {
+  DG_CUDA(cudaMalloc(reinterpret_cast<void**>(dst), src.size() * sizeof(T)), "cudaMalloc");
+  DG_CUDA(cudaMemcpy(*dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice),
+          "cudaMemcpy H2D");
+  return DG_OK;
+}
+
+// Launches `fn` (returning cudaError_t) and, when tracing, brackets it with a
+// pair of events on stream s.
+template <class F>
+static cudaError_t traced(dg_mesh* m, cudaStream_t s, int kind, F&& fn) {
+  DeviceState* d = m->dev;
+  if (!m->trace) return fn();
+  const size_t i = d->nrec;
+  while (d->ev.size() < 2 * i + 2) {
+    cudaEvent_t e;
+    cudaError_t c = cudaEventCreate(&e);
+    if (c != cudaSuccess) return c;
+    d->ev.push_back(e);
+  }
+  if (d->kind.size() < i + 1) d->kind.resize(i + 1);
+  cudaError_t c = cudaEventRecord(d->ev[2 * i], s);
+  if (c != cudaSuccess) return c;
+  if ((c = fn()) != cudaSuccess) return c;
+  if ((c = cudaEventRecord(d->ev[2 * i + 1], s)) != cudaSuccess) return c;
+  d->kind[i] = kind;
+  d->nrec = i + 1;
+  return cudaSuccess;
+}
+
+int ensure_device(dg_mesh* m, std::string& err);
+
+int device_trace_reset(dg_mesh* m, int reserve, std::string& err) {
+  int rc = ensure_device(m, err);
+  if (rc) return rc;
+  DeviceState* d = m->dev;
+  d->nrec = 0;
+  while (d->ev.size() < 2 * static_cast<size_t>(reserve)) {
+    cudaEvent_t e;
+    DG_CUDA(cudaEventCreate(&e), "cudaEventCreate");
+    d->ev.push_back(e);
+  }
+  d->kind.resize(std::max(d->kind.size(), static_cast<size_t>(reserve)));
+  return DG_OK;
+}
+
+int device_trace_read(dg_mesh* m, double* ms, int32_t* kind, int64_t cap, int64_t* count,
+                      std::string& err) {
+  DeviceState* d = m->dev;
+  if (!d || d->nrec == 0) { err = "no traced launches recorded"; return DG_ERR_STATE; }
+  DG_CUDA(cudaEventSynchronize(d->ev[2 * d->nrec - 1]), "cudaEventSynchronize");
+  *count = static_cast<int64_t>(d->nrec);
+  for (size_t i = 0; i < d->nrec && static_cast<int64_t>(i) < cap; ++i) {
+    float t = 0.f;
+    DG_CUDA(cudaEventElapsedTime(&t, d->ev[2 * i], d->ev[2 * i + 1]), "cudaEventElapsedTime");
+    ms[i] = t;
+    if (kind) kind[i] = d->kind[i];
+  }
+  return DG_OK;
+}
+
+// Creates (or re-creates after an order change) the device copy of the mesh.
+int ensure_device(dg_mesh* m, std::string& err) {
+  if (m->N == 0) { err = "dg_set_order() has not been called"; return DG_ERR_STATE; }
+  int cur = 0;
+  DG_CUDA(cudaGetDevice(&cur), "cudaGetDevice");
+  if (m->dev && m->dev->N == m->N && m->dev->device == cur) return DG_OK;
+  if (m->dev) { dgdev::destroy_device_state(m->dev); m->dev = nullptr; }
+  auto* d = new DeviceState();
+  m->dev = d;
+  d->device = cur;
+  d->N = m->N;
+  d->K = m->K;
+  d->Np = m->ops.Np;
+  d->Nfp = m->ops.Nfp;
+  DG_CUDA(cudaDeviceGetAttribute(&d->num_sms, cudaDevAttrMultiProcessorCount, cur),
+          "cudaDeviceGetAttribute");
+  const int64_t K = m->K;
+  const int Np = d->Np, Nfp = d->Nfp, NF = 4 * Nfp;
+
+  // geometry records
+  std::vector<float> geo(static_cast<size_t>(K) * dgdev::kGeoWords, 0.f);
+  for (int64_t k = 0; k < K; ++k) {
+    float* g = &geo[k * dgdev::kGeoWords];
+    for (int a = 0; a < 9; ++a) g[a] = static_cast<float>(m->metric[a * K + k]);
+    g[9] = static_cast<float>(m->J[k]);
+    uint32_t codes = 0;
+    for (int f = 0; f < 4; ++f) {
+      const int c = m->nbr_code[4 * k + f];
+      codes |= static_cast<uint32_t>(c + 1) << (8 * f);
+      for (int dd = 0; dd < 3; ++dd)
+        g[12 + 4 * f + dd] = static_cast<float>(m->normals[(dd * K + k) * 4 + f]);
+      g[15 + 4 * f] = static_cast<float>(m->Fscale[4 * k + f]);
+      const int32_t nb = m->nbr_elem[4 * k + f];
+      std::memcpy(&g[28 + f], &nb, 4);
+    }
+    std::memcpy(&g[10], &codes, 4);
+  }
+  std::vector<float4> geo4(static_cast<size_t>(K) * dgdev::kGeoWords / 4);
+  std::memcpy(geo4.data(), geo.data(), geo.size() * sizeof(float));
+  int rc = upload(&d->geo, geo4, err);
+  if (rc) return rc;
+
+  std::vector<float4> D4(static_cast<size_t>(Np) * Np);
+  for (int i = 0; i < Np; ++i)
+    for (int j = 0; j < Np; ++j)
+      D4[i * Np + j] = make_float4(static_cast<float>(m->ops.Dr[i * Np + j]),
+                                   static_cast<float>(m->ops.Ds[i * Np + j]),
+                                   static_cast<float>(m->ops.Dt[i * Np + j]), 0.f);
+  if ((rc = upload(&d->D4, D4, err))) return rc;
+  std::vector<float4> L4(static_cast<size_t>(Np) * NF / 4);
+  for (int i = 0; i < Np; ++i)
+    for (int q = 0; q < NF / 4; ++q)
+      L4[i * (NF / 4) + q] = make_float4(static_cast<float>(m->ops.LIFT[i * NF + 4 * q + 0]),
+                                         static_cast<float>(m->ops.LIFT[i * NF + 4 * q + 1]),
+                                         static_cast<float>(m->ops.LIFT[i * NF + 4 * q + 2]),
+                                         static_cast<float>(m->ops.LIFT[i * NF + 4 * q + 3]));
+  if ((rc = upload(&d->LIFT4, L4, err))) return rc;
+  std::vector<float> Mf(m->ops.M.begin(), m->ops.M.end());
+  if ((rc = upload(&d->M, Mf, err))) return rc;
+  std::vector<unsigned char> fm(m->ops.Fmask.begin(), m->ops.Fmask.end());
+  if ((rc = upload(&d->fmask, fm, err))) return rc;
+  std::vector<unsigned char> pm(m->ops.perm.begin(), m->ops.perm.end());
+  if ((rc = upload(&d->perm, pm, err))) return rc;
+  d->egrid = dgdev::energy_grid(d->num_sms);
+  DG_CUDA(cudaMalloc(&d->partials, sizeof(double) * d->egrid), "cudaMalloc");
+  DG_CUDA(cudaMalloc(&d->result, sizeof(double)), "cudaMalloc");
+  return DG_OK;
+}
+
+static dgdev::StageArgs stage_args(dg_mesh* m) {
+  DeviceState* d = m->dev;
+  dgdev::StageArgs a{};
+  a.geo = d->geo;
+  a.D4 = d->D4;
+  a.LIFT4 = d->LIFT4;
+  a.fmask = d->fmask;
+  a.perm = d->perm;
+  a.K = static_cast<int>(d->K);
+  a.alpha = static_cast<float>(m->alpha);
+  const int E = dgdev::stage_tile_elems(d->N);
+  a.num_tiles = static_cast<int>((d->K + E - 1) / E);
+  return a;
+}
+
+int device_rhs(dg_mesh* m, const float* u, float* rhs, void* stream, std::string& err) {
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  int rc = ensure_device(m, err);
+  if (rc) return rc;
+  dgdev::StageArgs a = stage_args(m);
+  a.u_in = u;
+  a.rhs = rhs;
+  DG_CUDA(traced(m, s, 1, [&] { return dgdev::launch_stage(m->N, false, a, m->dev->num_sms, s); }),
+          "stage kernel launch");
+  m->last_launches = 1;
+  return DG_OK;
+}
+
+// LSERK4 coefficients (Carpenter & Kennedy 1994, five stages, two registers).
+static const double kRkA[5] = {0.0, -567301805773.0 / 1357537059087.0,
+                               -2404267990393.0 / 2016746695238.0,
+                               -3550918686646.0 / 2091501179385.0,
+                               -1275806237668.0 / 842570457699.0};
+static const double kRkB[5] = {1432997174477.0 / 9575080441755.0,
+                               5161836677717.0 / 13612068292357.0,
+                               1720146321549.0 / 2090206949498.0,
+                               3134564353537.0 / 4481467310338.0,
+                               2277821191437.0 / 14882151754819.0};
+
+static int step_impl(dg_mesh* m, float* u, float* res, double dt, int nsteps, cudaStream_t s,
+                     std::string& err) {
+  DeviceState* d = m->dev;
+  const size_t n = static_cast<size_t>(6) * d->K * d->Np;
+  if (!d->u_work) DG_CUDA(cudaMalloc(&d->u_work, n * sizeof(float)), "cudaMalloc work state");
+  dgdev::StageArgs a = stage_args(m);
+  a.res = res;
+  a.dt = static_cast<float>(dt);
+  const float* src = u;
+  float* dst = d->u_work;
+  int64_t launches = 0;
+  for (int st = 0; st < nsteps; ++st)
+    for (int i = 0; i < 5; ++i) {
+      a.u_in = src;
+      a.u_out = dst;
+      a.a = static_cast<float>(kRkA[i]);
+      a.b = static_cast<float>(kRkB[i]);
+      DG_CUDA(traced(m, s, 0, [&] { return dgdev::launch_stage(m->N, true, a, d->num_sms, s); }),
+              "stage kernel launch");
+      ++launches;
+      float* nsrc = dst;
+      dst = const_cast<float*>(src);
+      src = nsrc;
+    }
+  if (src != u)  // odd number of stages: the state sits in the work buffer
+    DG_CUDA(cudaMemcpyAsync(u, src, n * sizeof(float), cudaMemcpyDeviceToDevice, s),
+            "cudaMemcpyAsync D2D");
+  m->last_launches = launches;
+  return DG_OK;
+}
+
+int device_step(dg_mesh* m, float* u, float* res, double dt, int nsteps, void* stream,
+                std::string& err) {
+  int rc = ensure_device(m, err);
+  if (rc) return rc;
+  return step_impl(m, u, res, dt, nsteps, static_cast<cudaStream_t>(stream), err);
+}
+
+static int energy_impl(dg_mesh* m, const float* u, double* out, cudaStream_t s,
+                       std::string& err) {
+  DeviceState* d = m->dev;
+  dgdev::EnergyArgs a{u, d->M, d->geo, static_cast<int>(d->K), d->Np, d->partials, d->result};
+  DG_CUDA(traced(m, s, 2, [&] { return dgdev::launch_energy_partials(a, d->egrid, s); }),
+          "energy kernel launch");
+  DG_CUDA(traced(m, s, 3, [&] { return dgdev::launch_energy_final(a, d->egrid, s); }),
+          "energy kernel launch");
+  double h = 0.0;
+  DG_CUDA(cudaMemcpyAsync(&h, d->result, sizeof(double), cudaMemcpyDeviceToHost, s),
+          "cudaMemcpyAsync D2H");
+  DG_CUDA(cudaStreamSynchronize(s), "cudaStreamSynchronize");
+  *out = h;
+  m->last_launches = 2;
+  if (!std::isfinite(h)) { err = "energy is not finite (unstable run)"; return DG_ERR_UNSTABLE; }
+  return DG_OK;
+}
+
+int device_energy(dg_mesh* m, const float* u, double* out, void* stream, std::string& err) {
+  int rc = ensure_device(m, err);
+  if (rc) return rc;
+  return energy_impl(m, u, out, static_cast<cudaStream_t>(stream), err);
+}
+
+int device_step_host(dg_mesh* m, float* u, float* res, double dt, int nsteps, double* energy,
+                     void* stream, std::string& err) {
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  int rc = ensure_device(m, err);
+  if (rc) return rc;
+  DeviceState* d = m->dev;
+  const size_t bytes = static_cast<size_t>(6) * d->K * d->Np * sizeof(float);
+  if (!d->h_u) DG_CUDA(cudaMalloc(&d->h_u, bytes), "cudaMalloc");
+  if (!d->h_res) DG_CUDA(cudaMalloc(&d->h_res, bytes), "cudaMalloc");
+  DG_CUDA(cudaMemcpyAsync(d->h_u, u, bytes, cudaMemcpyHostToDevice, s), "cudaMemcpyAsync H2D");
+  DG_CUDA(cudaMemcpyAsync(d->h_res, res, bytes, cudaMemcpyHostToDevice, s), "cudaMemcpyAsync H2D");
+  if ((rc = step_impl(m, d->h_u, d->h_res, dt, nsteps, s, err))) return rc;
+  int64_t launches = m->last_launches;
+  DG_CUDA(cudaMemcpyAsync(u, d->h_u, bytes, cudaMemcpyDeviceToHost, s), "cudaMemcpyAsync D2H");
+  DG_CUDA(cudaMemcpyAsync(res, d->h_res, bytes, cudaMemcpyDeviceToHost, s), "cudaMemcpyAsync D2H");
+  if (energy) {
+    if ((rc = energy_impl(m, d->h_u, energy, s, err))) return rc;
+    launches += 2;
+  } else {
+    DG_CUDA(cudaStreamSynchronize(s), "cudaStreamSynchronize");
+  }
+  m->last_launches = launches;
+  return DG_OK;
+}
+
+}  // namespace dg

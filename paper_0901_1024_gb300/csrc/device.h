@@ -1,0 +1,57 @@
+// Device-side data of a mesh and the kernel launch interface.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace dgdev {
+
+// Per-element geometry record, 32 words (128 bytes), one per tetrahedron:
+//   [0..8]   rx ry rz sx sy sz tx ty tz   (dr_mu/dx_nu, Eq. dg-reference-matrices)
+//   [9]      J
+//   [10]     neighbour codes, byte f = (g*6 + sigma) + 1 of face f, 0 = wall
+//   [11]     unused
+//   [12+4f .. 15+4f]  nx ny nz Fscale of face f
+//   [28+f]   neighbour element of face f (int32; itself on a wall)
+constexpr int kGeoWords = 32;
+
+// Stage-kernel tiling per order N: tile of E tetrahedra, G row groups (threads
+// = E * G).  Chosen so a thread holds at most 7 rows and the shared tiles of
+// one CTA stay near 100 KB.
+__host__ __device__ constexpr int stage_tile_elems(int N) { return N <= 5 ? 32 : (N <= 7 ? 16 : 8); }
+__host__ __device__ constexpr int stage_row_groups(int N) {
+  return N == 1 ? 4 : N <= 3 ? 5 : N == 4 ? 7 : N == 5 ? 8 : N == 6 ? 12 : N == 7 ? 18 : N == 8 ? 28 : 32;
+}
+
+struct StageArgs {
+  const float* u_in;       // [6][K][Np]
+  float* u_out;            // [6][K][Np] (RK mode)
+  float* res;              // [6][K][Np] (RK mode, in/out)
+  float* rhs;              // [6][K][Np] (RHS mode)
+  const float4* geo;       // [K][8] float4
+  const float4* D4;        // [Np][Np] (Dr, Ds, Dt, 0)
+  const float4* LIFT4;     // [Np][4*Nfp/4]
+  const unsigned char* fmask;  // [4][Nfp]
+  const unsigned char* perm;   // [4][24][Nfp]
+  int K;
+  int num_tiles;
+  float a, b, dt, alpha;
+};
+
+// Launches one RK stage (rk = true: res <- a res + dt rhs, u_out <- u_in + b res)
+// or one bare right-hand-side evaluation (rk = false: rhs <- rhs(u_in)).
+cudaError_t launch_stage(int N, bool rk, const StageArgs& a, int num_sms, cudaStream_t s);
+
+struct EnergyArgs {
+  const float* u;      // [6][K][Np]
+  const float* M;      // [Np][Np]
+  const float4* geo;   // for J
+  int K, Np;
+  double* partials;    // [grid]
+  double* result;      // [1]
+};
+int energy_grid(int num_sms);
+cudaError_t launch_energy_partials(const EnergyArgs& a, int grid, cudaStream_t s);
+cudaError_t launch_energy_final(const EnergyArgs& a, int grid, cudaStream_t s);
+
+}  // namespace dgdev

@@ -1,0 +1,274 @@
+// One RK stage of the nodal DG Maxwell operator, fused in a single kernel
+// (FP32, CUDA cores).  Included by stage_n<N>.cu, one translation unit per order.
+//
+// Per tile of E consecutive tetrahedra (one CTA, persistent over tiles):
+//   1. stage the six fields u[c][k][0..Np) and the 128-byte geometry records of
+//      the tile in shared memory (coalesced loads);
+//   2. flux extraction (Alg. 2 of the paper): for every face node, u- from the
+//      tile, u+ from the tile when the neighbour is in it and from global
+//      memory otherwise (PEC ghost on walls), the upwind flux of Section 6
+//      scaled by Fscale/2, into a shared flux tile [6][E][4 Nfp];
+//   3. local differentiation (Alg. 4): U_r, U_s, U_t = Dr U, Ds U, Dt U for
+//      three fields at a time, chain rule with the element's metric terms
+//      (Eq. dg-reference-matrices) and the curl (Eq. maxwells-claws),
+//      accumulated in registers;
+//   4. flux lifting (Alg. 1): rhs += LIFT * flux;
+//   5. epilogue: either rhs -> global, or the LSERK4 update
+//      res <- a res + dt rhs, u_out <- u + b res, so rhs never reaches HBM.
+// The operator reads u_in and writes u_out (a different buffer): neighbours
+// read u_in's face values during the same launch.
+//
+// Thread mapping: thread t = e + E*g handles element e of the tile and the
+// rows (nodes) i = g + G*q, q < R, of the volume and lifting products.  With
+// E = 32 every warp shares one g, so the matrix rows it reads are warp-uniform
+// (one broadcast load per row); element-strided shared-memory rows use odd
+// strides (no bank conflicts).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "device.h"
+
+namespace dgdev {
+
+template <int N> struct StageDims {
+  static constexpr int Np = (N + 1) * (N + 2) * (N + 3) / 6;
+  static constexpr int Nfp = (N + 1) * (N + 2) / 2;
+  static constexpr int NF = 4 * Nfp;
+  static constexpr int E = stage_tile_elems(N), G = stage_row_groups(N);
+  static constexpr int T = E * G;
+  static constexpr int R = (Np + G - 1) / G;
+  static constexpr int US = Np | 1;                          // odd element stride
+  static constexpr int FS = (Nfp % 2) ? NF : NF + 4;         // FS/4 odd: conflict-free float4
+  static constexpr int UT = 6 * E * US;
+  static constexpr int FT = 6 * E * (FS > US ? FS : US);     // flux tile, reused for rhs
+  static constexpr int GT = E * kGeoWords;
+  static constexpr size_t smem_bytes = size_t(UT + FT + GT) * sizeof(float);
+  static_assert((UT % 4) == 0 && (FT % 4) == 0, "tiles must stay 16-byte aligned");
+};
+
+template <int N, bool RK>
+__global__ void __launch_bounds__(StageDims<N>::T) stage_kernel(const StageArgs A) {
+  using D = StageDims<N>;
+  constexpr int E = D::E, G = D::G, Np = D::Np, Nfp = D::Nfp, NF = D::NF, R = D::R;
+  constexpr int US = D::US, FS = D::FS;
+  extern __shared__ float4 smem4[];
+  float* su = reinterpret_cast<float*>(smem4);
+  float* sf = su + D::UT;
+  float* sg = sf + D::FT;
+  const int tid = threadIdx.x;
+  const int e = tid % E, g = tid / E;
+  const int K = A.K;
+
+  for (int tile = blockIdx.x; tile < A.num_tiles; tile += gridDim.x) {
+    const int k0 = tile * E;
+    const int Ev = min(E, K - k0);
+
+    // ---- 1. stage geometry and fields -------------------------------------
+    for (int idx = tid; idx < Ev * (kGeoWords / 4); idx += D::T)
+      reinterpret_cast<float4*>(sg)[idx] = __ldg(&A.geo[size_t(k0) * (kGeoWords / 4) + idx]);
+#pragma unroll
+    for (int c = 0; c < 6; ++c) {
+      const float* src = A.u_in + (size_t(c) * K + k0) * Np;
+      for (int idx = tid; idx < Ev * Np; idx += D::T) {
+        const int ee = idx / Np, i = idx - ee * Np;
+        su[(c * E + ee) * US + i] = __ldg(src + idx);
+      }
+    }
+    __syncthreads();
+
+    // ---- 2. flux extraction -----------------------------------------------
+    if (e < Ev) {
+      const float* ge = sg + e * kGeoWords;
+      const unsigned codes = __float_as_uint(ge[10]);
+#pragma unroll
+      for (int qm = 0; qm < (NF + G - 1) / G; ++qm) {
+        const int m = g + G * qm;
+        if (m >= NF) break;
+        const int f = m / Nfp, j = m - f * Nfp;
+        const int idM = __ldg(A.fmask + f * Nfp + j);
+        float uM[6], uP[6];
+#pragma unroll
+        for (int c = 0; c < 6; ++c) uM[c] = su[(c * E + e) * US + idM];
+        const unsigned code = (codes >> (8 * f)) & 0xffu;
+        if (code == 0u) {                       // perfectly conducting wall
+#pragma unroll
+          for (int c = 0; c < 3; ++c) { uP[c] = -uM[c]; uP[c + 3] = uM[c + 3]; }
+        } else {
+          const int k2 = __float_as_int(ge[28 + f]);
+          const int i2 = __ldg(A.perm + (f * 24 + int(code) - 1) * Nfp + j);
+          const int e2 = k2 - k0;
+          if (e2 >= 0 && e2 < Ev) {
+#pragma unroll
+            for (int c = 0; c < 6; ++c) uP[c] = su[(c * E + e2) * US + i2];
+          } else {
+#pragma unroll
+            for (int c = 0; c < 6; ++c) uP[c] = __ldg(A.u_in + (size_t(c) * K + k2) * Np + i2);
+          }
+        }
+        const float nx = ge[12 + 4 * f], ny = ge[13 + 4 * f], nz = ge[14 + 4 * f];
+        const float sc = 0.5f * ge[15 + 4 * f];
+        const float dEx = uM[0] - uP[0], dEy = uM[1] - uP[1], dEz = uM[2] - uP[2];
+        const float dHx = uM[3] - uP[3], dHy = uM[4] - uP[4], dHz = uM[5] - uP[5];
+        const float ndE = nx * dEx + ny * dEy + nz * dEz;
+        const float ndH = nx * dHx + ny * dHy + nz * dHz;
+        const float al = A.alpha;
+        // E: -n x dH + alpha (n (n.dE) - dE);  H: n x dE + alpha (n (n.dH) - dH)
+        const float fl[6] = {
+            -(ny * dHz - nz * dHy) + al * (nx * ndE - dEx),
+            -(nz * dHx - nx * dHz) + al * (ny * ndE - dEy),
+            -(nx * dHy - ny * dHx) + al * (nz * ndE - dEz),
+            (ny * dEz - nz * dEy) + al * (nx * ndH - dHx),
+            (nz * dEx - nx * dEz) + al * (ny * ndH - dHy),
+            (nx * dEy - ny * dEx) + al * (nz * ndH - dHz)};
+#pragma unroll
+        for (int c = 0; c < 6; ++c) sf[(c * E + e) * FS + m] = sc * fl[c];
+      }
+    }
+    __syncthreads();
+
+    // ---- 3. local differentiation and curl -------------------------------
+    float rhs[6][R];
+    int row[R];
+#pragma unroll
+    for (int q = 0; q < R; ++q) row[q] = min(g + G * q, Np - 1);
+    {
+      const float* ge = sg + e * kGeoWords;
+      const float rx = ge[0], ry = ge[1], rz = ge[2];
+      const float sx = ge[3], sy = ge[4], sz = ge[5];
+      const float tx = ge[6], ty = ge[7], tz = ge[8];
+#pragma unroll
+      for (int pass = 0; pass < 2; ++pass) {
+        const int fb = pass == 0 ? 3 : 0;          // H fields first (curl H), then E
+        const float* u0 = su + ((fb + 0) * E + e) * US;
+        const float* u1 = su + ((fb + 1) * E + e) * US;
+        const float* u2 = su + ((fb + 2) * E + e) * US;
+        float acc[3][3][R];
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+#pragma unroll
+          for (int d = 0; d < 3; ++d)
+#pragma unroll
+            for (int q = 0; q < R; ++q) acc[c][d][q] = 0.f;
+#pragma unroll 5
+        for (int j = 0; j < Np; ++j) {
+          const float v0 = u0[j], v1 = u1[j], v2 = u2[j];
+#pragma unroll
+          for (int q = 0; q < R; ++q) {
+            const float4 dm = __ldg(&A.D4[row[q] * Np + j]);
+            acc[0][0][q] = fmaf(dm.x, v0, acc[0][0][q]);
+            acc[0][1][q] = fmaf(dm.y, v0, acc[0][1][q]);
+            acc[0][2][q] = fmaf(dm.z, v0, acc[0][2][q]);
+            acc[1][0][q] = fmaf(dm.x, v1, acc[1][0][q]);
+            acc[1][1][q] = fmaf(dm.y, v1, acc[1][1][q]);
+            acc[1][2][q] = fmaf(dm.z, v1, acc[1][2][q]);
+            acc[2][0][q] = fmaf(dm.x, v2, acc[2][0][q]);
+            acc[2][1][q] = fmaf(dm.y, v2, acc[2][1][q]);
+            acc[2][2][q] = fmaf(dm.z, v2, acc[2][2][q]);
+          }
+        }
+#pragma unroll
+        for (int q = 0; q < R; ++q) {
+          float dx[3], dy[3], dz[3];
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            dx[c] = rx * acc[c][0][q] + sx * acc[c][1][q] + tx * acc[c][2][q];
+            dy[c] = ry * acc[c][0][q] + sy * acc[c][1][q] + ty * acc[c][2][q];
+            dz[c] = rz * acc[c][0][q] + sz * acc[c][1][q] + tz * acc[c][2][q];
+          }
+          const float cx = dy[2] - dz[1], cy = dz[0] - dx[2], cz = dx[1] - dy[0];
+          if (pass == 0) {        // dE/dt = curl H
+            rhs[0][q] = cx; rhs[1][q] = cy; rhs[2][q] = cz;
+          } else {                // dH/dt = -curl E
+            rhs[3][q] = -cx; rhs[4][q] = -cy; rhs[5][q] = -cz;
+          }
+        }
+      }
+    }
+
+    // ---- 4. lifting ------------------------------------------------------
+    {
+      const float4* f4[6];
+#pragma unroll
+      for (int c = 0; c < 6; ++c) f4[c] = reinterpret_cast<const float4*>(sf + (c * E + e) * FS);
+#pragma unroll 3
+      for (int m4 = 0; m4 < NF / 4; ++m4) {
+        float4 fv[6];
+#pragma unroll
+        for (int c = 0; c < 6; ++c) fv[c] = f4[c][m4];
+#pragma unroll
+        for (int q = 0; q < R; ++q) {
+          const float4 L = __ldg(&A.LIFT4[row[q] * (NF / 4) + m4]);
+#pragma unroll
+          for (int c = 0; c < 6; ++c) {
+            float s = rhs[c][q];
+            s = fmaf(L.x, fv[c].x, s);
+            s = fmaf(L.y, fv[c].y, s);
+            s = fmaf(L.z, fv[c].z, s);
+            s = fmaf(L.w, fv[c].w, s);
+            rhs[c][q] = s;
+          }
+        }
+      }
+    }
+    __syncthreads();                         // flux tile no longer needed
+#pragma unroll
+    for (int q = 0; q < R; ++q) {
+      const int i = g + G * q;
+      if (i < Np && e < Ev) {
+#pragma unroll
+        for (int c = 0; c < 6; ++c) sf[(c * E + e) * US + i] = rhs[c][q];
+      }
+    }
+    __syncthreads();
+
+    // ---- 5. epilogue -----------------------------------------------------
+#pragma unroll
+    for (int c = 0; c < 6; ++c) {
+      const size_t base = (size_t(c) * K + k0) * Np;
+      for (int idx = tid; idx < Ev * Np; idx += D::T) {
+        const int ee = idx / Np, i = idx - ee * Np;
+        const float r = sf[(c * E + ee) * US + i];
+        if (RK) {
+          const float rn = fmaf(A.a, A.res[base + idx], A.dt * r);
+          A.res[base + idx] = rn;
+          A.u_out[base + idx] = fmaf(A.b, rn, su[(c * E + ee) * US + i]);
+        } else {
+          A.rhs[base + idx] = r;
+        }
+      }
+    }
+    __syncthreads();
+  }
+}
+
+template <int N>
+cudaError_t launch_stage_n(bool rk, const StageArgs& a, int num_sms, cudaStream_t s) {
+  using D = StageDims<N>;
+  static int occ[2][16] = {};
+  int dev = 0;
+  cudaError_t err = cudaGetDevice(&dev);
+  if (err != cudaSuccess) return err;
+  dev &= 15;
+  auto kern = rk ? stage_kernel<N, true> : stage_kernel<N, false>;
+  int& o = occ[rk ? 1 : 0][dev];
+  if (o == 0) {
+    err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               int(D::smem_bytes));
+    if (err != cudaSuccess) return err;
+    err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, kern, D::T, D::smem_bytes);
+    if (err != cudaSuccess) return err;
+    if (o < 1) o = 1;
+  }
+  const int grid = a.num_tiles < num_sms * o ? a.num_tiles : num_sms * o;
+  if (grid <= 0) return cudaSuccess;
+  kern<<<grid, D::T, D::smem_bytes, s>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace dgdev
+
+#define DG_INSTANTIATE_STAGE(NN)                                                          \
+  namespace dgdev {                                                                        \
+  template cudaError_t launch_stage_n<NN>(bool, const StageArgs&, int, cudaStream_t);      \
+  }

@@ -1,0 +1,123 @@
+"""C-ABI library on the CPU: it loads, exports every declared symbol, and its
+host-side setup (nodes, operators, geometry, connectivity, CFL step, error
+codes) matches the oracle.  No device computation is called here."""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+from workloads import kuhn_box_mesh
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="session")
+def dg():
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_0901_1024_gb300 as pkg
+    return pkg
+
+
+def _declared_symbols():
+    text = open(os.path.join(ROOT, "include", "dg.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(dg_[a-z0-9_]+)\s*\(", text)))
+
+
+def test_library_exports_every_declared_symbol(dg):
+    lib = C.CDLL(dg.library_path())
+    names = _declared_symbols()
+    assert len(names) >= 15
+    for n in names:
+        assert hasattr(lib, n), n
+    from paper_0901_1024_gb300._capi import SIGNATURES
+    assert sorted(SIGNATURES) == names
+
+
+@pytest.mark.parametrize("N", range(1, 10))
+def test_operators_and_nodes_match_oracle(dg, N):
+    verts, tets = kuhn_box_mesh(1, 0.1, 0)
+    m = dg.Mesh(verts, tets, N)
+    ref = oracle.ref_element(N)
+    assert (m.Np, m.Nfp) == (ref.Np, ref.Nfp)
+    ops = m.operators()
+    tol = 1e-12 * N ** 2
+    for name, want in (("Dr", ref.Dr), ("Ds", ref.Ds), ("Dt", ref.Dt), ("LIFT", ref.LIFT)):
+        assert np.abs(ops[name] - want).max() < tol * max(1, np.abs(want).max()), name
+    assert np.abs(ops["M"] - ref.M).max() < 1e-13 * N
+    om = oracle.build_mesh(verts, tets, N)
+    xyz = m.nodes()
+    assert np.abs(xyz - np.stack([om.x, om.y, om.z])).max() < 1e-13
+
+
+@pytest.mark.parametrize("n,N,jit,seed", [(2, 1, 0.1, 0), (2, 2, 0.15, 3), (3, 3, 0.1, 1), (2, 4, 0.15, 2),
+                                          (1, 7, 0.1, 5), (1, 9, 0.0, 0)])
+def test_connectivity_bit_exact(dg, n, N, jit, seed):
+    verts, tets = kuhn_box_mesh(n, jit, seed)
+    # shuffle the element order and the vertex order inside each tetrahedron
+    rng = np.random.default_rng(seed)
+    tets = tets[rng.permutation(len(tets))]
+    tets = np.array([t[rng.permutation(4)] for t in tets], dtype=np.int32)
+    m = dg.Mesh(verts, tets, N)
+    om = oracle.build_mesh(verts, tets, N)
+    vM, vP = m.connectivity()
+    assert np.array_equal(vM, om.vmapM.astype(np.int32))
+    assert np.array_equal(vP, om.vmapP.astype(np.int32))
+
+
+def test_geometry_and_cfl_match_oracle(dg):
+    verts, tets = kuhn_box_mesh(3, 0.15, 4)
+    m = dg.Mesh(verts, tets, 4)
+    om = oracle.build_mesh(verts, tets, 4)
+    g = m.geometry()
+    want = np.stack([om.rx, om.ry, om.rz, om.sx, om.sy, om.sz, om.tx, om.ty, om.tz])
+    assert np.abs(g["metric"] - want).max() < 1e-11 * np.abs(want).max()
+    assert np.allclose(g["J"], om.J, rtol=1e-13)
+    assert np.abs(g["normals"] - np.stack([om.nx, om.ny, om.nz])).max() < 1e-13
+    assert np.allclose(g["Fscale"], om.Fscale, rtol=1e-13)
+    assert abs(m.dt_cfl - oracle.cfl_dt(om)) < 1e-15 * m.dt_cfl * 10
+
+
+def test_error_codes(dg):
+    from paper_0901_1024_gb300 import DGError
+    verts = np.array([[0, 0, 0], [1, 0, 0], [0, 1, 0], [0, 0, 1], [1, 1, 1], [-1, -1, -1]], float)
+    with pytest.raises(DGError) as ei:
+        dg.Mesh(verts, np.array([[0, 1, 2, 7]]))
+    assert ei.value.code == -2
+    with pytest.raises(DGError) as ei:       # zero volume
+        dg.Mesh(np.array([[0, 0, 0], [1, 0, 0], [0, 1, 0], [1, 1, 0]], float), np.array([[0, 1, 2, 3]]))
+    assert ei.value.code == -2
+    with pytest.raises(DGError) as ei:       # face shared by three tets
+        dg.Mesh(verts, np.array([[0, 1, 2, 3], [0, 1, 2, 4], [0, 1, 2, 5]]))
+    assert ei.value.code == -2
+    m = dg.Mesh(verts[:5], np.array([[0, 1, 2, 3], [1, 2, 3, 4]]))
+    with pytest.raises(DGError) as ei:
+        m.set_order(10)
+    assert ei.value.code == -3
+    with pytest.raises(DGError) as ei:
+        m.set_order(0)
+    assert ei.value.code == -3
+    lib = dg.load()
+    assert lib.dg_info(m._h, None, None, None, None) == -7      # no order yet
+    assert lib.dg_rhs(m._h, None, None, None) == -7
+    m.set_order(2)
+    assert lib.dg_rhs(m._h, None, None, None) == -1
+    assert lib.dg_step(m._h, C.c_void_p(16), C.c_void_p(32), C.c_double(-1.0), 1, None) == -1
+    assert lib.dg_step(m._h, C.c_void_p(16), C.c_void_p(16), C.c_double(1.0), 1, None) == -1
+    assert lib.dg_set_flux(m._h, C.c_double(float("nan"))) == -1
+    assert b"dt must be" in lib.dg_last_error() or b"alpha" in lib.dg_last_error()
+    assert lib.dg_mesh_create(None, 0, None, 0, None) == -1
+    lib.dg_mesh_destroy(None)
+
+
+def test_two_tet_connectivity_matches_hand_count(dg):
+    verts = np.array([[0, 0, 0], [1, 0, 0], [0, 1, 0], [0, 0, 1], [1, 1, 1]], float)
+    m = dg.Mesh(verts, np.array([[0, 1, 2, 3], [1, 2, 3, 4]]), 1)
+    vM, vP = m.connectivity()
+    vP = vP.reshape(2, 4, 3)
+    assert list(vP[0, 2]) == [4, 5, 6] and list(vP[1, 0]) == [1, 2, 3]
+    assert (vP.reshape(-1) != vM).sum() == 6

@@ -1,0 +1,230 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle.
+
+Tolerances (relative L2 over all 6*K*Np nodal values): 1e-5 for one FP32
+right-hand side, 1e-4 after 100 LSERK4 steps, 1e-6 for the energy.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from workloads import cavity_mode, gaussian_pulse, kuhn_box_mesh, pulse_center, random_fields
+
+pytestmark = pytest.mark.gpu
+
+RHS_TOL = 1e-5
+STEP_TOL = 1e-4
+
+
+@pytest.fixture(scope="module")
+def env():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_0901_1024_gb300 as dg
+    return torch, dg
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a, np.float64) - b) / np.linalg.norm(b))
+
+
+def _setup(dg, verts, tets, N):
+    return dg.Mesh(verts, tets, N), oracle.build_mesh(verts, tets, N)
+
+
+def _gpu_rhs(torch, mesh, u32, alpha=None):
+    if alpha is not None:
+        mesh.set_flux(alpha)
+    u = torch.from_numpy(u32).cuda()
+    out = torch.full_like(u, float("nan"))
+    mesh.rhs(u, out)
+    torch.cuda.synchronize()
+    return out.cpu().numpy()
+
+
+@pytest.mark.parametrize("N", range(1, 10))
+def test_rhs_parity_all_orders(env, N):
+    torch, dg = env
+    n = 3 if N <= 4 else 2
+    verts, tets = kuhn_box_mesh(n, 0.15, N)          # K = 162 or 48: ragged last tile
+    mesh, om = _setup(dg, verts, tets, N)
+    u32 = random_fields(om.K, om.Np, 10 + N).astype(np.float32)
+    got = _gpu_rhs(torch, mesh, u32)
+    want = oracle.rhs(om, u32.astype(np.float64))
+    assert np.isfinite(got).all()
+    assert rel(got, want) < RHS_TOL
+
+
+@pytest.mark.parametrize("N", [2, 4, 6])
+def test_rhs_parity_smooth_fields_and_central_flux(env, N):
+    torch, dg = env
+    verts, tets = kuhn_box_mesh(3, 0.1, 2)
+    mesh, om = _setup(dg, verts, tets, N)
+    u32 = cavity_mode(om.x, om.y, om.z, 0.0).astype(np.float32)
+    u32[3:] = gaussian_pulse(om.x, om.y, om.z, 0.4, (0.1, -0.2, 0.3))[2]
+    for alpha in (1.0, 0.0):
+        got = _gpu_rhs(torch, mesh, u32, alpha)
+        want = oracle.rhs(om, u32.astype(np.float64), alpha=alpha)
+        assert rel(got, want) < RHS_TOL
+
+
+@pytest.mark.parametrize("case", ["single_tet", "two_tets", "one_tile_plus_one", "all_wall_hex"])
+def test_rhs_edge_cases(env, case):
+    torch, dg = env
+    if case == "single_tet":
+        verts = np.array([[0, 0, 0], [1, 0, 0], [0, 1, 0], [0, 0, 1]], float)
+        tets = np.array([[0, 1, 3, 2]])                  # negatively oriented: swapped internally
+    elif case == "two_tets":
+        verts = np.array([[0, 0, 0], [1, 0, 0], [0, 1, 0], [0, 0, 1], [0.9, 1.1, 1.2]], float)
+        tets = np.array([[0, 1, 2, 3], [1, 2, 3, 4]])
+    elif case == "one_tile_plus_one":                   # 33 elements: full tile + 1
+        verts, tets = kuhn_box_mesh(2, 0.1, 7)
+        tets = tets[:33]
+    else:                                                # 6 tets, every tet has wall faces
+        verts, tets = kuhn_box_mesh(1, 0.0, 0)
+    for N in (1, 4, 9):
+        mesh, om = _setup(dg, verts, tets, N)
+        u32 = random_fields(om.K, om.Np, N).astype(np.float32)
+        got = _gpu_rhs(torch, mesh, u32)
+        assert rel(got, oracle.rhs(om, u32.astype(np.float64))) < RHS_TOL
+
+
+@pytest.mark.parametrize("N", [1, 3, 5])
+def test_step_parity_100_steps(env, N):
+    torch, dg = env
+    verts, tets = kuhn_box_mesh(2, 0.1, 0)
+    mesh, om = _setup(dg, verts, tets, N)
+    u0 = cavity_mode(om.x, om.y, om.z, 0.0).astype(np.float32)
+    dt = mesh.dt_cfl
+    u = torch.from_numpy(u0).cuda()
+    res = torch.zeros_like(u)
+    mesh.step(u, res, dt, 100)
+    torch.cuda.synchronize()
+    ue, re_ = oracle.lserk4_run(om, u0.astype(np.float64), dt, 100)
+    assert rel(u.cpu().numpy(), ue) < STEP_TOL
+    assert rel(res.cpu().numpy(), re_) < 10 * STEP_TOL
+
+
+def test_golden_cavity_run_fp64_config(env):
+    """N=3 on 4^3 x 6 = 384 jittered tets, cavity mode, 10 LSERK4 steps at the CFL step."""
+    torch, dg = env
+    verts, tets = kuhn_box_mesh(4, 0.1, 0)
+    mesh, om = _setup(dg, verts, tets, 3)
+    u0 = cavity_mode(om.x, om.y, om.z, 0.0).astype(np.float32)
+    dt = mesh.dt_cfl
+    u = torch.from_numpy(u0).cuda()
+    res = torch.zeros_like(u)
+    e0 = mesh.energy(u)
+    for _ in range(10):                       # 10 calls of one step (odd stage count each)
+        mesh.step(u, res, dt, 1)
+    e1 = mesh.energy(u)
+    ue, _ = oracle.lserk4_run(om, u0.astype(np.float64), dt, 10)
+    assert rel(u.cpu().numpy(), ue) < STEP_TOL
+    assert abs(e1 - oracle.energy(om, ue)) < 1e-6 * oracle.energy(om, ue)
+    assert e1 <= e0 * (1 + 1e-6)
+
+
+@pytest.mark.parametrize("N", [1, 4, 9])
+def test_energy_parity(env, N):
+    torch, dg = env
+    verts, tets = kuhn_box_mesh(2, 0.15, 1)
+    mesh, om = _setup(dg, verts, tets, N)
+    u32 = random_fields(om.K, om.Np, 3).astype(np.float32)
+    e = mesh.energy(torch.from_numpy(u32).cuda())
+    eo = oracle.energy(om, u32.astype(np.float64))
+    assert abs(e - eo) < 1e-6 * eo
+
+
+def test_step_host_matches_device_step(env):
+    torch, dg = env
+    verts, tets = kuhn_box_mesh(3, 0.1, 0)
+    mesh = dg.Mesh(verts, tets, 4)
+    x = mesh.nodes()
+    u0 = cavity_mode(x[0], x[1], x[2], 0.0).astype(np.float32)
+    uh, rh = u0.copy(), np.zeros_like(u0)
+    eh = mesh.step_host(uh, rh, mesh.dt_cfl, 3)
+    ud, rd = torch.from_numpy(u0).cuda(), torch.zeros(u0.shape, device="cuda")
+    mesh.step(ud, rd, mesh.dt_cfl, 3)
+    torch.cuda.synchronize()
+    assert np.array_equal(uh, ud.cpu().numpy()) and np.array_equal(rh, rd.cpu().numpy())
+    assert abs(eh - mesh.energy(ud)) <= 1e-12 * eh
+
+
+def test_step_is_deterministic_and_resumable(env):
+    """Checkpoint/resume: 2+3 steps bit-identical to 5 steps."""
+    torch, dg = env
+    verts, tets = kuhn_box_mesh(3, 0.1, 0)
+    mesh = dg.Mesh(verts, tets, 3)
+    u0 = torch.from_numpy(random_fields(mesh.K, mesh.Np, 4).astype(np.float32)).cuda()
+    a, ra = u0.clone(), torch.zeros_like(u0)
+    mesh.step(a, ra, mesh.dt_cfl, 5)
+    b, rb = u0.clone(), torch.zeros_like(u0)
+    mesh.step(b, rb, mesh.dt_cfl, 2)
+    b2, rb2 = b.cpu().clone(), rb.cpu().clone()          # host checkpoint
+    b.copy_(b2.cuda()); rb.copy_(rb2.cuda())
+    mesh.step(b, rb, mesh.dt_cfl, 3)
+    torch.cuda.synchronize()
+    assert torch.equal(a, b) and torch.equal(ra, rb)
+
+
+# ---------------------------------------------------------------------------
+# full-size workload (N=4, 24^3 x 6 = 82 944 tets), sampled against the oracle
+# ---------------------------------------------------------------------------
+def _vertex_rings(tets, seeds, rings):
+    """Tetrahedra within `rings` vertex-adjacency steps of the seed elements."""
+    sel = np.zeros(len(tets), bool)
+    sel[seeds] = True
+    for _ in range(rings):
+        vs = np.unique(tets[sel])
+        sel |= np.isin(tets, vs).any(axis=1)
+    return np.nonzero(sel)[0]
+
+
+def _oracle_on_patch(verts, tets, patch, N):
+    return oracle.build_mesh(verts, tets[patch], N)
+
+
+@pytest.fixture(scope="module")
+def full(env):
+    torch, dg = env
+    verts, tets = kuhn_box_mesh(24, 0.15, 0)
+    mesh = dg.Mesh(verts, tets, 4)
+    x = mesh.nodes()
+    u0 = gaussian_pulse(x[0], x[1], x[2], 0.2, pulse_center(1)).astype(np.float32)
+    u0 += 1e-3 * random_fields(mesh.K, mesh.Np, 9).astype(np.float32)   # exercise every field
+    return verts, tets, mesh, u0
+
+
+def test_full_size_rhs_sampled(env, full):
+    torch, dg = env
+    verts, tets, mesh, u0 = full
+    got = _gpu_rhs(torch, mesh, u0)
+    rng = np.random.default_rng(0)
+    seeds = np.concatenate([[0, 1, mesh.K - 1], rng.integers(0, mesh.K, 29)])
+    patch = _vertex_rings(tets, seeds, 1)
+    om = _oracle_on_patch(verts, tets, patch, 4)
+    want = oracle.rhs(om, u0[:, patch].astype(np.float64))
+    pos = np.searchsorted(patch, seeds)
+    assert rel(got[:, seeds], want[:, pos]) < RHS_TOL
+
+
+def test_full_size_step_sampled(env, full):
+    """One LSERK4 step (5 stages) at full size: the centre of a 5-ring patch
+    depends only on patch data, so the oracle on the patch is exact there."""
+    torch, dg = env
+    verts, tets, mesh, u0 = full
+    u = torch.from_numpy(u0).cuda()
+    res = torch.zeros_like(u)
+    e0 = mesh.energy(u)
+    mesh.step(u, res, mesh.dt_cfl, 1)
+    got = u.cpu().numpy()
+    e1 = mesh.energy(u)
+    assert e1 <= e0 * (1 + 1e-6)
+    seeds = np.array([mesh.K // 2 + 3, 6 * (24 * 24 * 12 + 24 * 5 + 7) + 2])
+    patch = _vertex_rings(tets, seeds, 5)
+    om = _oracle_on_patch(verts, tets, patch, 4)
+    ue, _ = oracle.lserk4_run(om, u0[:, patch].astype(np.float64), mesh.dt_cfl, 1)
+    pos = np.searchsorted(patch, seeds)
+    assert rel(got[:, seeds], ue[:, pos]) < RHS_TOL
