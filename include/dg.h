@@ -178,6 +178,25 @@ int dg_trace_enable(dg_mesh* mesh, int n);
  */
 int dg_trace_read(dg_mesh* mesh, double* ms, int32_t* kind, int64_t cap, int64_t* count);
 
+/*
+ * dg_energy without any allocation (the paper has no counterpart; this is a
+ * library service).  For callers that must not allocate device memory while
+ * they run -- e.g. a serving process whose HBM is owned by its own pool and
+ * budget, or a time loop that keeps cudaMalloc/cudaFree, which can
+ * synchronise the device, out of its steady state.
+ *   u      : device, [6][K][Np] FP32, read only.
+ *   energy : device, receives one double, 1/2 sum_k J_k sum_c u^T M u.
+ * The partial sums live in a fixed 512 KiB device array inside the library
+ * (held by every GPU that loads the library until exit), so K may not exceed
+ * 4 194 304 tetrahedra (DG_ERR_ARG otherwise).  The mesh must already be on
+ * the current device (one earlier dg_rhs, dg_step or dg_energy call on it,
+ * else DG_ERR_STATE), because uploading it would allocate.  The first call on
+ * a device looks up that device's address of the array; make that first call
+ * before any stream capture.  Asynchronous on `stream`; no host sync.  All
+ * calls share the array: calls that overlap on the GPU race on it.
+ */
+int dg_energy_noalloc(dg_mesh* mesh, const float* u, double* energy, void* stream);
+
 /* Free the mesh and every device buffer it owns.  NULL is ignored. */
 void dg_mesh_destroy(dg_mesh* mesh);
 

@@ -45,6 +45,13 @@ def _devptr(x):
     return C.c_void_p(x.data_ptr())
 
 
+def _devptr_any(x):
+    if isinstance(x, int):
+        return C.c_void_p(x)
+    assert x.is_cuda and x.is_contiguous()
+    return C.c_void_p(x.data_ptr())
+
+
 class Mesh:
     """A tetrahedral mesh with its DG operators (owns a dg_mesh*)."""
 
@@ -125,6 +132,12 @@ class Mesh:
         check(self._lib.dg_energy(self._h, _devptr(u), C.byref(out), _stream_handle(stream)),
               "dg_energy")
         return out.value
+
+    def energy_noalloc(self, u, out, stream=None):
+        """Energy into the device double `out` (a CUDA tensor or pointer); allocates nothing."""
+        check(self._lib.dg_energy_noalloc(self._h, _devptr(u), _devptr_any(out),
+                                          _stream_handle(stream)), "dg_energy_noalloc")
+        return out
 
     def step_host(self, u_host, res_host, dt: float, nsteps: int, with_energy=True, stream=None):
         """u_host, res_host: host float32 buffers (NumPy arrays or pinned CPU tensors)."""

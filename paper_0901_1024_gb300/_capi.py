@@ -30,6 +30,7 @@ SIGNATURES = {
     "dg_rhs": (C.c_int, [_vp, _vp, _vp, _vp]),
     "dg_step": (C.c_int, [_vp, _vp, _vp, C.c_double, C.c_int, _vp]),
     "dg_energy": (C.c_int, [_vp, _vp, _dp, _vp]),
+    "dg_energy_noalloc": (C.c_int, [_vp, _vp, _vp, _vp]),
     "dg_step_host": (C.c_int, [_vp, _vp, _vp, C.c_double, C.c_int, _dp, _vp]),
     "dg_last_launch_count": (C.c_int64, [_vp]),
     "dg_trace_enable": (C.c_int, [_vp, C.c_int]),

@@ -24,6 +24,10 @@ int check_mesh(const dg_mesh* m, bool need_order) {
 
 }  // namespace
 
+namespace dg {
+void set_error(const std::string& msg) { g_error = msg; }
+}  // namespace dg
+
 extern "C" {
 
 const char* dg_last_error(void) { return g_error.c_str(); }

@@ -368,6 +368,23 @@ static int energy_impl(dg_mesh* m, const float* u, double* out, cudaStream_t s,
   return DG_OK;
 }
 
+int device_resident(const dg_mesh* m, const float** M, const void** geo, int64_t* K, int* Np,
+                    std::string& err) {
+  int cur = -1;
+  DG_CUDA(cudaGetDevice(&cur), "cudaGetDevice");
+  const DeviceState* d = m->dev;
+  if (!d || d->N != m->N || d->device != cur) {
+    err = "mesh data is not on the current device yet (make one dg_rhs, dg_step or "
+          "dg_energy call on this device first)";
+    return DG_ERR_STATE;
+  }
+  *M = d->M;
+  *geo = d->geo;
+  *K = d->K;
+  *Np = d->Np;
+  return DG_OK;
+}
+
 int device_energy(dg_mesh* m, const float* u, double* out, void* stream, std::string& err) {
   int rc = ensure_device(m, err);
   if (rc) return rc;

@@ -71,6 +71,8 @@ namespace dg {
 // mesh.cpp
 int mesh_build(dg_mesh* m, const double* verts, int64_t nv, const int32_t* tets, int64_t K,
                std::string& err);
+// capi.cpp: sets the message returned by dg_last_error() on this thread
+void set_error(const std::string& msg);
 // device.cu (stream = cudaStream_t)
 int device_rhs(dg_mesh* m, const float* u, float* rhs, void* stream, std::string& err);
 int device_step(dg_mesh* m, float* u, float* res, double dt, int nsteps, void* stream,
@@ -79,6 +81,10 @@ int device_energy(dg_mesh* m, const float* u, double* out, void* stream, std::st
 int device_step_host(dg_mesh* m, float* u, float* res, double dt, int nsteps, double* energy,
                      void* stream, std::string& err);
 int device_trace_reset(dg_mesh* m, int reserve, std::string& err);
+// Device copies of M and the geometry records if the mesh is resident on the
+// current device at its current order (no allocation), else DG_ERR_STATE.
+int device_resident(const dg_mesh* m, const float** M, const void** geo, int64_t* K, int* Np,
+                    std::string& err);
 int device_trace_read(dg_mesh* m, double* ms, int32_t* kind, int64_t cap, int64_t* count,
                       std::string& err);
 }  // namespace dg
