@@ -85,7 +85,7 @@ def load_peaks():
 
 def kernel_source_digest():
     h = hashlib.sha256()
-    for n in ("stage_kernel.cuh", "device.h"):
+    for n in ("stage_kernel.cuh", "tc_stage.cuh", "tcgen05.cuh", "device.h"):
         with open(os.path.join(ROOT, "paper_0901_1024_gb300", "csrc", n), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
@@ -216,7 +216,8 @@ def run_ours(args):
 
     dof_stage = 6 * K * Np
     value = world * dof_stage * 5 * args.steps / (ms * 1e-3)
-    stage_ms = [t for t, k in zip(trace_ms, trace_kind) if k == 0]
+    stage_ms = [t for t, k in zip(trace_ms, trace_kind) if k in (0, 4)]
+    tc_path = any(k == 4 for k in trace_kind)
     avg_stage_s = statistics.fmean(stage_ms) * 1e-3
     peaks, peaks_src = load_peaks()
     algo_bytes = stage_bytes_per_elem(Np) * K
@@ -265,7 +266,8 @@ def run_ours(args):
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                          "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
-                         "kernel": f"stage_kernel<N={w['N']},RK>",
+                         "kernel": (f"tc_stage_kernel<N={w['N']},RK> (tcgen05, FP16x3 split)" if tc_path
+                                    else f"stage_kernel<N={w['N']},RK> (FP32 CUDA cores)"),
                          "algorithmic_bytes_per_launch": algo_bytes,
                          "avg_launch_ms": avg_stage_s * 1e3, "launches_timed": len(stage_ms),
                          "peak_source": f"{peaks_src} (MEASURED_PEAKS.json hbm_gbs)" if peaks_src == "measured"

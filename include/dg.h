@@ -112,6 +112,25 @@ int dg_get_geometry(const dg_mesh* mesh, double* metric, double* J, double* norm
 int dg_set_flux(dg_mesh* mesh, double alpha);
 
 /*
+ * Implementation of the RK-stage operator (the paper notes that each operator
+ * part may need its own strategy on the GPU, Section 4):
+ *   DG_STAGE_AUTO   tensor cores for N <= 4, FP32 CUDA cores above (default);
+ *   DG_STAGE_FP32   FP32 CUDA cores for every order;
+ *   DG_STAGE_TC     tensor cores (tcgen05): the volume and lifting contractions
+ *                   as one GEMM per tile with three FP16 products
+ *                   (A_hi B_hi + A_hi B_lo + A_lo B_hi, power-of-two row
+ *                   scaling, FP32 accumulation), FP32 elsewhere; orders 1..4.
+ *                   Its tiles move by bulk copies, so it also needs K*Np to
+ *                   be a multiple of 4 and 16-byte aligned field buffers;
+ *                   otherwise (and for N > 4) the call runs DG_STAGE_FP32.
+ * Host only.  Errors: DG_ERR_ARG for an unknown value.
+ */
+#define DG_STAGE_AUTO 0
+#define DG_STAGE_FP32 1
+#define DG_STAGE_TC   2
+int dg_set_stage_impl(dg_mesh* mesh, int impl);
+
+/*
  * One evaluation of the semi-discrete operator (Eq. semidiscrete-dg):
  * rhs = curl terms (local differentiation, Alg. 4) + LIFT * flux (flux
  * extraction, Alg. 2, and lifting, Alg. 1).
@@ -170,9 +189,10 @@ int dg_trace_enable(dg_mesh* mesh, int n);
  * Durations of the launches recorded since the last dg_trace_enable(), in
  * launch order:
  *   ms   : host, receives up to `cap` device durations in milliseconds;
- *   kind : host, receives the kernel of each launch (0 = fused RK stage,
- *          1 = right-hand side, 2 = energy partial sums, 3 = energy final sum);
- *          may be NULL;
+ *   kind : host, receives the kernel of each launch (0 = fused RK stage and
+ *          1 = right-hand side on CUDA cores, 4 = fused RK stage and 5 =
+ *          right-hand side on tensor cores, 2 = energy partial sums, 3 =
+ *          energy final sum); may be NULL;
  *   count: receives the number of recorded launches (may exceed cap).
  * Waits for the last recorded event.  Errors: DG_ERR_STATE if nothing was traced.
  */

@@ -91,6 +91,12 @@ class Mesh:
     def set_flux(self, alpha: float):
         check(self._lib.dg_set_flux(self._h, float(alpha)), "dg_set_flux")
 
+    STAGE_AUTO, STAGE_FP32, STAGE_TC = 0, 1, 2
+
+    def set_stage_impl(self, impl: int):
+        """0 = auto (tensor cores for N <= 4), 1 = FP32 CUDA cores, 2 = tensor cores."""
+        check(self._lib.dg_set_stage_impl(self._h, int(impl)), "dg_set_stage_impl")
+
     def nodes(self) -> np.ndarray:
         out = np.empty((3, self.K, self.Np), np.float64)
         check(self._lib.dg_nodes(self._h, _dptr(out, np.float64)), "dg_nodes")

@@ -154,6 +154,14 @@ int dg_set_flux(dg_mesh* m, double alpha) {
   return DG_OK;
 }
 
+int dg_set_stage_impl(dg_mesh* m, int impl) {
+  if (int rc = check_mesh(m, false)) return rc;
+  if (impl != DG_STAGE_AUTO && impl != DG_STAGE_FP32 && impl != DG_STAGE_TC)
+    return fail(DG_ERR_ARG, "unknown stage implementation");
+  m->stage_impl = impl;
+  return DG_OK;
+}
+
 int dg_rhs(dg_mesh* m, const float* u, float* rhs, void* stream) {
   if (int rc = check_mesh(m, true)) return rc;
   if (!u || !rhs) return fail(DG_ERR_ARG, "u or rhs is NULL");

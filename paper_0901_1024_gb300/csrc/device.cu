@@ -1,11 +1,14 @@
 // Device buffers of a mesh, kernel dispatch, the energy reduction and the
 // host-facing device operations behind the C ABI.
 #include <algorithm>
+#include <cstdint>
+#include <initializer_list>
 #include <cmath>
 #include <cstring>
 #include <string>
 #include <vector>
 
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include "device.h"
@@ -15,6 +18,19 @@ namespace dgdev {
 
 template <int N>
 cudaError_t launch_stage_n(bool rk, const StageArgs& a, int num_sms, cudaStream_t s);
+
+template <int N>
+cudaError_t launch_tc_stage_n(bool rk, const StageArgs& a, int num_sms, cudaStream_t s);
+
+cudaError_t launch_tc_stage(int N, bool rk, const StageArgs& a, int num_sms, cudaStream_t s) {
+  switch (N) {
+    case 1: return launch_tc_stage_n<1>(rk, a, num_sms, s);
+    case 2: return launch_tc_stage_n<2>(rk, a, num_sms, s);
+    case 3: return launch_tc_stage_n<3>(rk, a, num_sms, s);
+    case 4: return launch_tc_stage_n<4>(rk, a, num_sms, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
 
 cudaError_t launch_stage(int N, bool rk, const StageArgs& a, int num_sms, cudaStream_t s) {
   switch (N) {
@@ -107,6 +123,9 @@ struct DeviceState {
   double* partials = nullptr;   // energy partials, one per block
   double* result = nullptr;
   int egrid = 0;
+  void* tcB = nullptr;          // tensor-core B pieces (orders <= kTcMaxOrder)
+  float tc_inv_bscale = 1.f;
+  int* status = nullptr;        // pipeline status word (0 = ok)
   // per-launch tracing: event pair 2i, 2i+1 around launch i
   std::vector<cudaEvent_t> ev;
   std::vector<int> kind;
@@ -121,6 +140,7 @@ void destroy_device_state(DeviceState* d) {
   cudaFree(d->geo); cudaFree(d->D4); cudaFree(d->LIFT4); cudaFree(d->M);
   cudaFree(d->fmask); cudaFree(d->perm); cudaFree(d->u_work); cudaFree(d->h_u);
   cudaFree(d->h_res); cudaFree(d->partials); cudaFree(d->result);
+  cudaFree(d->tcB); cudaFree(d->status);
   for (cudaEvent_t e : d->ev) cudaEventDestroy(e);
   if (cur >= 0) cudaSetDevice(cur);
   delete d;
@@ -267,15 +287,65 @@ int ensure_device(dg_mesh* m, std::string& err) {
   if ((rc = upload(&d->fmask, fm, err))) return rc;
   std::vector<unsigned char> pm(m->ops.perm.begin(), m->ops.perm.end());
   if ((rc = upload(&d->perm, pm, err))) return rc;
+  if (d->N <= dgdev::kTcMaxOrder) {
+    // B = [Dr Ds Dt LIFT] (Np x KT, zero padded), scaled by 2^p, split into FP16
+    // hi + lo, stored in the canonical K-major core-matrix layout.
+    const int KB = (Np + 1) & ~1, KT = (3 * KB + NF + 15) & ~15, NN = (Np + 15) & ~15;
+    std::vector<double> B(static_cast<size_t>(NN) * KT, 0.0);
+    double mx = 0.0;
+    for (int n = 0; n < Np; ++n)
+      for (int k = 0; k < KT; ++k) {
+        double v = 0.0;
+        if (k < 3 * KB) {
+          const int mu = k / KB, j = k % KB;
+          const std::vector<double>& Dm = mu == 0 ? m->ops.Dr : mu == 1 ? m->ops.Ds : m->ops.Dt;
+          if (j < Np) v = Dm[n * Np + j];
+        } else if (k < 3 * KB + NF) {
+          v = m->ops.LIFT[n * NF + (k - 3 * KB)];
+        }
+        B[n * KT + k] = v;
+        mx = std::max(mx, std::fabs(v));
+      }
+    const double sB = std::ldexp(1.0, static_cast<int>(std::floor(std::log2(16384.0 / mx))));
+    d->tc_inv_bscale = static_cast<float>(1.0 / sB);
+    const size_t piece = static_cast<size_t>(NN) * KT;
+    std::vector<__half> P(2 * piece);
+    for (int n = 0; n < NN; ++n)
+      for (int k = 0; k < KT; ++k) {
+        const float x = static_cast<float>(B[n * KT + k] * sB);
+        const __half hi = __float2half_rn(x);
+        const __half lo = __float2half_rn(x - __half2float(hi));
+        const size_t off = ((k / 8) * (NN / 8) + n / 8) * 64 + (n % 8) * 8 + (k % 8);
+        P[off] = hi;
+        P[piece + off] = lo;
+      }
+    if ((rc = upload(reinterpret_cast<__half**>(&d->tcB), P, err))) return rc;
+  }
+  DG_CUDA(cudaMalloc(&d->status, sizeof(int)), "cudaMalloc");
+  DG_CUDA(cudaMemset(d->status, 0, sizeof(int)), "cudaMemset");
   d->egrid = dgdev::energy_grid(d->num_sms);
   DG_CUDA(cudaMalloc(&d->partials, sizeof(double) * d->egrid), "cudaMalloc");
   DG_CUDA(cudaMalloc(&d->result, sizeof(double)), "cudaMalloc");
   return DG_OK;
 }
 
-static dgdev::StageArgs stage_args(dg_mesh* m) {
+// Tensor cores for orders <= kTcMaxOrder unless the CUDA-core path is forced.
+// The tensor-core kernel moves whole tiles with bulk copies, which need every
+// field chunk 16-byte aligned: (K * Np) % 4 == 0 and 16-byte aligned buffers.
+static bool use_tc(const dg_mesh* m, std::initializer_list<const void*> bufs) {
+  if (m->stage_impl == DG_STAGE_FP32 || m->N > dgdev::kTcMaxOrder) return false;
+  if ((m->K * m->ops.Np) % 4 != 0) return false;
+  for (const void* p : bufs)
+    if (reinterpret_cast<uintptr_t>(p) % 16 != 0) return false;
+  return true;
+}
+
+static dgdev::StageArgs stage_args(dg_mesh* m, bool tc) {
   DeviceState* d = m->dev;
   dgdev::StageArgs a{};
+  a.tcB = d->tcB;
+  a.tc_inv_bscale = d->tc_inv_bscale;
+  a.status = d->status;
   a.geo = d->geo;
   a.D4 = d->D4;
   a.LIFT4 = d->LIFT4;
@@ -283,7 +353,7 @@ static dgdev::StageArgs stage_args(dg_mesh* m) {
   a.perm = d->perm;
   a.K = static_cast<int>(d->K);
   a.alpha = static_cast<float>(m->alpha);
-  const int E = dgdev::stage_tile_elems(d->N);
+  const int E = tc ? dgdev::kTcTileElems : dgdev::stage_tile_elems(d->N);
   a.num_tiles = static_cast<int>((d->K + E - 1) / E);
   return a;
 }
@@ -292,11 +362,14 @@ int device_rhs(dg_mesh* m, const float* u, float* rhs, void* stream, std::string
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   int rc = ensure_device(m, err);
   if (rc) return rc;
-  dgdev::StageArgs a = stage_args(m);
+  const bool tc = use_tc(m, {u, rhs});
+  dgdev::StageArgs a = stage_args(m, tc);
   a.u_in = u;
   a.rhs = rhs;
-  DG_CUDA(traced(m, s, 1, [&] { return dgdev::launch_stage(m->N, false, a, m->dev->num_sms, s); }),
-          "stage kernel launch");
+  DG_CUDA(traced(m, s, tc ? 5 : 1, [&] {
+            return tc ? dgdev::launch_tc_stage(m->N, false, a, m->dev->num_sms, s)
+                             : dgdev::launch_stage(m->N, false, a, m->dev->num_sms, s);
+          }), "stage kernel launch");
   m->last_launches = 1;
   return DG_OK;
 }
@@ -317,7 +390,8 @@ static int step_impl(dg_mesh* m, float* u, float* res, double dt, int nsteps, cu
   DeviceState* d = m->dev;
   const size_t n = static_cast<size_t>(6) * d->K * d->Np;
   if (!d->u_work) DG_CUDA(cudaMalloc(&d->u_work, n * sizeof(float)), "cudaMalloc work state");
-  dgdev::StageArgs a = stage_args(m);
+  const bool tc = use_tc(m, {u, res, d->u_work});
+  dgdev::StageArgs a = stage_args(m, tc);
   a.res = res;
   a.dt = static_cast<float>(dt);
   const float* src = u;
@@ -329,8 +403,10 @@ static int step_impl(dg_mesh* m, float* u, float* res, double dt, int nsteps, cu
       a.u_out = dst;
       a.a = static_cast<float>(kRkA[i]);
       a.b = static_cast<float>(kRkB[i]);
-      DG_CUDA(traced(m, s, 0, [&] { return dgdev::launch_stage(m->N, true, a, d->num_sms, s); }),
-              "stage kernel launch");
+      DG_CUDA(traced(m, s, tc ? 4 : 0, [&] {
+                return tc ? dgdev::launch_tc_stage(m->N, true, a, d->num_sms, s)
+                          : dgdev::launch_stage(m->N, true, a, d->num_sms, s);
+              }), "stage kernel launch");
       ++launches;
       float* nsrc = dst;
       dst = const_cast<float*>(src);
@@ -350,6 +426,18 @@ int device_step(dg_mesh* m, float* u, float* res, double dt, int nsteps, void* s
   return step_impl(m, u, res, dt, nsteps, static_cast<cudaStream_t>(stream), err);
 }
 
+// Reads (and clears) the pipeline status word; only after a synchronisation.
+static int check_status(dg_mesh* m, std::string& err) {
+  int st = 0;
+  DG_CUDA(cudaMemcpy(&st, m->dev->status, sizeof(int), cudaMemcpyDeviceToHost), "cudaMemcpy D2H");
+  if (st != 0) {
+    DG_CUDA(cudaMemset(m->dev->status, 0, sizeof(int)), "cudaMemset");
+    err = "tensor-core stage: an MMA completion wait timed out (results invalid)";
+    return DG_ERR_CUDA;
+  }
+  return DG_OK;
+}
+
 static int energy_impl(dg_mesh* m, const float* u, double* out, cudaStream_t s,
                        std::string& err) {
   DeviceState* d = m->dev;
@@ -362,6 +450,7 @@ static int energy_impl(dg_mesh* m, const float* u, double* out, cudaStream_t s,
   DG_CUDA(cudaMemcpyAsync(&h, d->result, sizeof(double), cudaMemcpyDeviceToHost, s),
           "cudaMemcpyAsync D2H");
   DG_CUDA(cudaStreamSynchronize(s), "cudaStreamSynchronize");
+  if (int rc = check_status(m, err)) return rc;
   *out = h;
   m->last_launches = 2;
   if (!std::isfinite(h)) { err = "energy is not finite (unstable run)"; return DG_ERR_UNSTABLE; }
@@ -411,6 +500,7 @@ int device_step_host(dg_mesh* m, float* u, float* res, double dt, int nsteps, do
     launches += 2;
   } else {
     DG_CUDA(cudaStreamSynchronize(s), "cudaStreamSynchronize");
+    if ((rc = check_status(m, err))) return rc;
   }
   m->last_launches = launches;
   return DG_OK;

@@ -36,11 +36,25 @@ struct StageArgs {
   int K;
   int num_tiles;
   float a, b, dt, alpha;
+  // tensor-core path only
+  const void* tcB;          // FP16 [Dr Ds Dt LIFT] hi/lo pieces, canonical K-major layout
+  float tc_inv_bscale;      // 1 / (power-of-two scale applied to B)
+  int* status;              // set to 1 if an MMA completion wait timed out
 };
+
+// Tensor-core stage: elements per tile (6 * 20 = 120 of the 128 MMA rows).
+constexpr int kTcTileElems = 20;
+constexpr int kTcMaxOrder = 4;
+// Bytes of the prepared B buffer for order N (two FP16 pieces of NN x KT).
+__host__ __device__ constexpr int tc_b_bytes(int N) {
+  return 2 * 2 * ((((N + 1) * (N + 2) * (N + 3) / 6) + 15) & ~15) *
+         ((3 * ((((N + 1) * (N + 2) * (N + 3) / 6) + 1) & ~1) + 4 * ((N + 1) * (N + 2) / 2) + 15) & ~15);
+}
 
 // Launches one RK stage (rk = true: res <- a res + dt rhs, u_out <- u_in + b res)
 // or one bare right-hand-side evaluation (rk = false: rhs <- rhs(u_in)).
 cudaError_t launch_stage(int N, bool rk, const StageArgs& a, int num_sms, cudaStream_t s);
+cudaError_t launch_tc_stage(int N, bool rk, const StageArgs& a, int num_sms, cudaStream_t s);
 
 struct EnergyArgs {
   const float* u;      // [6][K][Np]

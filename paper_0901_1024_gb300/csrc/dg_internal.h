@@ -65,6 +65,7 @@ struct dg_mesh {
   dgdev::DeviceState* dev = nullptr;
   int64_t last_launches = 0;
   bool trace = false;
+  int stage_impl = DG_STAGE_AUTO;
 };
 
 namespace dg {

@@ -1,0 +1,3 @@
+// Tensor-core stage kernel instantiation for order N=1.
+#include "tc_stage.cuh"
+DG_INSTANTIATE_TC_STAGE(1)

@@ -1,0 +1,3 @@
+// Tensor-core stage kernel instantiation for order N=4.
+#include "tc_stage.cuh"
+DG_INSTANTIATE_TC_STAGE(4)

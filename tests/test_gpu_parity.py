@@ -34,9 +34,14 @@ def _setup(dg, verts, tets, N):
     return dg.Mesh(verts, tets, N), oracle.build_mesh(verts, tets, N)
 
 
-def _gpu_rhs(torch, mesh, u32, alpha=None):
+FP32, TC = 1, 2     # stage implementations (dg_set_stage_impl)
+
+
+def _gpu_rhs(torch, mesh, u32, alpha=None, impl=None):
     if alpha is not None:
         mesh.set_flux(alpha)
+    if impl is not None:
+        mesh.set_stage_impl(impl)
     u = torch.from_numpy(u32).cuda()
     out = torch.full_like(u, float("nan"))
     mesh.rhs(u, out)
@@ -55,6 +60,56 @@ def test_rhs_parity_all_orders(env, N):
     want = oracle.rhs(om, u32.astype(np.float64))
     assert np.isfinite(got).all()
     assert rel(got, want) < RHS_TOL
+
+
+def _stage_kinds(mesh):
+    _, kinds = mesh.trace_read()
+    return set(int(k) for k in kinds)
+
+
+@pytest.mark.parametrize("impl", [FP32, TC])
+@pytest.mark.parametrize("N", [1, 2, 3, 4])
+def test_rhs_parity_both_implementations(env, N, impl):
+    """Orders 1..4 run on the tensor cores by default; both paths must match.
+    K = 384 = 19 full tiles of 20 + a ragged tile of 4."""
+    torch, dg = env
+    verts, tets = kuhn_box_mesh(4, 0.15, 20 + N)
+    mesh, om = _setup(dg, verts, tets, N)
+    u32 = random_fields(om.K, om.Np, 30 + N).astype(np.float32)
+    u32[:, ::7] *= 1e-6                                  # rows with very different scales
+    mesh.trace_enable(4)
+    got = _gpu_rhs(torch, mesh, u32, impl=impl)
+    assert _stage_kinds(mesh) == ({5} if impl == TC else {1})
+    assert rel(got, oracle.rhs(om, u32.astype(np.float64))) < RHS_TOL
+
+
+def test_tc_falls_back_when_tiles_are_not_aligned(env):
+    """K * Np not a multiple of 4 (K = 162, N = 4): the FP32 kernel runs."""
+    torch, dg = env
+    verts, tets = kuhn_box_mesh(3, 0.15, 2)
+    mesh, om = _setup(dg, verts, tets, 4)
+    u32 = random_fields(om.K, om.Np, 8).astype(np.float32)
+    mesh.trace_enable(4)
+    got = _gpu_rhs(torch, mesh, u32, impl=TC)
+    assert _stage_kinds(mesh) == {1}
+    assert rel(got, oracle.rhs(om, u32.astype(np.float64))) < RHS_TOL
+
+
+@pytest.mark.parametrize("impl", [FP32, TC])
+def test_step_parity_both_implementations(env, impl):
+    torch, dg = env
+    verts, tets = kuhn_box_mesh(2, 0.1, 0)
+    mesh, om = _setup(dg, verts, tets, 4)
+    mesh.set_stage_impl(impl)
+    u0 = cavity_mode(om.x, om.y, om.z, 0.0).astype(np.float32)
+    u = torch.from_numpy(u0).cuda()
+    res = torch.zeros_like(u)
+    mesh.trace_enable(500)
+    mesh.step(u, res, mesh.dt_cfl, 100)
+    torch.cuda.synchronize()
+    assert _stage_kinds(mesh) == ({4} if impl == TC else {0})
+    ue, _ = oracle.lserk4_run(om, u0.astype(np.float64), mesh.dt_cfl, 100)
+    assert rel(u.cpu().numpy(), ue) < STEP_TOL
 
 
 @pytest.mark.parametrize("N", [2, 4, 6])
@@ -208,6 +263,20 @@ def test_full_size_rhs_sampled(env, full):
     want = oracle.rhs(om, u0[:, patch].astype(np.float64))
     pos = np.searchsorted(patch, seeds)
     assert rel(got[:, seeds], want[:, pos]) < RHS_TOL
+
+
+def test_full_size_tc_matches_fp32_everywhere(env, full):
+    """Every value at full size: tensor-core and FP32 paths agree (each is
+    within 1e-5 of the oracle, so they agree within 2e-5)."""
+    torch, dg = env
+    verts, tets, mesh, u0 = full
+    mesh.trace_enable(4)
+    a = _gpu_rhs(torch, mesh, u0, impl=TC)
+    assert _stage_kinds(mesh) == {5}
+    b = _gpu_rhs(torch, mesh, u0, impl=FP32)
+    mesh.set_stage_impl(0)
+    assert np.isfinite(a).all()
+    assert rel(a, b.astype(np.float64)) < 2 * RHS_TOL
 
 
 def test_full_size_step_sampled(env, full):
