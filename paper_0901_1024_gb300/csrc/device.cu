@@ -124,6 +124,8 @@ struct DeviceState {
   double* result = nullptr;
   int egrid = 0;
   void* tcB = nullptr;          // tensor-core B pieces (orders <= kTcMaxOrder)
+  float* tcgeo = nullptr;       // word-major geometry for the tensor-core stage
+  int tc_geo_stride = 0;
   float tc_inv_bscale = 1.f;
   int* status = nullptr;        // pipeline status word (0 = ok)
   // per-launch tracing: event pair 2i, 2i+1 around launch i
@@ -140,7 +142,7 @@ void destroy_device_state(DeviceState* d) {
   cudaFree(d->geo); cudaFree(d->D4); cudaFree(d->LIFT4); cudaFree(d->M);
   cudaFree(d->fmask); cudaFree(d->perm); cudaFree(d->u_work); cudaFree(d->h_u);
   cudaFree(d->h_res); cudaFree(d->partials); cudaFree(d->result);
-  cudaFree(d->tcB); cudaFree(d->status);
+  cudaFree(d->tcB); cudaFree(d->tcgeo); cudaFree(d->status);
   for (cudaEvent_t e : d->ev) cudaEventDestroy(e);
   if (cur >= 0) cudaSetDevice(cur);
   delete d;
@@ -320,6 +322,19 @@ int ensure_device(dg_mesh* m, std::string& err) {
         P[piece + off] = lo;
       }
     if ((rc = upload(reinterpret_cast<__half**>(&d->tcB), P, err))) return rc;
+    // tiled word-major geometry, one contiguous [kTcGeoWords][E] block per tile:
+    // record words {0..8 metric, 10 codes, 12..27 faces, 28..31 neighbours} ->
+    // words {0..8, 9, 10..25, 26..29}
+    constexpr int E = dgdev::kTcTileElems;
+    const int64_t ntiles = (K + E - 1) / E;
+    d->tc_geo_stride = dgdev::kTcGeoWords * E;
+    std::vector<float> tg(static_cast<size_t>(ntiles) * dgdev::kTcGeoWords * E, 0.f);
+    for (int64_t k = 0; k < K; ++k)
+      for (int w = 0; w < dgdev::kTcGeoWords; ++w) {
+        const int src = w < 9 ? w : (w == 9 ? 10 : w + 2);
+        tg[((k / E) * dgdev::kTcGeoWords + w) * E + k % E] = geo[k * dgdev::kGeoWords + src];
+      }
+    if ((rc = upload(&d->tcgeo, tg, err))) return rc;
   }
   DG_CUDA(cudaMalloc(&d->status, sizeof(int)), "cudaMalloc");
   DG_CUDA(cudaMemset(d->status, 0, sizeof(int)), "cudaMemset");
@@ -344,6 +359,8 @@ static dgdev::StageArgs stage_args(dg_mesh* m, bool tc) {
   DeviceState* d = m->dev;
   dgdev::StageArgs a{};
   a.tcB = d->tcB;
+  a.tcgeo = d->tcgeo;
+  a.tc_geo_stride = d->tc_geo_stride;
   a.tc_inv_bscale = d->tc_inv_bscale;
   a.status = d->status;
   a.geo = d->geo;

@@ -37,6 +37,8 @@ struct StageArgs {
   int num_tiles;
   float a, b, dt, alpha;
   // tensor-core path only
+  const float* tcgeo;       // per tile: [kTcGeoWords][kTcTileElems] word-major geometry
+  int tc_geo_stride;        // floats per tile block
   const void* tcB;          // FP16 [Dr Ds Dt LIFT] hi/lo pieces, canonical K-major layout
   float tc_inv_bscale;      // 1 / (power-of-two scale applied to B)
   int* status;              // set to 1 if an MMA completion wait timed out
@@ -44,6 +46,10 @@ struct StageArgs {
 
 // Tensor-core stage: elements per tile (6 * 20 = 120 of the 128 MMA rows).
 constexpr int kTcTileElems = 20;
+// Word-major geometry for the tensor-core stage: words 0..8 metric, 9 packed
+// neighbour codes, 10 + 4f .. 13 + 4f normal and Fscale of face f, 26 + f
+// neighbour element of face f.
+constexpr int kTcGeoWords = 30;
 constexpr int kTcMaxOrder = 4;
 // Bytes of the prepared B buffer for order N (two FP16 pieces of NN x KT).
 __host__ __device__ constexpr int tc_b_bytes(int N) {

@@ -65,7 +65,7 @@ template <int N> struct TcDims {
   static constexpr int ITEMS = (E * NF + THREADS - 1) / THREADS;   // flux items per thread
   // shared memory (bytes)
   static constexpr int U_FLOATS = 6 * E * Np;         // one tile of one state array
-  static constexpr int G_FLOATS = E * kGeoWords;
+  static constexpr int G_FLOATS = E * kTcGeoWords;   // word-major: [w][E]
   static constexpr int F_FLOATS = ROWS * FSTR;
   static constexpr int B_BYTES = NN * KT * 2;         // one FP16 piece
   static constexpr int TAB_BYTES = (4 * Nfp + 96 * Nfp + 15) & ~15;
@@ -77,11 +77,15 @@ template <int N> struct TcDims {
   static constexpr int OFF_MAX = OFF_F + F_FLOATS * 4;   // [4][128] float
   static constexpr int OFF_SC = OFF_MAX + 4 * 128 * 4;   // [2][128] float
   static constexpr int OFF_TAB = OFF_SC + 2 * 128 * 4;
-  static constexpr int OFF_GH = OFF_TAB + TAB_BYTES;     // [E*NF][6] gathered neighbour values
-  static constexpr int SMEM = OFF_GH + E * NF * 6 * 4;
+  static constexpr int GH_STR = 7;                       // ghost record stride (odd)
+  static constexpr int OFF_GH = OFF_TAB + TAB_BYTES;     // [E*NF][GH_STR] neighbour values
+  static constexpr int OFF_IT = OFF_GH + E * NF * GH_STR * 4;   // [E*NF] packed item words
+  static constexpr int OFF_DESC = OFF_IT + E * NF * 4;   // [3][KSTEPS] B descriptors
+  static constexpr int SMEM = OFF_DESC + ((3 * KSTEPS * 8 + 15) & ~15);
   static_assert((U_FLOATS * 4) % 16 == 0 && (E * Np * 4) % 16 == 0, "bulk-copy alignment");
   static_assert(OFF_U % 16 == 0 && OFF_R % 16 == 0 && OFF_G % 16 == 0 && OFF_F % 16 == 0 &&
-                OFF_TAB % 16 == 0, "alignment");
+                OFF_TAB % 16 == 0 && OFF_IT % 16 == 0 && OFF_DESC % 16 == 0, "alignment");
+  static_assert((E * 4) % 16 == 0, "geometry word chunks must be 16-byte multiples");
   static_assert(SMEM <= 220 * 1024, "shared memory budget");
 };
 
@@ -142,20 +146,21 @@ __device__ __forceinline__ float row_scale(float rmax) {
   return ex == 0 ? 1.f : __uint_as_float(uint32_t(max(1, min(254, 268 - ex))) << 23);
 }
 
-// One thread: bulk copies of tile `tile` (fields, RK register, geometry) into
-// ring slot buffers, completing on `bar`.
+// One thread: bulk copies of tile `tile` (fields, RK register, geometry block)
+// into ring slot buffers, completing on `bar`.
 template <int N, bool RK>
 __device__ __forceinline__ void tc_issue_loads(const StageArgs& A, int tile, float* su, float* sr,
                                                float* sg, uint64_t* bar) {
   using D = TcDims<N>;
   const int K = A.K, k0 = tile * D::E, Ev = min(D::E, K - k0);
   const uint32_t fb = uint32_t(Ev) * D::Np * 4;
-  tc::mbar_expect_tx(bar, (RK ? 12u : 6u) * fb + uint32_t(Ev) * kGeoWords * 4);
+  constexpr uint32_t gb = kTcGeoWords * D::E * 4;      // one tiled geometry block
+  tc::mbar_expect_tx(bar, (RK ? 12u : 6u) * fb + gb);
   for (int c = 0; c < 6; ++c) {
     tc::bulk_g2s(su + c * D::E * D::Np, A.u_in + (size_t(c) * K + k0) * D::Np, fb, bar);
     if (RK) tc::bulk_g2s(sr + c * D::E * D::Np, A.res + (size_t(c) * K + k0) * D::Np, fb, bar);
   }
-  tc::bulk_g2s(sg, A.geo + size_t(k0) * (kGeoWords / 4), uint32_t(Ev) * kGeoWords * 4, bar);
+  tc::bulk_g2s(sg, A.tcgeo + size_t(tile) * A.tc_geo_stride, gb, bar);
 }
 
 template <int N, bool RK>
@@ -180,6 +185,7 @@ __global__ void __launch_bounds__(TcDims<N>::THREADS, 1) tc_stage_kernel(const S
   float* sMax = reinterpret_cast<float*>(smem + D::OFF_MAX);
   float* sScale = reinterpret_cast<float*>(smem + D::OFF_SC);
   float* sGhost = reinterpret_cast<float*>(smem + D::OFF_GH);
+  uint32_t* sItem = reinterpret_cast<uint32_t*>(smem + D::OFF_IT);
   unsigned char* sFmask = smem + D::OFF_TAB;
   unsigned char* sPerm = sFmask + 4 * Nfp;
 
@@ -190,6 +196,13 @@ __global__ void __launch_bounds__(TcDims<N>::THREADS, 1) tc_stage_kernel(const S
     for (int i = tid; i < 2 * D::B_BYTES / 16; i += D::THREADS) dst[i] = __ldg(src + i);
     for (int i = tid; i < 4 * Nfp; i += D::THREADS) sFmask[i] = __ldg(A.fmask + i);
     for (int i = tid; i < 96 * Nfp; i += D::THREADS) sPerm[i] = __ldg(A.perm + i);
+    // flux item idx -> e | m << 5 | f << 13 | j << 15 | idM << 21, face nodes of
+    // one element consecutive: a warp's gathers hit the same neighbour blocks
+    for (int idx = tid; idx < E * NF; idx += D::THREADS) {
+      const int m = idx % NF, e = idx / NF, f = m / Nfp, j = m - f * Nfp;
+      sItem[idx] = uint32_t(e) | uint32_t(m) << 5 | uint32_t(f) << 13 | uint32_t(j) << 15 |
+                   uint32_t(__ldg(A.fmask + f * Nfp + j)) << 21;
+    }
   }
   tc::fence_proxy_async_smem();
   if (warp == 0) tc::tmem_alloc(&s_tmem, 512);
@@ -202,13 +215,12 @@ __global__ void __launch_bounds__(TcDims<N>::THREADS, 1) tc_stage_kernel(const S
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
-  if (tid == 0) tc_issue_loads<N, RK>(A, blockIdx.x, sU, sR, sG, &s_load_bar[0]);
+  if (warp == 0 && tc::elect_one()) tc_issue_loads<N, RK>(A, blockIdx.x, sU, sR, sG, &s_load_bar[0]);
   const uint32_t tbase = s_tmem;
   const uint32_t lane_off = uint32_t(quarter * 32) << 16;
   const int row = quarter * 32 + lane;               // A / D row owned by this thread
   const int rc = row / E, re = row - (row / E) * E;  // field, element of that row
   constexpr uint32_t IDESC = tc::idesc_f16(128, D::NN);
-  constexpr uint32_t LBO = (D::NN / 8) * 128, SBO = 128;
   constexpr uint32_t WAIT_LIMIT = 1u << 26;
 
   for (int t = 0; t <= ntiles_cta; ++t) {
@@ -222,41 +234,39 @@ __global__ void __launch_bounds__(TcDims<N>::THREADS, 1) tc_stage_kernel(const S
       if (!tc::mbar_wait_bounded(&s_load_bar[slot], (t / 3) & 1, WAIT_LIMIT) && A.status)
         atomicExch(A.status, 1);
       __syncthreads();                                  // previous epilogue done everywhere
-      if (tid == 0 && t + 1 < ntiles_cta) {
-        const int ns = (t + 1) % 3;
-        tc::bulk_wait_read_all();                       // stores of tile t-2 left that slot
-        tc::fence_proxy_async_smem();
-        tc_issue_loads<N, RK>(A, tile + gridDim.x, sU + ns * D::U_FLOATS, sR + ns * D::U_FLOATS,
-                              sG + ns * D::G_FLOATS, &s_load_bar[ns]);
-      }
 
       // ---- flux, step 1: request neighbour values that leave the tile -----
+      uint32_t item[D::ITEMS];
       int kind[D::ITEMS];        // 0 skip, 1 wall, 2 in tile (offset in ofs), 3 gathered
       int ofs[D::ITEMS];
 #pragma unroll
       for (int q = 0; q < D::ITEMS; ++q) {
         const int idx = tid + q * D::THREADS;
-        const int e = idx % E, m = idx / E;
         kind[q] = 0;
         ofs[q] = 0;
-        if (idx < E * NF && e < Ev) {
-          const float* ge = sg + e * kGeoWords;
-          const int f = m / Nfp, j = m - f * Nfp;
-          const unsigned code = (__float_as_uint(ge[10]) >> (8 * f)) & 0xffu;
-          if (code == 0u) {
-            kind[q] = 1;
-          } else {
-            const int k2 = __float_as_int(ge[28 + f]);
-            const int i2 = sPerm[(f * 24 + int(code) - 1) * Nfp + j];
-            const int e2 = k2 - k0;
-            if (e2 >= 0 && e2 < Ev) {
-              kind[q] = 2;
-              ofs[q] = e2 * Np + i2;
+        item[q] = 0;
+        if (idx < E * NF) {
+          const uint32_t it = sItem[idx];
+          item[q] = it;
+          const int e = it & 31, f = (it >> 13) & 3, j = (it >> 15) & 63;
+          if (e < Ev) {
+            const unsigned code = (__float_as_uint(sg[9 * E + e]) >> (8 * f)) & 0xffu;
+            if (code == 0u) {
+              kind[q] = 1;
             } else {
-              kind[q] = 3;
+              const int k2 = __float_as_int(sg[(26 + f) * E + e]);
+              const int i2 = sPerm[(f * 24 + int(code) - 1) * Nfp + j];
+              const int e2 = k2 - k0;
+              if (e2 >= 0 && e2 < Ev) {
+                kind[q] = 2;
+                ofs[q] = e2 * Np + i2;
+              } else {
+                kind[q] = 3;
+                const float* src = A.u_in + size_t(k2) * Np + i2;
 #pragma unroll
-              for (int c = 0; c < 6; ++c)
-                tc::cp_async4(sGhost + idx * 6 + c, A.u_in + (size_t(c) * K + k2) * Np + i2);
+                for (int c = 0; c < 6; ++c)
+                  tc::cp_async4(sGhost + idx * D::GH_STR + c, src + size_t(c) * K * Np);
+              }
             }
           }
         }
@@ -268,14 +278,13 @@ __global__ void __launch_bounds__(TcDims<N>::THREADS, 1) tc_stage_kernel(const S
       float mx = 0.f;
       if (part < 3) {
         if (live) {
-          const float* ge = sg + re * kGeoWords;
           // curl component o of the other field kind: rhs_E = curl H, rhs_H = -curl E
           const int o = rc % 3;
           const int fa = rc < 3 ? 3 + (o + 2) % 3 : (o + 2) % 3;
           const int fb = rc < 3 ? 3 + (o + 1) % 3 : (o + 1) % 3;
           const float sgn = rc < 3 ? 1.f : -1.f;
-          const float ca = sgn * ge[3 * part + (o + 1) % 3];
-          const float cb = -sgn * ge[3 * part + (o + 2) % 3];
+          const float ca = sgn * sg[(3 * part + (o + 1) % 3) * E + re];
+          const float cb = -sgn * sg[(3 * part + (o + 2) % 3) * E + re];
           const float* ua = su + (fa * E + re) * Np;
           const float* ub = su + (fb * E + re) * Np;
 #pragma unroll
@@ -295,10 +304,8 @@ __global__ void __launch_bounds__(TcDims<N>::THREADS, 1) tc_stage_kernel(const S
       for (int q = 0; q < D::ITEMS; ++q) {
         if (kind[q] == 0) continue;
         const int idx = tid + q * D::THREADS;
-        const int e = idx % E, m = idx / E;
-        const float* ge = sg + e * kGeoWords;
-        const int f = m / Nfp, j = m - f * Nfp;
-        const int idM = sFmask[f * Nfp + j];
+        const uint32_t it = item[q];
+        const int e = it & 31, m = (it >> 5) & 255, f = (it >> 13) & 3, idM = it >> 21;
         float uM[6], up[6];
 #pragma unroll
         for (int c = 0; c < 6; ++c) uM[c] = su[(c * E + e) * Np + idM];
@@ -310,10 +317,11 @@ __global__ void __launch_bounds__(TcDims<N>::THREADS, 1) tc_stage_kernel(const S
           for (int c = 0; c < 6; ++c) up[c] = su[c * E * Np + ofs[q]];
         } else {
 #pragma unroll
-          for (int c = 0; c < 6; ++c) up[c] = sGhost[idx * 6 + c];
+          for (int c = 0; c < 6; ++c) up[c] = sGhost[idx * D::GH_STR + c];
         }
-        const float nx = ge[12 + 4 * f], ny = ge[13 + 4 * f], nz = ge[14 + 4 * f];
-        const float sc = 0.5f * ge[15 + 4 * f];
+        const float nx = sg[(10 + 4 * f) * E + e], ny = sg[(11 + 4 * f) * E + e];
+        const float nz = sg[(12 + 4 * f) * E + e];
+        const float sc = 0.5f * sg[(13 + 4 * f) * E + e];
         const float dEx = uM[0] - up[0], dEy = uM[1] - up[1], dEz = uM[2] - up[2];
         const float dHx = uM[3] - up[3], dHy = uM[4] - up[4], dHz = uM[5] - up[5];
         const float ndE = nx * dEx + ny * dEy + nz * dEz;
@@ -367,22 +375,31 @@ __global__ void __launch_bounds__(TcDims<N>::THREADS, 1) tc_stage_kernel(const S
       tc::fence_before_sync();
       __syncthreads();
 
-      // ---- issue the MMAs of tile t ---------------------------------------
-      if (tid == 0) {
+      // ---- warp 0: issue the MMAs of tile t, then the loads of tile t+1 ---
+      if (warp == 0) {
         tc::fence_after_sync();
         const uint32_t d_acc = tbase + buf * D::BUF_COLS + 2 * D::ACOLS;
         const uint32_t a_base = tbase + buf * D::BUF_COLS;
-        const uint32_t b0 = tc::smem_u32(smem + D::OFF_B);
-        const uint32_t a_off[3] = {0u, 0u, uint32_t(D::ACOLS)};       // hi, hi, lo
-        const uint32_t b_off[3] = {0u, uint32_t(D::B_BYTES), 0u};     // hi, lo, hi
+        constexpr uint32_t LBO = (D::NN / 8) * 128;
+        const uint64_t b_hi = tc::smem_desc(tc::smem_u32(smem + D::OFF_B), LBO, 128);
+        const uint64_t b_lo = b_hi + uint64_t(D::B_BYTES >> 4);
 #pragma unroll
-        for (int p = 0; p < 3; ++p)
-#pragma unroll 1
-          for (int ks = 0; ks < D::KSTEPS; ++ks)
-            tc::mma_f16_ts(d_acc, a_base + a_off[p] + ks * 8,
-                           tc::smem_desc(b0 + b_off[p] + ks * 2 * LBO, LBO, SBO), IDESC,
-                           p > 0 || ks > 0);
-        tc::mma_commit(&s_mma_bar[buf]);
+        for (int i = 0; i < 3 * D::KSTEPS; ++i) {
+          const int p = i / D::KSTEPS, ks = i - p * D::KSTEPS;   // passes: hi.hi, hi.lo, lo.hi
+          const uint64_t bd = (p == 1 ? b_lo : b_hi) + uint64_t((ks * 2 * LBO) >> 4);
+          const uint32_t ad = a_base + (p == 2 ? D::ACOLS : 0) + ks * 8;
+          tc::mma_f16_ts_warp(d_acc, ad, bd, IDESC, i > 0 ? 1u : 0u);
+        }
+        tc::mma_commit_warp(&s_mma_bar[buf]);
+        __syncwarp();
+        if (t + 1 < ntiles_cta && tc::elect_one()) {
+          const int ns = (t + 1) % 3;
+          tc::bulk_wait_read_all();                     // stores of tile t-2 left that slot
+          tc::fence_proxy_async_smem();
+          tc_issue_loads<N, RK>(A, tile + gridDim.x, sU + ns * D::U_FLOATS, sR + ns * D::U_FLOATS,
+                                sG + ns * D::G_FLOATS, &s_load_bar[ns]);
+        }
+        __syncwarp();
       }
     }
 
@@ -421,7 +438,7 @@ __global__ void __launch_bounds__(TcDims<N>::THREADS, 1) tc_stage_kernel(const S
       }
       tc::fence_proxy_async_smem();
       __syncthreads();
-      if (tid == 0) {
+      if (warp == 0 && tc::elect_one()) {
         const uint32_t fb = uint32_t(Ev) * Np * 4;
         for (int c = 0; c < 6; ++c) {
           const size_t g = (size_t(c) * K + k0) * Np;
@@ -436,7 +453,7 @@ __global__ void __launch_bounds__(TcDims<N>::THREADS, 1) tc_stage_kernel(const S
       }
     }
   }
-  if (tid == 0) tc::bulk_wait_all();
+  if (warp == 0 && tc::elect_one()) tc::bulk_wait_all();
   tc::fence_before_sync();
   __syncthreads();
   if (warp == 0) tc::tmem_dealloc(tbase, 512);

@@ -121,6 +121,30 @@ __device__ __forceinline__ void mma_f16_ts(uint32_t d_tmem, uint32_t a_tmem, uin
       " tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n}"
       :: "r"(d_tmem), "r"(a_tmem), "l"(b_desc), "r"(idesc), "r"(accumulate ? 1u : 0u) : "memory");
 }
+// Same, executed by a whole warp with warp-uniform operands: one elected lane
+// issues (keeps the operands in uniform registers; much cheaper to issue than
+// from a divergent single-thread branch).
+__device__ __forceinline__ void mma_f16_ts_warp(uint32_t d_tmem, uint32_t a_tmem, uint64_t b_desc,
+                                                uint32_t idesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred P, Q;\n elect.sync _|P, 0xffffffff;\n setp.ne.b32 Q, %4, 0;\n"
+      " @P tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, Q;\n}"
+      :: "r"(d_tmem), "r"(a_tmem), "l"(b_desc), "r"(idesc), "r"(accumulate) : "memory");
+}
+__device__ __forceinline__ void mma_commit_warp(uint64_t* mbar) {
+  asm volatile(
+      "{\n .reg .pred P;\n elect.sync _|P, 0xffffffff;\n"
+      " @P tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n}"
+      :: "r"(smem_u32(mbar)) : "memory");
+}
+// One lane of a converged warp returns true.
+__device__ __forceinline__ bool elect_one() {
+  uint32_t p;
+  asm volatile("{\n .reg .pred P;\n elect.sync _|P, 0xffffffff;\n selp.u32 %0, 1, 0, P;\n}"
+               : "=r"(p));
+  return p != 0;
+}
+
 // Arrive once on the mbarrier when every previously issued MMA has completed.
 __device__ __forceinline__ void mma_commit(uint64_t* mbar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
