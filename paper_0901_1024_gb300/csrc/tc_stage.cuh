@@ -16,24 +16,24 @@
 // and B = [Dr Ds Dt LIFT] scaled by a power of two; both scales are removed in
 // the epilogue.
 //
-// Per persistent CTA (one per SM, 16 warps, all 512 tensor-memory columns):
-//   * B and the face-node tables are staged once in shared memory;
-//   * each tile's fields, RK register and geometry arrive by bulk copies
-//     (TMA engine, mbarrier completion) one tile ahead, into a 3-slot ring;
-//   * flux extraction (Alg. 2 of the paper): the neighbour values of faces that
-//     leave the tile are requested first (cp.async into a shared ghost
-//     buffer), the g^mu part of the A rows is computed while they are in
-//     flight, then the upwind flux of every face node goes to a shared
-//     [row][m] buffer (PEC ghost state on walls);
-//   * A rows are built by the warps owning their tensor-memory lane quarter
-//     (warp w: lanes 32 (w % 4).., K-range w / 4), split into FP16 hi/lo and
-//     written straight into tensor memory (tcgen05.st);
-//   * one thread issues the 3 x K/16 MMAs into a double-buffered FP32
-//     accumulator in tensor memory and commits them to an mbarrier;
-//   * while they run, the epilogue of tile t-1 reads its accumulator rows
-//     (tcgen05.ld), unscales them and applies the LSERK4 update
-//     res <- a res + dt rhs, u <- u + b res in place in shared memory; bulk
-//     copies write u_out and res back.
+// One persistent CTA per SM (all 512 tensor-memory columns), three warp groups
+// working on different tiles at once, linked by mbarriers:
+//   * flux warps (4): flux extraction (Alg. 2 of the paper) for tile t -- the
+//     neighbour values of faces leaving the tile are loaded into registers
+//     first, then every face node's upwind flux (PEC ghost state on walls) is
+//     written to a double-buffered shared [row][m] buffer;
+//   * builder warps (8, two per tensor-memory lane quarter): the A rows of
+//     tile t -- g^mu from the staged fields, flux rows from the flux buffer,
+//     one power-of-two scale per row, FP16 hi/lo split -- written straight
+//     into a double-buffered A in tensor memory (tcgen05.st);
+//   * MMA/epilogue warps (4): warp 0 issues the 3 x K/16 MMAs of tile t into a
+//     double-buffered FP32 accumulator (elect.sync, commit to an mbarrier) and
+//     all bulk copies; all four then read tile t-1's accumulator rows
+//     (tcgen05.ld), unscale them and apply the LSERK4 update
+//     res <- a res + dt rhs, u <- u + b res in place in shared memory, and
+//     bulk copies write u_out and res back.
+// Fields and geometry arrive by bulk copies three tiles ahead into a 4-slot
+// ring; the RK register one tile ahead into a 2-slot ring.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -52,41 +52,40 @@ template <int N> struct TcDims {
   static constexpr int KB = (Np + 1) & ~1;            // one mu block, even
   static constexpr int KG = 3 * KB;                   // g part
   static constexpr int KT = (KG + NF + 15) & ~15;     // total K, multiple of 16
+  static constexpr int KF = KT - KG;                  // flux part (with padding)
   static constexpr int KSTEPS = KT / 16;
   static constexpr int ACOLS = KT / 2;                // tensor-memory columns per A piece
   static constexpr int NN = (Np + 15) & ~15;          // MMA N
   static constexpr int BUF_COLS = 256;                // columns per pipeline buffer
   static_assert(2 * ACOLS + NN <= BUF_COLS, "tensor-memory buffer overflow");
   static constexpr int COLS_G = KB / 2;               // columns of one mu block
-  static constexpr int COLS_F = (KT - KG) / 2;        // columns of the flux block
-  static constexpr int ECOLS = NN / 4;                // epilogue columns per warp
+  static constexpr int COLS_F = KF / 2;               // columns of the flux block
   static constexpr int FSTR = NF | 1;                 // flux buffer row stride (odd)
-  static constexpr int THREADS = 512;
-  static constexpr int ITEMS = (E * NF + THREADS - 1) / THREADS;   // flux items per thread
+  static constexpr int THREADS = 512;                 // 4 epilogue + 4 flux + 8 builder warps
+  static constexpr int FLUX_THREADS = 128;
+  static constexpr int ITEMS = (E * NF + FLUX_THREADS - 1) / FLUX_THREADS;  // per flux thread
+  static constexpr int NSU = 4, NSR = 2;              // ring slots: fields+geometry, RK register
   // shared memory (bytes)
   static constexpr int U_FLOATS = 6 * E * Np;         // one tile of one state array
-  static constexpr int G_FLOATS = E * kTcGeoWords;   // word-major: [w][E]
+  static constexpr int G_FLOATS = E * kTcGeoWords;    // word-major [w][E]
   static constexpr int F_FLOATS = ROWS * FSTR;
   static constexpr int B_BYTES = NN * KT * 2;         // one FP16 piece
   static constexpr int TAB_BYTES = (4 * Nfp + 96 * Nfp + 15) & ~15;
   static constexpr int OFF_B = 0;                     // 2 pieces
-  static constexpr int OFF_U = OFF_B + 2 * B_BYTES;   // 3 slots
-  static constexpr int OFF_R = OFF_U + 3 * U_FLOATS * 4;
-  static constexpr int OFF_G = OFF_R + 3 * U_FLOATS * 4;
-  static constexpr int OFF_F = OFF_G + 3 * G_FLOATS * 4;
-  static constexpr int OFF_MAX = OFF_F + F_FLOATS * 4;   // [4][128] float
-  static constexpr int OFF_SC = OFF_MAX + 4 * 128 * 4;   // [2][128] float
-  static constexpr int OFF_TAB = OFF_SC + 2 * 128 * 4;
-  static constexpr int GH_STR = 7;                       // ghost record stride (odd)
-  static constexpr int OFF_GH = OFF_TAB + TAB_BYTES;     // [E*NF][GH_STR] neighbour values
-  static constexpr int OFF_IT = OFF_GH + E * NF * GH_STR * 4;   // [E*NF] packed item words
-  static constexpr int OFF_DESC = OFF_IT + E * NF * 4;   // [3][KSTEPS] B descriptors
-  static constexpr int SMEM = OFF_DESC + ((3 * KSTEPS * 8 + 15) & ~15);
+  static constexpr int OFF_U = OFF_B + 2 * B_BYTES;   // NSU slots
+  static constexpr int OFF_G = OFF_U + NSU * U_FLOATS * 4;
+  static constexpr int OFF_R = OFF_G + NSU * G_FLOATS * 4;   // NSR slots
+  static constexpr int OFF_F = OFF_R + NSR * U_FLOATS * 4;   // 2 buffers
+  static constexpr int OFF_MAX = OFF_F + 2 * F_FLOATS * 4;   // [2][128] float
+  static constexpr int OFF_SC = OFF_MAX + 2 * 128 * 4;       // [4][128] float
+  static constexpr int OFF_TAB = OFF_SC + 4 * 128 * 4;
+  static constexpr int OFF_IT = OFF_TAB + TAB_BYTES;         // [E*NF] packed item words
+  static constexpr int SMEM = OFF_IT + E * NF * 4;
   static_assert((U_FLOATS * 4) % 16 == 0 && (E * Np * 4) % 16 == 0, "bulk-copy alignment");
   static_assert(OFF_U % 16 == 0 && OFF_R % 16 == 0 && OFF_G % 16 == 0 && OFF_F % 16 == 0 &&
-                OFF_TAB % 16 == 0 && OFF_IT % 16 == 0 && OFF_DESC % 16 == 0, "alignment");
-  static_assert((E * 4) % 16 == 0, "geometry word chunks must be 16-byte multiples");
-  static_assert(SMEM <= 220 * 1024, "shared memory budget");
+                OFF_TAB % 16 == 0 && OFF_IT % 16 == 0, "alignment");
+  static_assert((G_FLOATS * 4) % 16 == 0, "geometry block must be a 16-byte multiple");
+  static_assert(SMEM <= 226 * 1024, "shared memory budget");
 };
 
 static_assert(tc_b_bytes(4) == 2 * TcDims<4>::B_BYTES, "B buffer size formula");
@@ -136,7 +135,7 @@ __device__ __forceinline__ void tmem_load_cols(uint32_t taddr, uint32_t* v) {
     tc::tmem_ld<4>(taddr, v);
     tmem_load_cols<NC - 4>(taddr + 4, v + 4);
   } else {
-    static_assert(NC == 0, "epilogue columns must be a multiple of 4");
+    static_assert(NC == 0, "accumulator columns must be a multiple of 4");
   }
 }
 
@@ -146,21 +145,40 @@ __device__ __forceinline__ float row_scale(float rmax) {
   return ex == 0 ? 1.f : __uint_as_float(uint32_t(max(1, min(254, 268 - ex))) << 23);
 }
 
-// One thread: bulk copies of tile `tile` (fields, RK register, geometry block)
-// into ring slot buffers, completing on `bar`.
-template <int N, bool RK>
-__device__ __forceinline__ void tc_issue_loads(const StageArgs& A, int tile, float* su, float* sr,
-                                               float* sg, uint64_t* bar) {
+__device__ __forceinline__ void named_sync(int id, int nthreads) {
+  asm volatile("bar.sync %0, %1;" :: "r"(id), "r"(nthreads) : "memory");
+}
+
+constexpr uint32_t kWaitLimit = 1u << 26;
+
+// Bounded mbarrier wait; on timeout records the failure in *status.
+__device__ __forceinline__ void wait_or_flag(uint64_t* bar, uint32_t parity, int* status) {
+  if (!tc::mbar_wait_bounded(bar, parity, kWaitLimit) && status) atomicExch(status, 1);
+}
+
+// One thread: bulk copies of tile `tile`'s fields and geometry block.
+template <int N>
+__device__ __forceinline__ void tc_load_u(const StageArgs& A, int tile, float* su, float* sg,
+                                          uint64_t* bar) {
   using D = TcDims<N>;
   const int K = A.K, k0 = tile * D::E, Ev = min(D::E, K - k0);
   const uint32_t fb = uint32_t(Ev) * D::Np * 4;
-  constexpr uint32_t gb = kTcGeoWords * D::E * 4;      // one tiled geometry block
-  tc::mbar_expect_tx(bar, (RK ? 12u : 6u) * fb + gb);
-  for (int c = 0; c < 6; ++c) {
+  constexpr uint32_t gb = D::G_FLOATS * 4;
+  tc::mbar_expect_tx(bar, 6u * fb + gb);
+  for (int c = 0; c < 6; ++c)
     tc::bulk_g2s(su + c * D::E * D::Np, A.u_in + (size_t(c) * K + k0) * D::Np, fb, bar);
-    if (RK) tc::bulk_g2s(sr + c * D::E * D::Np, A.res + (size_t(c) * K + k0) * D::Np, fb, bar);
-  }
   tc::bulk_g2s(sg, A.tcgeo + size_t(tile) * A.tc_geo_stride, gb, bar);
+}
+
+// One thread: bulk copies of tile `tile`'s RK register.
+template <int N>
+__device__ __forceinline__ void tc_load_res(const StageArgs& A, int tile, float* sr, uint64_t* bar) {
+  using D = TcDims<N>;
+  const int K = A.K, k0 = tile * D::E, Ev = min(D::E, K - k0);
+  const uint32_t fb = uint32_t(Ev) * D::Np * 4;
+  tc::mbar_expect_tx(bar, 6u * fb);
+  for (int c = 0; c < 6; ++c)
+    tc::bulk_g2s(sr + c * D::E * D::Np, A.res + (size_t(c) * K + k0) * D::Np, fb, bar);
 }
 
 template <int N, bool RK>
@@ -169,35 +187,34 @@ __global__ void __launch_bounds__(TcDims<N>::THREADS, 1) tc_stage_kernel(const S
   constexpr int E = D::E, Np = D::Np, Nfp = D::Nfp, NF = D::NF, FSTR = D::FSTR;
   extern __shared__ __align__(1024) unsigned char smem[];
   __shared__ uint32_t s_tmem;
-  __shared__ __align__(8) uint64_t s_mma_bar[2];
-  __shared__ __align__(8) uint64_t s_load_bar[3];
+  __shared__ __align__(8) uint64_t s_u_full[D::NSU];
+  __shared__ __align__(8) uint64_t s_r_full[D::NSR];
+  __shared__ __align__(8) uint64_t s_f_full[2], s_f_empty[2], s_a_full[2], s_mma_done[2];
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int quarter = warp & 3, part = warp >> 2;     // lane quarter, K-range / column part
   const int K = A.K;
-  const int ntiles_cta = (A.num_tiles - int(blockIdx.x) + int(gridDim.x) - 1) / int(gridDim.x);
-  if (ntiles_cta <= 0) return;
+  const int ntiles = (A.num_tiles - int(blockIdx.x) + int(gridDim.x) - 1) / int(gridDim.x);
+  if (ntiles <= 0) return;
 
   float* sU = reinterpret_cast<float*>(smem + D::OFF_U);
-  float* sR = reinterpret_cast<float*>(smem + D::OFF_R);
   float* sG = reinterpret_cast<float*>(smem + D::OFF_G);
+  float* sR = reinterpret_cast<float*>(smem + D::OFF_R);
   float* sF = reinterpret_cast<float*>(smem + D::OFF_F);
   float* sMax = reinterpret_cast<float*>(smem + D::OFF_MAX);
   float* sScale = reinterpret_cast<float*>(smem + D::OFF_SC);
-  float* sGhost = reinterpret_cast<float*>(smem + D::OFF_GH);
-  uint32_t* sItem = reinterpret_cast<uint32_t*>(smem + D::OFF_IT);
   unsigned char* sFmask = smem + D::OFF_TAB;
   unsigned char* sPerm = sFmask + 4 * Nfp;
+  uint32_t* sItem = reinterpret_cast<uint32_t*>(smem + D::OFF_IT);
 
-  // ---- set-up: B pieces, tables, tensor memory, barriers, first loads ------
+  // ---- set-up: B pieces, tables, tensor memory, barriers -------------------
   {
     const uint4* src = reinterpret_cast<const uint4*>(A.tcB);
     uint4* dst = reinterpret_cast<uint4*>(smem + D::OFF_B);
     for (int i = tid; i < 2 * D::B_BYTES / 16; i += D::THREADS) dst[i] = __ldg(src + i);
     for (int i = tid; i < 4 * Nfp; i += D::THREADS) sFmask[i] = __ldg(A.fmask + i);
     for (int i = tid; i < 96 * Nfp; i += D::THREADS) sPerm[i] = __ldg(A.perm + i);
-    // flux item idx -> e | m << 5 | f << 13 | j << 15 | idM << 21, face nodes of
-    // one element consecutive: a warp's gathers hit the same neighbour blocks
+    // flux item idx -> e | m << 5 | f << 13 | j << 15 | idM << 21, the face nodes of
+    // one element consecutive (a warp's gathers share neighbour blocks)
     for (int idx = tid; idx < E * NF; idx += D::THREADS) {
       const int m = idx % NF, e = idx / NF, f = m / Nfp, j = m - f * Nfp;
       sItem[idx] = uint32_t(e) | uint32_t(m) << 5 | uint32_t(f) << 13 | uint32_t(j) << 15 |
@@ -207,55 +224,153 @@ __global__ void __launch_bounds__(TcDims<N>::THREADS, 1) tc_stage_kernel(const S
   tc::fence_proxy_async_smem();
   if (warp == 0) tc::tmem_alloc(&s_tmem, 512);
   if (tid == 0) {
-    tc::mbar_init(&s_mma_bar[0], 1);
-    tc::mbar_init(&s_mma_bar[1], 1);
-    for (int i = 0; i < 3; ++i) tc::mbar_init(&s_load_bar[i], 1);
+    for (int i = 0; i < D::NSU; ++i) tc::mbar_init(&s_u_full[i], 1);
+    for (int i = 0; i < D::NSR; ++i) tc::mbar_init(&s_r_full[i], 1);
+    for (int i = 0; i < 2; ++i) {
+      tc::mbar_init(&s_f_full[i], D::FLUX_THREADS);
+      tc::mbar_init(&s_f_empty[i], 128);          // the builder warps reading flux rows
+      tc::mbar_init(&s_a_full[i], 256);           // all builder threads
+      tc::mbar_init(&s_mma_done[i], 1);
+    }
     tc::fence_mbar_init();
   }
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
-  if (warp == 0 && tc::elect_one()) tc_issue_loads<N, RK>(A, blockIdx.x, sU, sR, sG, &s_load_bar[0]);
   const uint32_t tbase = s_tmem;
-  const uint32_t lane_off = uint32_t(quarter * 32) << 16;
-  const int row = quarter * 32 + lane;               // A / D row owned by this thread
-  const int rc = row / E, re = row - (row / E) * E;  // field, element of that row
-  constexpr uint32_t IDESC = tc::idesc_f16(128, D::NN);
-  constexpr uint32_t WAIT_LIMIT = 1u << 26;
 
-  for (int t = 0; t <= ntiles_cta; ++t) {
-    const int buf = t & 1;
-    if (t < ntiles_cta) {
-      const int slot = t % 3;
+  if (warp < 4) {
+    // ======================= MMA issue + epilogue warps ========================
+    const int row = warp * 32 + lane;
+    const int rc = row / E, re = row - (row / E) * E;
+    const uint32_t lane_off = uint32_t(warp * 32) << 16;
+    if (warp == 0 && tc::elect_one()) {   // first loads: fields of tiles 0..2, res of tile 0
+      for (int t = 0; t < 3 && t < ntiles; ++t)
+        tc_load_u<N>(A, blockIdx.x + t * gridDim.x, sU + t * D::U_FLOATS, sG + t * D::G_FLOATS,
+                     &s_u_full[t]);
+      if (RK) tc_load_res<N>(A, blockIdx.x, sR, &s_r_full[0]);
+    }
+    __syncwarp();
+    constexpr uint32_t IDESC = tc::idesc_f16(128, D::NN);
+    constexpr uint32_t LBO = (D::NN / 8) * 128;
+    for (int j = 0; j <= ntiles; ++j) {
+      if (j < ntiles) {
+        // every epilogue warp observes A(j) complete (this also publishes tile j's
+        // row scales) before the MMAs start, so no waiter can fall a phase behind
+        wait_or_flag(&s_a_full[j & 1], (j >> 1) & 1, A.status);
+        named_sync(1, 128);
+      }
+      if (j < ntiles && warp == 0) {                 // MMAs of tile j
+        const int buf = j & 1;
+        tc::fence_after_sync();
+        const uint32_t d_acc = tbase + buf * D::BUF_COLS + 2 * D::ACOLS;
+        const uint32_t a_base = tbase + buf * D::BUF_COLS;
+        const uint64_t b_hi = tc::smem_desc(tc::smem_u32(smem + D::OFF_B), LBO, 128);
+        const uint64_t b_lo = b_hi + uint64_t(D::B_BYTES >> 4);
+#pragma unroll
+        for (int i = 0; i < 3 * D::KSTEPS; ++i) {
+          const int p = i / D::KSTEPS, ks = i - p * D::KSTEPS;   // passes: hi.hi, hi.lo, lo.hi
+          const uint64_t bd = (p == 1 ? b_lo : b_hi) + uint64_t((ks * 2 * LBO) >> 4);
+          const uint32_t ad = a_base + (p == 2 ? D::ACOLS : 0) + ks * 8;
+          tc::mma_f16_ts_warp(d_acc, ad, bd, IDESC, i > 0 ? 1u : 0u);
+        }
+        tc::mma_commit_warp(&s_mma_done[buf]);
+        __syncwarp();
+      }
+      if (j >= 1) {                                  // epilogue of tile t = j - 1
+        const int t = j - 1, buf = t & 1;
+        const int tile = blockIdx.x + t * gridDim.x;
+        const int k0 = tile * E, Ev = min(E, K - k0);
+        float* su = sU + (t % D::NSU) * D::U_FLOATS;
+        float* sr = sR + (t % D::NSR) * D::U_FLOATS;
+        wait_or_flag(&s_mma_done[buf], (t >> 1) & 1, A.status);
+        if (RK) wait_or_flag(&s_r_full[t % D::NSR], (t / D::NSR) & 1, A.status);
+        tc::fence_after_sync();
+        uint32_t acc[D::NN];
+        tmem_load_cols<D::NN>(tbase + lane_off + buf * D::BUF_COLS + 2 * D::ACOLS, acc);
+        tc::tmem_ld_wait();
+        tc::fence_before_sync();
+        if (row < D::ROWS && re < Ev) {
+          const float inv = A.tc_inv_bscale / sScale[(t & 3) * 128 + row];
+          const int base = (rc * E + re) * Np;
+#pragma unroll
+          for (int i = 0; i < Np; ++i) {
+            const float r = __uint_as_float(acc[i]) * inv;
+            if (RK) {
+              const float rn = fmaf(A.a, sr[base + i], A.dt * r);
+              sr[base + i] = rn;
+              su[base + i] = fmaf(A.b, rn, su[base + i]);
+            } else {
+              sr[base + i] = r;
+            }
+          }
+        }
+        tc::fence_proxy_async_smem();
+        named_sync(1, 128);
+        if (warp == 0 && tc::elect_one()) {
+          const uint32_t fb = uint32_t(Ev) * Np * 4;
+          for (int c = 0; c < 6; ++c) {
+            const size_t g = (size_t(c) * K + k0) * Np;
+            if (RK) {
+              tc::bulk_s2g(A.u_out + g, su + c * E * Np, fb);
+              tc::bulk_s2g(A.res + g, sr + c * E * Np, fb);
+            } else {
+              tc::bulk_s2g(A.rhs + g, sr + c * E * Np, fb);
+            }
+          }
+          tc::bulk_commit();
+          // slots of tile t-1 (stored one round ago) take tiles t+3 and t+1
+          asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
+          tc::fence_proxy_async_smem();
+          if (t + 3 < ntiles) {
+            const int s = (t + 3) % D::NSU;
+            tc_load_u<N>(A, tile + 3 * gridDim.x, sU + s * D::U_FLOATS, sG + s * D::G_FLOATS,
+                         &s_u_full[s]);
+          }
+          if (RK && t + 1 < ntiles) {
+            const int s = (t + 1) % D::NSR;
+            tc_load_res<N>(A, tile + gridDim.x, sR + s * D::U_FLOATS, &s_r_full[s]);
+          }
+        }
+        __syncwarp();
+      }
+    }
+    if (warp == 0 && tc::elect_one()) tc::bulk_wait_all();
+    __syncwarp();
+  } else if (warp < 8) {
+    // ============================== flux warps =================================
+    const int ft = tid - 128;
+    for (int t = 0; t < ntiles; ++t) {
       const int tile = blockIdx.x + t * gridDim.x;
       const int k0 = tile * E, Ev = min(E, K - k0);
-      float* su = sU + slot * D::U_FLOATS;
-      float* sg = sG + slot * D::G_FLOATS;
-      if (!tc::mbar_wait_bounded(&s_load_bar[slot], (t / 3) & 1, WAIT_LIMIT) && A.status)
-        atomicExch(A.status, 1);
-      __syncthreads();                                  // previous epilogue done everywhere
-
-      // ---- flux, step 1: request neighbour values that leave the tile -----
+      const int slot = t % D::NSU, fb = t & 1;
+      const float* su = sU + slot * D::U_FLOATS;
+      const float* sg = sG + slot * D::G_FLOATS;
+      float* F = sF + fb * D::F_FLOATS;
+      wait_or_flag(&s_u_full[slot], (t / D::NSU) & 1, A.status);
+      if (t >= 2) wait_or_flag(&s_f_empty[fb], ((t - 2) >> 1) & 1, A.status);
+      // step 1: classify items, load neighbour values that leave the tile
       uint32_t item[D::ITEMS];
-      int kind[D::ITEMS];        // 0 skip, 1 wall, 2 in tile (offset in ofs), 3 gathered
+      int kind[D::ITEMS];          // 0 none, 1 wall, 2 in tile (ofs), 3 loaded
       int ofs[D::ITEMS];
+      float uP[D::ITEMS][6];
 #pragma unroll
       for (int q = 0; q < D::ITEMS; ++q) {
-        const int idx = tid + q * D::THREADS;
+        const int idx = ft + q * D::FLUX_THREADS;
         kind[q] = 0;
         ofs[q] = 0;
         item[q] = 0;
         if (idx < E * NF) {
           const uint32_t it = sItem[idx];
           item[q] = it;
-          const int e = it & 31, f = (it >> 13) & 3, j = (it >> 15) & 63;
+          const int e = it & 31, f = (it >> 13) & 3, jj = (it >> 15) & 63;
           if (e < Ev) {
             const unsigned code = (__float_as_uint(sg[9 * E + e]) >> (8 * f)) & 0xffu;
             if (code == 0u) {
               kind[q] = 1;
             } else {
               const int k2 = __float_as_int(sg[(26 + f) * E + e]);
-              const int i2 = sPerm[(f * 24 + int(code) - 1) * Nfp + j];
+              const int i2 = sPerm[(f * 24 + int(code) - 1) * Nfp + jj];
               const int e2 = k2 - k0;
               if (e2 >= 0 && e2 < Ev) {
                 kind[q] = 2;
@@ -264,46 +379,16 @@ __global__ void __launch_bounds__(TcDims<N>::THREADS, 1) tc_stage_kernel(const S
                 kind[q] = 3;
                 const float* src = A.u_in + size_t(k2) * Np + i2;
 #pragma unroll
-                for (int c = 0; c < 6; ++c)
-                  tc::cp_async4(sGhost + idx * D::GH_STR + c, src + size_t(c) * K * Np);
+                for (int c = 0; c < 6; ++c) uP[q][c] = __ldg(src + size_t(c) * K * Np);
               }
             }
           }
         }
       }
-
-      // ---- g^mu part of the A rows (parts 0..2), while the loads fly ------
-      const bool live = row < D::ROWS && re < Ev;
-      float v[D::KB];
-      float mx = 0.f;
-      if (part < 3) {
-        if (live) {
-          // curl component o of the other field kind: rhs_E = curl H, rhs_H = -curl E
-          const int o = rc % 3;
-          const int fa = rc < 3 ? 3 + (o + 2) % 3 : (o + 2) % 3;
-          const int fb = rc < 3 ? 3 + (o + 1) % 3 : (o + 1) % 3;
-          const float sgn = rc < 3 ? 1.f : -1.f;
-          const float ca = sgn * sg[(3 * part + (o + 1) % 3) * E + re];
-          const float cb = -sgn * sg[(3 * part + (o + 2) % 3) * E + re];
-          const float* ua = su + (fa * E + re) * Np;
-          const float* ub = su + (fb * E + re) * Np;
+      // step 2: upwind flux of every face node
 #pragma unroll
-          for (int j = 0; j < D::KB; ++j) {
-            v[j] = j < Np ? fmaf(ca, ua[j], cb * ub[j]) : 0.f;
-            mx = fmaxf(mx, fabsf(v[j]));
-          }
-        } else {
-#pragma unroll
-          for (int j = 0; j < D::KB; ++j) v[j] = 0.f;
-        }
-      }
-
-      // ---- flux, step 2: upwind flux of every face node -> sF -------------
-      tc::cp_async_wait_all();                          // this thread's gathers
-#pragma unroll 1
       for (int q = 0; q < D::ITEMS; ++q) {
         if (kind[q] == 0) continue;
-        const int idx = tid + q * D::THREADS;
         const uint32_t it = item[q];
         const int e = it & 31, m = (it >> 5) & 255, f = (it >> 13) & 3, idM = it >> 21;
         float uM[6], up[6];
@@ -317,17 +402,17 @@ __global__ void __launch_bounds__(TcDims<N>::THREADS, 1) tc_stage_kernel(const S
           for (int c = 0; c < 6; ++c) up[c] = su[c * E * Np + ofs[q]];
         } else {
 #pragma unroll
-          for (int c = 0; c < 6; ++c) up[c] = sGhost[idx * D::GH_STR + c];
+          for (int c = 0; c < 6; ++c) up[c] = uP[q][c];
         }
+        const float sc = 0.5f * sg[(13 + 4 * f) * E + e];
         const float nx = sg[(10 + 4 * f) * E + e], ny = sg[(11 + 4 * f) * E + e];
         const float nz = sg[(12 + 4 * f) * E + e];
-        const float sc = 0.5f * sg[(13 + 4 * f) * E + e];
         const float dEx = uM[0] - up[0], dEy = uM[1] - up[1], dEz = uM[2] - up[2];
         const float dHx = uM[3] - up[3], dHy = uM[4] - up[4], dHz = uM[5] - up[5];
         const float ndE = nx * dEx + ny * dEy + nz * dEz;
         const float ndH = nx * dHx + ny * dHy + nz * dHz;
         const float al = A.alpha;
-        float* fr = sF + e * FSTR + m;
+        float* fr = F + e * FSTR + m;
         fr[0 * E * FSTR] = sc * (-(ny * dHz - nz * dHy) + al * (nx * ndE - dEx));
         fr[1 * E * FSTR] = sc * (-(nz * dHx - nx * dHz) + al * (ny * ndE - dEy));
         fr[2 * E * FSTR] = sc * (-(nx * dHy - ny * dHx) + al * (nz * ndE - dEz));
@@ -335,125 +420,96 @@ __global__ void __launch_bounds__(TcDims<N>::THREADS, 1) tc_stage_kernel(const S
         fr[4 * E * FSTR] = sc * ((nz * dEx - nx * dEz) + al * (ny * ndH - dHy));
         fr[5 * E * FSTR] = sc * ((nx * dEy - ny * dEx) + al * (nz * ndH - dHz));
       }
-      __syncthreads();
-
-      // ---- flux part of the A rows (part 3), row scales, split, store -----
-      constexpr int KF = D::KT - D::KG;
-      const float* frow = sF + (rc * E + re) * FSTR;
-      if (part == 3 && live) {
-#pragma unroll 4
-        for (int m = 0; m < NF; ++m) mx = fmaxf(mx, fabsf(frow[m]));
+      tc::mbar_arrive(&s_f_full[fb]);
+    }
+  } else {
+    // ============================= builder warps ===============================
+    const int bw = warp - 8;
+    const int quarter = bw & 3, part = bw >> 2;     // part 0: g^r, g^s; part 1: g^t + flux
+    const int row = quarter * 32 + lane;
+    const int rc = row / E, re = row - (row / E) * E;
+    const uint32_t lane_off = uint32_t(quarter * 32) << 16;
+    for (int t = 0; t < ntiles; ++t) {
+      const int tile = blockIdx.x + t * gridDim.x;
+      const int k0 = tile * E, Ev = min(E, K - k0);
+      const int slot = t % D::NSU, buf = t & 1;
+      const float* su = sU + slot * D::U_FLOATS;
+      const float* sg = sG + slot * D::G_FLOATS;
+      (void)k0;
+      wait_or_flag(&s_u_full[slot], (t / D::NSU) & 1, A.status);
+      const bool live = row < D::ROWS && re < Ev;
+      // g^mu values of this row: part 0 mu = 0, 1; part 1 mu = 2
+      float v[2 * D::KB];
+      float mx = 0.f;
+      {
+        const int o = rc % 3;
+        const int fa = rc < 3 ? 3 + (o + 2) % 3 : (o + 2) % 3;
+        const int fb = rc < 3 ? 3 + (o + 1) % 3 : (o + 1) % 3;
+        const float sgn = rc < 3 ? 1.f : -1.f;
+        const float* ua = su + (fa * E + re) * Np;
+        const float* ub = su + (fb * E + re) * Np;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int mu = part == 0 ? h : 2;
+          if (part == 1 && h == 1) break;
+          const float ca = live ? sgn * sg[(3 * mu + (o + 1) % 3) * E + re] : 0.f;
+          const float cb = live ? -sgn * sg[(3 * mu + (o + 2) % 3) * E + re] : 0.f;
+#pragma unroll
+          for (int jj = 0; jj < D::KB; ++jj) {
+            const float g = (live && jj < Np) ? fmaf(ca, ua[jj], cb * ub[jj]) : 0.f;
+            v[h * D::KB + jj] = g;
+            mx = fmaxf(mx, fabsf(g));
+          }
+        }
       }
+      // flux rows (part 1): first pass for the row maximum
+      const float* F = sF + buf * D::F_FLOATS;
+      const float* frow = F + (rc * E + re) * FSTR;
+      if (part == 1) {
+        wait_or_flag(&s_f_full[buf], (t >> 1) & 1, A.status);
+        if (live) {
+#pragma unroll 4
+          for (int m = 0; m < NF; ++m) mx = fmaxf(mx, fabsf(frow[m]));
+        }
+      }
+      // A[buf] is free once the MMAs of tile t-2 have completed
+      if (t >= 2) wait_or_flag(&s_mma_done[buf], ((t - 2) >> 1) & 1, A.status);
+      tc::fence_after_sync();
       sMax[part * 128 + row] = mx;
-      __syncthreads();
-      const float s = row_scale(fmaxf(fmaxf(sMax[row], sMax[128 + row]),
-                                      fmaxf(sMax[256 + row], sMax[384 + row])));
+      named_sync(2, 256);
+      const float s = row_scale(fmaxf(sMax[row], sMax[128 + row]));
+      if (part == 0) sScale[(t & 3) * 128 + row] = s;
       const uint32_t a_hi = tbase + lane_off + buf * D::BUF_COLS;
       const uint32_t a_lo = a_hi + D::ACOLS;
-      if (part < 3) {
-        if (part == 0) sScale[buf * 128 + row] = s;
-        split_store<D::COLS_G>(v, s, a_hi + part * D::COLS_G, a_lo + part * D::COLS_G);
+      if (part == 0) {
+        split_store<2 * D::COLS_G>(v, s, a_hi, a_lo);
       } else {
-        // second pass over the flux row, 32 values (16 columns) at a time
+        split_store<D::COLS_G>(v, s, a_hi + 2 * D::COLS_G, a_lo + 2 * D::COLS_G);
+        // flux rows, second pass, 32 values (16 columns) at a time
 #pragma unroll
         for (int c0 = 0; c0 < D::COLS_F; c0 += 16) {
-          constexpr int CH = 16;
-          float w[2 * CH];
+          float w[32];
 #pragma unroll
-          for (int q = 0; q < 2 * CH; ++q) {
+          for (int q = 0; q < 32; ++q) {
             const int m = 2 * c0 + q;
             w[q] = (live && m < NF) ? frow[m] : 0.f;
           }
-          if (c0 + CH <= D::COLS_F) {
-            split_store<CH>(w, s, a_hi + 3 * D::COLS_G + c0, a_lo + 3 * D::COLS_G + c0);
+          if (c0 + 16 <= D::COLS_F) {
+            split_store<16>(w, s, a_hi + 3 * D::COLS_G + c0, a_lo + 3 * D::COLS_G + c0);
           } else {
-            split_store<D::COLS_F % CH>(w, s, a_hi + 3 * D::COLS_G + c0, a_lo + 3 * D::COLS_G + c0);
+            split_store<D::COLS_F % 16>(w, s, a_hi + 3 * D::COLS_G + c0,
+                                        a_lo + 3 * D::COLS_G + c0);
           }
         }
+        tc::mbar_arrive(&s_f_empty[buf]);
       }
       tc::tmem_st_wait();
       tc::fence_before_sync();
-      __syncthreads();
-
-      // ---- warp 0: issue the MMAs of tile t, then the loads of tile t+1 ---
-      if (warp == 0) {
-        tc::fence_after_sync();
-        const uint32_t d_acc = tbase + buf * D::BUF_COLS + 2 * D::ACOLS;
-        const uint32_t a_base = tbase + buf * D::BUF_COLS;
-        constexpr uint32_t LBO = (D::NN / 8) * 128;
-        const uint64_t b_hi = tc::smem_desc(tc::smem_u32(smem + D::OFF_B), LBO, 128);
-        const uint64_t b_lo = b_hi + uint64_t(D::B_BYTES >> 4);
-#pragma unroll
-        for (int i = 0; i < 3 * D::KSTEPS; ++i) {
-          const int p = i / D::KSTEPS, ks = i - p * D::KSTEPS;   // passes: hi.hi, hi.lo, lo.hi
-          const uint64_t bd = (p == 1 ? b_lo : b_hi) + uint64_t((ks * 2 * LBO) >> 4);
-          const uint32_t ad = a_base + (p == 2 ? D::ACOLS : 0) + ks * 8;
-          tc::mma_f16_ts_warp(d_acc, ad, bd, IDESC, i > 0 ? 1u : 0u);
-        }
-        tc::mma_commit_warp(&s_mma_bar[buf]);
-        __syncwarp();
-        if (t + 1 < ntiles_cta && tc::elect_one()) {
-          const int ns = (t + 1) % 3;
-          tc::bulk_wait_read_all();                     // stores of tile t-2 left that slot
-          tc::fence_proxy_async_smem();
-          tc_issue_loads<N, RK>(A, tile + gridDim.x, sU + ns * D::U_FLOATS, sR + ns * D::U_FLOATS,
-                                sG + ns * D::G_FLOATS, &s_load_bar[ns]);
-        }
-        __syncwarp();
-      }
-    }
-
-    // ---- epilogue of tile t-1 ---------------------------------------------
-    if (t >= 1) {
-      const int tp = t - 1, pbuf = tp & 1, pslot = tp % 3;
-      const int tile = blockIdx.x + tp * gridDim.x;
-      const int k0 = tile * E, Ev = min(E, K - k0);
-      float* su = sU + pslot * D::U_FLOATS;
-      float* sr = sR + pslot * D::U_FLOATS;
-      if (!tc::mbar_wait_bounded(&s_mma_bar[pbuf], (tp >> 1) & 1, WAIT_LIMIT) && A.status)
-        atomicExch(A.status, 1);
-      tc::fence_after_sync();
-      uint32_t acc[D::ECOLS];
-      tmem_load_cols<D::ECOLS>(tbase + lane_off + pbuf * D::BUF_COLS + 2 * D::ACOLS +
-                               part * D::ECOLS, acc);
-      tc::tmem_ld_wait();
-      tc::fence_before_sync();
-      if (row < D::ROWS && re < Ev) {
-        const float inv = A.tc_inv_bscale / sScale[pbuf * 128 + row];
-        const int base = (rc * E + re) * Np;
-#pragma unroll
-        for (int q = 0; q < D::ECOLS; ++q) {
-          const int i = part * D::ECOLS + q;
-          if (i < Np) {
-            const float r = __uint_as_float(acc[q]) * inv;
-            if (RK) {
-              const float rn = fmaf(A.a, sr[base + i], A.dt * r);
-              sr[base + i] = rn;
-              su[base + i] = fmaf(A.b, rn, su[base + i]);
-            } else {
-              sr[base + i] = r;
-            }
-          }
-        }
-      }
-      tc::fence_proxy_async_smem();
-      __syncthreads();
-      if (warp == 0 && tc::elect_one()) {
-        const uint32_t fb = uint32_t(Ev) * Np * 4;
-        for (int c = 0; c < 6; ++c) {
-          const size_t g = (size_t(c) * K + k0) * Np;
-          if (RK) {
-            tc::bulk_s2g(A.u_out + g, su + c * E * Np, fb);
-            tc::bulk_s2g(A.res + g, sr + c * E * Np, fb);
-          } else {
-            tc::bulk_s2g(A.rhs + g, sr + c * E * Np, fb);
-          }
-        }
-        tc::bulk_commit();
-      }
+      named_sync(2, 256);          // sMax reused next tile; all A columns written
+      tc::mbar_arrive(&s_a_full[buf]);
     }
   }
-  if (warp == 0 && tc::elect_one()) tc::bulk_wait_all();
+
   tc::fence_before_sync();
   __syncthreads();
   if (warp == 0) tc::tmem_dealloc(tbase, 512);
