@@ -32,7 +32,7 @@
 //     (tcgen05.ld), unscale them and apply the LSERK4 update
 //     res <- a res + dt rhs, u <- u + b res in place in shared memory, and
 //     bulk copies write u_out and res back.
-// Fields and geometry arrive by bulk copies three tiles ahead into a 4-slot
+// Fields and geometry arrive by bulk copies four tiles ahead into a 5-slot
 // ring; the RK register one tile ahead into a 2-slot ring.
 #pragma once
 
@@ -64,7 +64,7 @@ template <int N> struct TcDims {
   static constexpr int THREADS = 512;                 // 4 epilogue + 4 flux + 8 builder warps
   static constexpr int FLUX_THREADS = 128;
   static constexpr int ITEMS = (E * NF + FLUX_THREADS - 1) / FLUX_THREADS;  // per flux thread
-  static constexpr int NSU = 4, NSR = 2;              // ring slots: fields+geometry, RK register
+  static constexpr int NSU = 5, NSR = 2;              // ring slots: fields+geometry, RK register
   // shared memory (bytes)
   static constexpr int U_FLOATS = 6 * E * Np;         // one tile of one state array
   static constexpr int G_FLOATS = E * kTcGeoWords;    // word-major [w][E]
@@ -76,14 +76,14 @@ template <int N> struct TcDims {
   static constexpr int OFF_G = OFF_U + NSU * U_FLOATS * 4;
   static constexpr int OFF_R = OFF_G + NSU * G_FLOATS * 4;   // NSR slots
   static constexpr int OFF_F = OFF_R + NSR * U_FLOATS * 4;   // 2 buffers
-  static constexpr int OFF_MAX = OFF_F + 2 * F_FLOATS * 4;   // [2][128] float
-  static constexpr int OFF_SC = OFF_MAX + 2 * 128 * 4;       // [4][128] float
-  static constexpr int OFF_TAB = OFF_SC + 4 * 128 * 4;
-  static constexpr int OFF_IT = OFF_TAB + TAB_BYTES;         // [E*NF] packed item words
-  static constexpr int SMEM = OFF_IT + E * NF * 4;
+  static constexpr int OFF_BND = OFF_F + 2 * F_FLOATS * 4;     // [2 parts][128] row bounds
+  static constexpr int OFF_SC = OFF_BND + 2 * 128 * 4;       // [4][128] row scales
+  static constexpr int OFF_INFO = OFF_SC + 4 * 128 * 4;      // [ITEMS][128] u16 item kinds
+  static constexpr int OFF_TAB = OFF_INFO + ((ITEMS * FLUX_THREADS * 2 + 15) & ~15);
+  static constexpr int SMEM = OFF_TAB + TAB_BYTES;
   static_assert((U_FLOATS * 4) % 16 == 0 && (E * Np * 4) % 16 == 0, "bulk-copy alignment");
   static_assert(OFF_U % 16 == 0 && OFF_R % 16 == 0 && OFF_G % 16 == 0 && OFF_F % 16 == 0 &&
-                OFF_TAB % 16 == 0 && OFF_IT % 16 == 0, "alignment");
+                OFF_TAB % 16 == 0 && OFF_INFO % 16 == 0, "alignment");
   static_assert((G_FLOATS * 4) % 16 == 0, "geometry block must be a 16-byte multiple");
   static_assert(SMEM <= 226 * 1024, "shared memory budget");
 };
@@ -121,6 +121,20 @@ __device__ __forceinline__ void split_store(const float* v, float s, uint32_t t_
   tmem_store_cols<CH>(t_hi, hi);
   tmem_store_cols<CH>(t_lo, lo);
   if constexpr (NC > CH) split_store<NC - CH>(v + 2 * CH, s, t_hi + CH, t_lo + CH);
+}
+
+// Columns [C0, C0 + NC) of one row: value j = val(j) for j < 2 NC, split into
+// FP16 hi/lo pairs and stored 8 columns at a time (values are produced only as
+// they are stored, so few registers are live).
+template <int NC, int C0 = 0, typename Val>
+__device__ __forceinline__ void split_store_fn(const Val& val, uint32_t t_hi, uint32_t t_lo) {
+  constexpr int CH = NC < 8 ? NC : 8;
+  uint32_t hi[CH], lo[CH];
+#pragma unroll
+  for (int p = 0; p < CH; ++p) tc::split2(val(2 * (C0 + p)), val(2 * (C0 + p) + 1), hi[p], lo[p]);
+  tmem_store_cols<CH>(t_hi + C0, hi);
+  tmem_store_cols<CH>(t_lo + C0, lo);
+  if constexpr (NC > CH) split_store_fn<NC - CH, C0 + CH>(val, t_hi, t_lo);
 }
 
 template <int NC>
@@ -200,11 +214,11 @@ __global__ void __launch_bounds__(TcDims<N>::THREADS, 1) tc_stage_kernel(const S
   float* sG = reinterpret_cast<float*>(smem + D::OFF_G);
   float* sR = reinterpret_cast<float*>(smem + D::OFF_R);
   float* sF = reinterpret_cast<float*>(smem + D::OFF_F);
-  float* sMax = reinterpret_cast<float*>(smem + D::OFF_MAX);
   float* sScale = reinterpret_cast<float*>(smem + D::OFF_SC);
+  float* sBound = reinterpret_cast<float*>(smem + D::OFF_BND);
+  uint16_t* sInfo = reinterpret_cast<uint16_t*>(smem + D::OFF_INFO);
   unsigned char* sFmask = smem + D::OFF_TAB;
   unsigned char* sPerm = sFmask + 4 * Nfp;
-  uint32_t* sItem = reinterpret_cast<uint32_t*>(smem + D::OFF_IT);
 
   // ---- set-up: B pieces, tables, tensor memory, barriers -------------------
   {
@@ -213,13 +227,6 @@ __global__ void __launch_bounds__(TcDims<N>::THREADS, 1) tc_stage_kernel(const S
     for (int i = tid; i < 2 * D::B_BYTES / 16; i += D::THREADS) dst[i] = __ldg(src + i);
     for (int i = tid; i < 4 * Nfp; i += D::THREADS) sFmask[i] = __ldg(A.fmask + i);
     for (int i = tid; i < 96 * Nfp; i += D::THREADS) sPerm[i] = __ldg(A.perm + i);
-    // flux item idx -> e | m << 5 | f << 13 | j << 15 | idM << 21, the face nodes of
-    // one element consecutive (a warp's gathers share neighbour blocks)
-    for (int idx = tid; idx < E * NF; idx += D::THREADS) {
-      const int m = idx % NF, e = idx / NF, f = m / Nfp, j = m - f * Nfp;
-      sItem[idx] = uint32_t(e) | uint32_t(m) << 5 | uint32_t(f) << 13 | uint32_t(j) << 15 |
-                   uint32_t(__ldg(A.fmask + f * Nfp + j)) << 21;
-    }
   }
   tc::fence_proxy_async_smem();
   if (warp == 0) tc::tmem_alloc(&s_tmem, 512);
@@ -244,8 +251,8 @@ __global__ void __launch_bounds__(TcDims<N>::THREADS, 1) tc_stage_kernel(const S
     const int row = warp * 32 + lane;
     const int rc = row / E, re = row - (row / E) * E;
     const uint32_t lane_off = uint32_t(warp * 32) << 16;
-    if (warp == 0 && tc::elect_one()) {   // first loads: fields of tiles 0..2, res of tile 0
-      for (int t = 0; t < 3 && t < ntiles; ++t)
+    if (warp == 0 && tc::elect_one()) {   // first loads: fields of tiles 0..NSU-2, res of tile 0
+      for (int t = 0; t < D::NSU - 1 && t < ntiles; ++t)
         tc_load_u<N>(A, blockIdx.x + t * gridDim.x, sU + t * D::U_FLOATS, sG + t * D::G_FLOATS,
                      &s_u_full[t]);
       if (RK) tc_load_res<N>(A, blockIdx.x, sR, &s_r_full[0]);
@@ -319,13 +326,13 @@ __global__ void __launch_bounds__(TcDims<N>::THREADS, 1) tc_stage_kernel(const S
             }
           }
           tc::bulk_commit();
-          // slots of tile t-1 (stored one round ago) take tiles t+3 and t+1
+          // slots of tile t-1 (stored one round ago) take tiles t+NSU-1 and t+1
           asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
           tc::fence_proxy_async_smem();
-          if (t + 3 < ntiles) {
-            const int s = (t + 3) % D::NSU;
-            tc_load_u<N>(A, tile + 3 * gridDim.x, sU + s * D::U_FLOATS, sG + s * D::G_FLOATS,
-                         &s_u_full[s]);
+          if (t + D::NSU - 1 < ntiles) {
+            const int s = (t + D::NSU - 1) % D::NSU;
+            tc_load_u<N>(A, tile + (D::NSU - 1) * gridDim.x, sU + s * D::U_FLOATS,
+                         sG + s * D::G_FLOATS, &s_u_full[s]);
           }
           if (RK && t + 1 < ntiles) {
             const int s = (t + 1) % D::NSR;
@@ -339,6 +346,8 @@ __global__ void __launch_bounds__(TcDims<N>::THREADS, 1) tc_stage_kernel(const S
     __syncwarp();
   } else if (warp < 8) {
     // ============================== flux warps =================================
+    // Item idx = ft + q * 128 is face node m of element e (idx = e * NF + m), so a
+    // warp's items are consecutive face nodes of one or two elements.
     const int ft = tid - 128;
     for (int t = 0; t < ntiles; ++t) {
       const int tile = blockIdx.x + t * gridDim.x;
@@ -349,70 +358,60 @@ __global__ void __launch_bounds__(TcDims<N>::THREADS, 1) tc_stage_kernel(const S
       float* F = sF + fb * D::F_FLOATS;
       wait_or_flag(&s_u_full[slot], (t / D::NSU) & 1, A.status);
       if (t >= 2) wait_or_flag(&s_f_empty[fb], ((t - 2) >> 1) & 1, A.status);
-      // step 1: classify items, load neighbour values that leave the tile
-      uint32_t item[D::ITEMS];
-      int kind[D::ITEMS];          // 0 none, 1 wall, 2 in tile (ofs), 3 loaded
-      int ofs[D::ITEMS];
-      float uP[D::ITEMS][6];
-#pragma unroll
+      // classify every item (0 none, 1 wall, 2 neighbour in the tile, 3 neighbour
+      // outside it) and start the gathers of kind 3: the six neighbour values go
+      // by 4-byte asynchronous copies into the flux-buffer words this item's flux
+      // will overwrite, so they need no registers and no extra shared memory
+#pragma unroll 2
       for (int q = 0; q < D::ITEMS; ++q) {
         const int idx = ft + q * D::FLUX_THREADS;
-        kind[q] = 0;
-        ofs[q] = 0;
-        item[q] = 0;
-        if (idx < E * NF) {
-          const uint32_t it = sItem[idx];
-          item[q] = it;
-          const int e = it & 31, f = (it >> 13) & 3, jj = (it >> 15) & 63;
-          if (e < Ev) {
-            const unsigned code = (__float_as_uint(sg[9 * E + e]) >> (8 * f)) & 0xffu;
-            if (code == 0u) {
-              kind[q] = 1;
-            } else {
-              const int k2 = __float_as_int(sg[(26 + f) * E + e]);
-              const int i2 = sPerm[(f * 24 + int(code) - 1) * Nfp + jj];
-              const int e2 = k2 - k0;
-              if (e2 >= 0 && e2 < Ev) {
-                kind[q] = 2;
-                ofs[q] = e2 * Np + i2;
-              } else {
-                kind[q] = 3;
-                const float* src = A.u_in + size_t(k2) * Np + i2;
+        const int e = idx / NF, m = idx - e * NF, f = m / Nfp, jj = m - f * Nfp;
+        const bool ok = idx < E * NF && e < Ev;
+        const int ec = ok ? e : 0;
+        const unsigned code = ok ? (__float_as_uint(sg[9 * E + ec]) >> (8 * f)) & 0xffu : 0u;
+        const int k2 = __float_as_int(sg[(26 + f) * E + ec]);
+        const int i2 = code ? sPerm[(f * 24 + int(code) - 1) * Nfp + jj] : 0;
+        const int e2 = k2 - k0;
+        const bool in_tile = unsigned(e2) < unsigned(Ev);
+        const uint32_t kind = !ok ? 0u : code == 0u ? 1u : in_tile ? 2u : 3u;
+        if (kind == 3u) {
+          const float* src = A.u_in + size_t(k2) * Np + i2;
 #pragma unroll
-                for (int c = 0; c < 6; ++c) uP[q][c] = __ldg(src + size_t(c) * K * Np);
-              }
-            }
-          }
+          for (int c = 0; c < 6; ++c)
+            tc::cp_async4(F + (c * E + e) * FSTR + m, src + size_t(c) * K * Np);
         }
+        const int ofs = kind == 2u ? e2 * Np + i2 : ec * Np + sFmask[m];
+        sInfo[q * D::FLUX_THREADS + ft] = uint16_t(kind | uint32_t(ofs) << 2);
       }
-      // step 2: upwind flux of every face node
-#pragma unroll
+      tc::cp_async_commit();
+      tc::cp_async_wait_all();
+      // upwind flux of every face node (PEC ghost state E+ = -E-, H+ = H- on walls)
+      const float al = A.alpha;
+#pragma unroll 2
       for (int q = 0; q < D::ITEMS; ++q) {
-        if (kind[q] == 0) continue;
-        const uint32_t it = item[q];
-        const int e = it & 31, m = (it >> 5) & 255, f = (it >> 13) & 3, idM = it >> 21;
+        const uint32_t info = sInfo[q * D::FLUX_THREADS + ft];
+        const uint32_t kind = info & 3u;
+        if (kind == 0u) continue;
+        const int idx = ft + q * D::FLUX_THREADS;
+        const int e = idx / NF, m = idx - e * NF, f = m / Nfp;
+        const int idM = sFmask[m];
+        float* fr = F + e * FSTR + m;
+        const float* pp = kind == 3u ? fr : su + (info >> 2);
+        const int ps = kind == 3u ? E * FSTR : E * Np;
         float uM[6], up[6];
 #pragma unroll
-        for (int c = 0; c < 6; ++c) uM[c] = su[(c * E + e) * Np + idM];
-        if (kind[q] == 1) {
-#pragma unroll
-          for (int c = 0; c < 3; ++c) { up[c] = -uM[c]; up[c + 3] = uM[c + 3]; }
-        } else if (kind[q] == 2) {
-#pragma unroll
-          for (int c = 0; c < 6; ++c) up[c] = su[c * E * Np + ofs[q]];
-        } else {
-#pragma unroll
-          for (int c = 0; c < 6; ++c) up[c] = uP[q][c];
+        for (int c = 0; c < 6; ++c) {
+          uM[c] = su[(c * E + e) * Np + idM];
+          up[c] = pp[c * ps];
         }
+        const float we = kind == 1u ? -1.f : 1.f;
         const float sc = 0.5f * sg[(13 + 4 * f) * E + e];
         const float nx = sg[(10 + 4 * f) * E + e], ny = sg[(11 + 4 * f) * E + e];
         const float nz = sg[(12 + 4 * f) * E + e];
-        const float dEx = uM[0] - up[0], dEy = uM[1] - up[1], dEz = uM[2] - up[2];
+        const float dEx = uM[0] - we * up[0], dEy = uM[1] - we * up[1], dEz = uM[2] - we * up[2];
         const float dHx = uM[3] - up[3], dHy = uM[4] - up[4], dHz = uM[5] - up[5];
         const float ndE = nx * dEx + ny * dEy + nz * dEz;
         const float ndH = nx * dHx + ny * dHy + nz * dHz;
-        const float al = A.alpha;
-        float* fr = F + e * FSTR + m;
         fr[0 * E * FSTR] = sc * (-(ny * dHz - nz * dHy) + al * (nx * ndE - dEx));
         fr[1 * E * FSTR] = sc * (-(nz * dHx - nx * dHz) + al * (ny * ndE - dEy));
         fr[2 * E * FSTR] = sc * (-(nx * dHy - ny * dHx) + al * (nz * ndE - dEz));
@@ -424,88 +423,92 @@ __global__ void __launch_bounds__(TcDims<N>::THREADS, 1) tc_stage_kernel(const S
     }
   } else {
     // ============================= builder warps ===============================
+    // Two warps per tensor-memory lane quarter: part 0 builds the g^r, g^s, g^t
+    // blocks of its 32 rows, part 1 the flux block.
     const int bw = warp - 8;
-    const int quarter = bw & 3, part = bw >> 2;     // part 0: g^r, g^s; part 1: g^t + flux
+    const int quarter = bw & 3, part = bw >> 2;
     const int row = quarter * 32 + lane;
     const int rc = row / E, re = row - (row / E) * E;
     const uint32_t lane_off = uint32_t(quarter * 32) << 16;
+    const int o = rc % 3;                                  // curl: field c takes fields fa, fb
+    const int fa = rc < 3 ? 3 + (o + 2) % 3 : (o + 2) % 3;
+    const int fb = rc < 3 ? 3 + (o + 1) % 3 : (o + 1) % 3;
+    const float sgn = rc < 3 ? 1.f : -1.f;
     for (int t = 0; t < ntiles; ++t) {
       const int tile = blockIdx.x + t * gridDim.x;
-      const int k0 = tile * E, Ev = min(E, K - k0);
+      const int Ev = min(E, K - tile * E);
       const int slot = t % D::NSU, buf = t & 1;
       const float* su = sU + slot * D::U_FLOATS;
       const float* sg = sG + slot * D::G_FLOATS;
-      (void)k0;
-      wait_or_flag(&s_u_full[slot], (t / D::NSU) & 1, A.status);
       const bool live = row < D::ROWS && re < Ev;
-      // g^mu values of this row: part 0 mu = 0, 1; part 1 mu = 2
-      float v[2 * D::KB];
-      float mx = 0.f;
-      {
-        const int o = rc % 3;
-        const int fa = rc < 3 ? 3 + (o + 2) % 3 : (o + 2) % 3;
-        const int fb = rc < 3 ? 3 + (o + 1) % 3 : (o + 1) % 3;
-        const float sgn = rc < 3 ? 1.f : -1.f;
-        const float* ua = su + (fa * E + re) * Np;
-        const float* ub = su + (fb * E + re) * Np;
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          const int mu = part == 0 ? h : 2;
-          if (part == 1 && h == 1) break;
-          const float ca = live ? sgn * sg[(3 * mu + (o + 1) % 3) * E + re] : 0.f;
-          const float cb = live ? -sgn * sg[(3 * mu + (o + 2) % 3) * E + re] : 0.f;
-#pragma unroll
-          for (int jj = 0; jj < D::KB; ++jj) {
-            const float g = (live && jj < Np) ? fmaf(ca, ua[jj], cb * ub[jj]) : 0.f;
-            v[h * D::KB + jj] = g;
-            mx = fmaxf(mx, fabsf(g));
-          }
-        }
-      }
-      // flux rows (part 1): first pass for the row maximum
-      const float* F = sF + buf * D::F_FLOATS;
-      const float* frow = F + (rc * E + re) * FSTR;
-      if (part == 1) {
-        wait_or_flag(&s_f_full[buf], (t >> 1) & 1, A.status);
-        if (live) {
-#pragma unroll 4
-          for (int m = 0; m < NF; ++m) mx = fmaxf(mx, fabsf(frow[m]));
-        }
-      }
-      // A[buf] is free once the MMAs of tile t-2 have completed
-      if (t >= 2) wait_or_flag(&s_mma_done[buf], ((t - 2) >> 1) & 1, A.status);
-      tc::fence_after_sync();
-      sMax[part * 128 + row] = mx;
-      named_sync(2, 256);
-      const float s = row_scale(fmaxf(sMax[row], sMax[128 + row]));
-      if (part == 0) sScale[(t & 3) * 128 + row] = s;
       const uint32_t a_hi = tbase + lane_off + buf * D::BUF_COLS;
       const uint32_t a_lo = a_hi + D::ACOLS;
       if (part == 0) {
-        split_store<2 * D::COLS_G>(v, s, a_hi, a_lo);
-      } else {
-        split_store<D::COLS_G>(v, s, a_hi + 2 * D::COLS_G, a_lo + 2 * D::COLS_G);
-        // flux rows, second pass, 32 values (16 columns) at a time
+        // the two fields of the row's curl, kept in registers for all three mu
+        wait_or_flag(&s_u_full[slot], (t / D::NSU) & 1, A.status);
+        float ua[Np], ub[Np];
+        float umax = 0.f, cmax = 0.f;
+        const float* pa = su + (fa * E + re) * Np;
+        const float* pb = su + (fb * E + re) * Np;
 #pragma unroll
-        for (int c0 = 0; c0 < D::COLS_F; c0 += 16) {
-          float w[32];
-#pragma unroll
-          for (int q = 0; q < 32; ++q) {
-            const int m = 2 * c0 + q;
-            w[q] = (live && m < NF) ? frow[m] : 0.f;
-          }
-          if (c0 + 16 <= D::COLS_F) {
-            split_store<16>(w, s, a_hi + 3 * D::COLS_G + c0, a_lo + 3 * D::COLS_G + c0);
-          } else {
-            split_store<D::COLS_F % 16>(w, s, a_hi + 3 * D::COLS_G + c0,
-                                        a_lo + 3 * D::COLS_G + c0);
-          }
+        for (int j = 0; j < Np; ++j) {
+          ua[j] = live ? pa[j] : 0.f;
+          ub[j] = live ? pb[j] : 0.f;
+          umax = fmaxf(umax, fmaxf(fabsf(ua[j]), fabsf(ub[j])));
         }
-        tc::mbar_arrive(&s_f_empty[buf]);
+        if (live) {
+#pragma unroll
+          for (int mu = 0; mu < 3; ++mu)
+            cmax = fmaxf(cmax, fabsf(sg[(3 * mu + (o + 1) % 3) * E + re]) +
+                                   fabsf(sg[(3 * mu + (o + 2) % 3) * E + re]));
+        }
+        // |g^mu| <= (|r_mu,a| + |r_mu,b|) max(max|U_a|, max|U_b|)
+        sBound[row] = cmax * umax;
+        named_sync(2, 256);
+        const float s = row_scale(fmaxf(sBound[row], sBound[128 + row]));
+        named_sync(2, 256);                              // bounds read by everyone
+        // A[buf] is free once the MMAs of tile t-2 have completed
+        if (t >= 2) wait_or_flag(&s_mma_done[buf], ((t - 2) >> 1) & 1, A.status);
+        tc::fence_after_sync();
+        sScale[(t & 3) * 128 + row] = s;
+        // the scale goes on the fields, not on the metric terms: s may be as large
+        // as 2^127 for a row of tiny values, while |U s| < 2^15 / (|r_a| + |r_b|)
+#pragma unroll
+        for (int j = 0; j < Np; ++j) {
+          ua[j] *= s;
+          ub[j] *= s;
+        }
+#pragma unroll 1
+        for (int mu = 0; mu < 3; ++mu) {
+          const float ca = live ? sgn * sg[(3 * mu + (o + 1) % 3) * E + re] : 0.f;
+          const float cb = live ? -sgn * sg[(3 * mu + (o + 2) % 3) * E + re] : 0.f;
+          split_store_fn<D::COLS_G>(
+              [&](int j) { return j < Np ? fmaf(ca, ua[j], cb * ub[j]) : 0.f; },
+              a_hi + mu * D::COLS_G, a_lo + mu * D::COLS_G);
+        }
+      } else {
+        // the flux row, kept in registers from the bound to the split
+        wait_or_flag(&s_f_full[buf], (t >> 1) & 1, A.status);
+        const float* frow = sF + buf * D::F_FLOATS + (rc * E + re) * FSTR;
+        float w[D::KF];
+        float fmax = 0.f;
+#pragma unroll
+        for (int m = 0; m < D::KF; ++m) {
+          w[m] = (live && m < NF) ? frow[m] : 0.f;
+          fmax = fmaxf(fmax, fabsf(w[m]));
+        }
+        sBound[128 + row] = fmax;
+        named_sync(2, 256);
+        const float s = row_scale(fmaxf(sBound[row], sBound[128 + row]));
+        named_sync(2, 256);
+        tc::mbar_arrive(&s_f_empty[buf]);                // flux row now in registers
+        if (t >= 2) wait_or_flag(&s_mma_done[buf], ((t - 2) >> 1) & 1, A.status);
+        tc::fence_after_sync();
+        split_store_fn<D::COLS_F>([&](int m) { return w[m] * s; }, a_hi + 3 * D::COLS_G,
+                                  a_lo + 3 * D::COLS_G);
       }
       tc::tmem_st_wait();
       tc::fence_before_sync();
-      named_sync(2, 256);          // sMax reused next tile; all A columns written
       tc::mbar_arrive(&s_a_full[buf]);
     }
   }

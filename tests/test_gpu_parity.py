@@ -112,6 +112,48 @@ def test_step_parity_both_implementations(env, impl):
     assert rel(u.cpu().numpy(), ue) < STEP_TOL
 
 
+def test_step_parity_several_tiles_per_cta(env):
+    """K = 10 368 tets = 519 tiles of 20: every persistent CTA of the
+    tensor-core stage runs its tile pipeline over several tiles (the smaller
+    meshes give each CTA one tile)."""
+    torch, dg = env
+    verts, tets = kuhn_box_mesh(12, 0.15, 5)
+    mesh, om = _setup(dg, verts, tets, 4)
+    mesh.set_stage_impl(TC)
+    u0 = random_fields(om.K, om.Np, 41).astype(np.float32)
+    u = torch.from_numpy(u0).cuda()
+    res = torch.zeros_like(u)
+    mesh.trace_enable(10)
+    mesh.step(u, res, mesh.dt_cfl, 2)
+    torch.cuda.synchronize()
+    assert _stage_kinds(mesh) == {4}
+    ue, _ = oracle.lserk4_run(om, u0.astype(np.float64), mesh.dt_cfl, 2)
+    assert rel(u.cpu().numpy(), ue) < STEP_TOL
+
+
+def test_tc_rows_of_every_magnitude(env):
+    """Per-element magnitudes from exact zero through 1e-37 (the row scale hits
+    its 2^127 clamp) to 1e20, several tiles per CTA: every value finite and each
+    magnitude class within the one-RHS tolerance of the oracle."""
+    torch, dg = env
+    verts, tets = kuhn_box_mesh(12, 0.15, 6)
+    mesh, om = _setup(dg, verts, tets, 4)
+    rng = np.random.Generator(np.random.PCG64(31))
+    scales = np.array([0.0, 1e-37, 1e-30, 1e-3, 1.0, 1e20])
+    cls = rng.integers(0, len(scales), om.K)
+    u32 = (random_fields(om.K, om.Np, 32) * scales[cls][None, :, None]).astype(np.float32)
+    mesh.trace_enable(4)
+    got = _gpu_rhs(torch, mesh, u32, impl=TC)
+    assert _stage_kinds(mesh) == {5}
+    mesh.set_stage_impl(0)
+    want = oracle.rhs(om, u32.astype(np.float64))
+    assert np.isfinite(got).all()
+    for k in range(len(scales)):
+        sel = cls == k
+        if np.any(want[:, sel]):
+            assert rel(got[:, sel], want[:, sel]) < RHS_TOL, scales[k]
+
+
 @pytest.mark.parametrize("N", [2, 4, 6])
 def test_rhs_parity_smooth_fields_and_central_flux(env, N):
     torch, dg = env
@@ -277,6 +319,26 @@ def test_full_size_tc_matches_fp32_everywhere(env, full):
     mesh.set_stage_impl(0)
     assert np.isfinite(a).all()
     assert rel(a, b.astype(np.float64)) < 2 * RHS_TOL
+
+
+def test_full_size_pure_pulse_step_both_implementations(env, full):
+    """The Gaussian pulse alone (H = 0, E underflowing to zero far from the
+    centre), one LSERK4 step at full size: the two stage implementations agree
+    everywhere and every value stays finite."""
+    torch, dg = env
+    verts, tets, mesh, _ = full
+    x = mesh.nodes()
+    u0 = gaussian_pulse(x[0], x[1], x[2], 0.2, pulse_center(1)).astype(np.float32)
+    out = []
+    for impl in (TC, FP32):
+        mesh.set_stage_impl(impl)
+        u = torch.from_numpy(u0).cuda()
+        res = torch.zeros_like(u)
+        mesh.step(u, res, mesh.dt_cfl, 1)
+        out.append(u.cpu().numpy())
+    mesh.set_stage_impl(0)
+    assert np.isfinite(out[0]).all()
+    assert rel(out[0], out[1].astype(np.float64)) < RHS_TOL
 
 
 def test_full_size_step_sampled(env, full):
