@@ -322,18 +322,28 @@ int ensure_device(dg_mesh* m, std::string& err) {
         P[piece + off] = lo;
       }
     if ((rc = upload(reinterpret_cast<__half**>(&d->tcB), P, err))) return rc;
-    // tiled word-major geometry, one contiguous [kTcGeoWords][E] block per tile:
-    // record words {0..8 metric, 10 codes, 12..27 faces, 28..31 neighbours} ->
-    // words {0..8, 9, 10..25, 26..29}
+    // tiled geometry, one contiguous block per tile: word-major [kTcGeoWords][E]
+    // (record words {0..8 metric, 10 codes, 12..27 faces, 28..31 neighbours} ->
+    // words {0..8, 9, 10..25, 26..29}), then one byte per face node (e, m):
+    // the node of the neighbour across face m / Nfp that matches it (0 on walls)
     constexpr int E = dgdev::kTcTileElems;
     const int64_t ntiles = (K + E - 1) / E;
-    d->tc_geo_stride = dgdev::kTcGeoWords * E;
-    std::vector<float> tg(static_cast<size_t>(ntiles) * dgdev::kTcGeoWords * E, 0.f);
-    for (int64_t k = 0; k < K; ++k)
+    d->tc_geo_stride = dgdev::tc_geo_floats(d->N);
+    std::vector<float> tg(static_cast<size_t>(ntiles) * d->tc_geo_stride, 0.f);
+    for (int64_t k = 0; k < K; ++k) {
+      float* blk = &tg[(k / E) * d->tc_geo_stride];
       for (int w = 0; w < dgdev::kTcGeoWords; ++w) {
         const int src = w < 9 ? w : (w == 9 ? 10 : w + 2);
-        tg[((k / E) * dgdev::kTcGeoWords + w) * E + k % E] = geo[k * dgdev::kGeoWords + src];
+        blk[w * E + k % E] = geo[k * dgdev::kGeoWords + src];
       }
+      unsigned char* nodes = reinterpret_cast<unsigned char*>(blk + dgdev::kTcGeoWords * E);
+      for (int f = 0; f < 4; ++f) {
+        const int c = m->nbr_code[4 * k + f];
+        for (int j = 0; j < Nfp; ++j)
+          nodes[(k % E) * NF + f * Nfp + j] =
+              c < 0 ? 0 : static_cast<unsigned char>(m->ops.perm[(f * 24 + c) * Nfp + j]);
+      }
+    }
     if ((rc = upload(&d->tcgeo, tg, err))) return rc;
   }
   DG_CUDA(cudaMalloc(&d->status, sizeof(int)), "cudaMalloc");

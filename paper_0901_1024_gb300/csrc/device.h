@@ -51,6 +51,11 @@ constexpr int kTcTileElems = 20;
 // neighbour element of face f.
 constexpr int kTcGeoWords = 30;
 constexpr int kTcMaxOrder = 4;
+// Floats of one tile's geometry block: kTcGeoWords x kTcTileElems words, then
+// kTcTileElems * 4 Nfp neighbour-node bytes (a multiple of 16 bytes).
+__host__ __device__ constexpr int tc_geo_floats(int N) {
+  return kTcGeoWords * kTcTileElems + kTcTileElems * 4 * ((N + 1) * (N + 2) / 2) / 4;
+}
 // Bytes of the prepared B buffer for order N (two FP16 pieces of NN x KT).
 __host__ __device__ constexpr int tc_b_bytes(int N) {
   return 2 * 2 * ((((N + 1) * (N + 2) * (N + 3) / 6) + 15) & ~15) *

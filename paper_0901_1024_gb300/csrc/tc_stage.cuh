@@ -61,13 +61,13 @@ template <int N> struct TcDims {
   static constexpr int COLS_G = KB / 2;               // columns of one mu block
   static constexpr int COLS_F = KF / 2;               // columns of the flux block
   static constexpr int FSTR = NF | 1;                 // flux buffer row stride (odd)
-  static constexpr int THREADS = 512;                 // 4 epilogue + 4 flux + 8 builder warps
-  static constexpr int FLUX_THREADS = 128;
-  static constexpr int ITEMS = (E * NF + FLUX_THREADS - 1) / FLUX_THREADS;  // per flux thread
+  static constexpr int THREADS = 512;                 // 4 epilogue + 12 producer warps
+  static constexpr int PRODUCERS = 384;
+  static constexpr int ITEMS = (E * NF + PRODUCERS - 1) / PRODUCERS;   // flux items per producer
   static constexpr int NSU = 5, NSR = 2;              // ring slots: fields+geometry, RK register
   // shared memory (bytes)
   static constexpr int U_FLOATS = 6 * E * Np;         // one tile of one state array
-  static constexpr int G_FLOATS = E * kTcGeoWords;    // word-major [w][E]
+  static constexpr int G_FLOATS = tc_geo_floats(N);  // word-major [w][E], node bytes
   static constexpr int F_FLOATS = ROWS * FSTR;
   static constexpr int B_BYTES = NN * KT * 2;         // one FP16 piece
   static constexpr int TAB_BYTES = (4 * Nfp + 96 * Nfp + 15) & ~15;
@@ -75,20 +75,21 @@ template <int N> struct TcDims {
   static constexpr int OFF_U = OFF_B + 2 * B_BYTES;   // NSU slots
   static constexpr int OFF_G = OFF_U + NSU * U_FLOATS * 4;
   static constexpr int OFF_R = OFF_G + NSU * G_FLOATS * 4;   // NSR slots
-  static constexpr int OFF_F = OFF_R + NSR * U_FLOATS * 4;   // 2 buffers
-  static constexpr int OFF_BND = OFF_F + 2 * F_FLOATS * 4;     // [2 parts][128] row bounds
+  static constexpr int OFF_F = OFF_R + NSR * U_FLOATS * 4;   // one flux buffer
+  static constexpr int OFF_BND = OFF_F + F_FLOATS * 4;         // [2 parts][128] row bounds
   static constexpr int OFF_SC = OFF_BND + 2 * 128 * 4;       // [4][128] row scales
-  static constexpr int OFF_INFO = OFF_SC + 4 * 128 * 4;      // [ITEMS][128] u16 item kinds
-  static constexpr int OFF_TAB = OFF_INFO + ((ITEMS * FLUX_THREADS * 2 + 15) & ~15);
+  static constexpr int OFF_TAB = OFF_SC + 4 * 128 * 4;
   static constexpr int SMEM = OFF_TAB + TAB_BYTES;
   static_assert((U_FLOATS * 4) % 16 == 0 && (E * Np * 4) % 16 == 0, "bulk-copy alignment");
   static_assert(OFF_U % 16 == 0 && OFF_R % 16 == 0 && OFF_G % 16 == 0 && OFF_F % 16 == 0 &&
-                OFF_TAB % 16 == 0 && OFF_INFO % 16 == 0, "alignment");
+                OFF_TAB % 16 == 0, "alignment");
   static_assert((G_FLOATS * 4) % 16 == 0, "geometry block must be a 16-byte multiple");
   static_assert(SMEM <= 226 * 1024, "shared memory budget");
 };
 
 static_assert(tc_b_bytes(4) == 2 * TcDims<4>::B_BYTES, "B buffer size formula");
+static_assert(TcDims<4>::G_FLOATS == kTcGeoWords * kTcTileElems + kTcTileElems * TcDims<4>::NF / 4,
+              "geometry block size");
 
 template <int NC>
 __device__ __forceinline__ void tmem_store_cols(uint32_t taddr, const uint32_t* v) {
@@ -203,7 +204,7 @@ __global__ void __launch_bounds__(TcDims<N>::THREADS, 1) tc_stage_kernel(const S
   __shared__ uint32_t s_tmem;
   __shared__ __align__(8) uint64_t s_u_full[D::NSU];
   __shared__ __align__(8) uint64_t s_r_full[D::NSR];
-  __shared__ __align__(8) uint64_t s_f_full[2], s_f_empty[2], s_a_full[2], s_mma_done[2];
+  __shared__ __align__(8) uint64_t s_a_full[2], s_mma_done[2];
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int K = A.K;
@@ -216,7 +217,6 @@ __global__ void __launch_bounds__(TcDims<N>::THREADS, 1) tc_stage_kernel(const S
   float* sF = reinterpret_cast<float*>(smem + D::OFF_F);
   float* sScale = reinterpret_cast<float*>(smem + D::OFF_SC);
   float* sBound = reinterpret_cast<float*>(smem + D::OFF_BND);
-  uint16_t* sInfo = reinterpret_cast<uint16_t*>(smem + D::OFF_INFO);
   unsigned char* sFmask = smem + D::OFF_TAB;
   unsigned char* sPerm = sFmask + 4 * Nfp;
 
@@ -234,9 +234,7 @@ __global__ void __launch_bounds__(TcDims<N>::THREADS, 1) tc_stage_kernel(const S
     for (int i = 0; i < D::NSU; ++i) tc::mbar_init(&s_u_full[i], 1);
     for (int i = 0; i < D::NSR; ++i) tc::mbar_init(&s_r_full[i], 1);
     for (int i = 0; i < 2; ++i) {
-      tc::mbar_init(&s_f_full[i], D::FLUX_THREADS);
-      tc::mbar_init(&s_f_empty[i], 128);          // the builder warps reading flux rows
-      tc::mbar_init(&s_a_full[i], 256);           // all builder threads
+      tc::mbar_init(&s_a_full[i], D::PRODUCERS);  // every producer thread stores A columns
       tc::mbar_init(&s_mma_done[i], 1);
     }
     tc::fence_mbar_init();
@@ -299,17 +297,34 @@ __global__ void __launch_bounds__(TcDims<N>::THREADS, 1) tc_stage_kernel(const S
         tc::fence_before_sync();
         if (row < D::ROWS && re < Ev) {
           const float inv = A.tc_inv_bscale / sScale[(t & 3) * 128 + row];
-          const int base = (rc * E + re) * Np;
+          float* pr = sr + (rc * E + re) * Np;
+          float* pu = su + (rc * E + re) * Np;
+          // u and res share one shared array, so every batch is loaded before any
+          // of its stores (the compiler cannot move loads across them)
+          constexpr int CH = 12;
 #pragma unroll
-          for (int i = 0; i < Np; ++i) {
-            const float r = __uint_as_float(acc[i]) * inv;
+          for (int i0 = 0; i0 < Np; i0 += CH) {
+            float rv[CH], uv[CH];
             if (RK) {
-              const float rn = fmaf(A.a, sr[base + i], A.dt * r);
-              sr[base + i] = rn;
-              su[base + i] = fmaf(A.b, rn, su[base + i]);
-            } else {
-              sr[base + i] = r;
+#pragma unroll
+              for (int i = 0; i < CH; ++i)
+                if (i0 + i < Np) {
+                  rv[i] = pr[i0 + i];
+                  uv[i] = pu[i0 + i];
+                }
             }
+#pragma unroll
+            for (int i = 0; i < CH; ++i)
+              if (i0 + i < Np) {
+                const float r = __uint_as_float(acc[i0 + i]) * inv;
+                if (RK) {
+                  const float rn = fmaf(A.a, rv[i], A.dt * r);
+                  pr[i0 + i] = rn;
+                  pu[i0 + i] = fmaf(A.b, rn, uv[i]);
+                } else {
+                  pr[i0 + i] = r;
+                }
+              }
           }
         }
         tc::fence_proxy_async_smem();
@@ -344,89 +359,13 @@ __global__ void __launch_bounds__(TcDims<N>::THREADS, 1) tc_stage_kernel(const S
     }
     if (warp == 0 && tc::elect_one()) tc::bulk_wait_all();
     __syncwarp();
-  } else if (warp < 8) {
-    // ============================== flux warps =================================
-    // Item idx = ft + q * 128 is face node m of element e (idx = e * NF + m), so a
-    // warp's items are consecutive face nodes of one or two elements.
-    const int ft = tid - 128;
-    for (int t = 0; t < ntiles; ++t) {
-      const int tile = blockIdx.x + t * gridDim.x;
-      const int k0 = tile * E, Ev = min(E, K - k0);
-      const int slot = t % D::NSU, fb = t & 1;
-      const float* su = sU + slot * D::U_FLOATS;
-      const float* sg = sG + slot * D::G_FLOATS;
-      float* F = sF + fb * D::F_FLOATS;
-      wait_or_flag(&s_u_full[slot], (t / D::NSU) & 1, A.status);
-      if (t >= 2) wait_or_flag(&s_f_empty[fb], ((t - 2) >> 1) & 1, A.status);
-      // classify every item (0 none, 1 wall, 2 neighbour in the tile, 3 neighbour
-      // outside it) and start the gathers of kind 3: the six neighbour values go
-      // by 4-byte asynchronous copies into the flux-buffer words this item's flux
-      // will overwrite, so they need no registers and no extra shared memory
-#pragma unroll 2
-      for (int q = 0; q < D::ITEMS; ++q) {
-        const int idx = ft + q * D::FLUX_THREADS;
-        const int e = idx / NF, m = idx - e * NF, f = m / Nfp, jj = m - f * Nfp;
-        const bool ok = idx < E * NF && e < Ev;
-        const int ec = ok ? e : 0;
-        const unsigned code = ok ? (__float_as_uint(sg[9 * E + ec]) >> (8 * f)) & 0xffu : 0u;
-        const int k2 = __float_as_int(sg[(26 + f) * E + ec]);
-        const int i2 = code ? sPerm[(f * 24 + int(code) - 1) * Nfp + jj] : 0;
-        const int e2 = k2 - k0;
-        const bool in_tile = unsigned(e2) < unsigned(Ev);
-        const uint32_t kind = !ok ? 0u : code == 0u ? 1u : in_tile ? 2u : 3u;
-        if (kind == 3u) {
-          const float* src = A.u_in + size_t(k2) * Np + i2;
-#pragma unroll
-          for (int c = 0; c < 6; ++c)
-            tc::cp_async4(F + (c * E + e) * FSTR + m, src + size_t(c) * K * Np);
-        }
-        const int ofs = kind == 2u ? e2 * Np + i2 : ec * Np + sFmask[m];
-        sInfo[q * D::FLUX_THREADS + ft] = uint16_t(kind | uint32_t(ofs) << 2);
-      }
-      tc::cp_async_commit();
-      tc::cp_async_wait_all();
-      // upwind flux of every face node (PEC ghost state E+ = -E-, H+ = H- on walls)
-      const float al = A.alpha;
-#pragma unroll 2
-      for (int q = 0; q < D::ITEMS; ++q) {
-        const uint32_t info = sInfo[q * D::FLUX_THREADS + ft];
-        const uint32_t kind = info & 3u;
-        if (kind == 0u) continue;
-        const int idx = ft + q * D::FLUX_THREADS;
-        const int e = idx / NF, m = idx - e * NF, f = m / Nfp;
-        const int idM = sFmask[m];
-        float* fr = F + e * FSTR + m;
-        const float* pp = kind == 3u ? fr : su + (info >> 2);
-        const int ps = kind == 3u ? E * FSTR : E * Np;
-        float uM[6], up[6];
-#pragma unroll
-        for (int c = 0; c < 6; ++c) {
-          uM[c] = su[(c * E + e) * Np + idM];
-          up[c] = pp[c * ps];
-        }
-        const float we = kind == 1u ? -1.f : 1.f;
-        const float sc = 0.5f * sg[(13 + 4 * f) * E + e];
-        const float nx = sg[(10 + 4 * f) * E + e], ny = sg[(11 + 4 * f) * E + e];
-        const float nz = sg[(12 + 4 * f) * E + e];
-        const float dEx = uM[0] - we * up[0], dEy = uM[1] - we * up[1], dEz = uM[2] - we * up[2];
-        const float dHx = uM[3] - up[3], dHy = uM[4] - up[4], dHz = uM[5] - up[5];
-        const float ndE = nx * dEx + ny * dEy + nz * dEz;
-        const float ndH = nx * dHx + ny * dHy + nz * dHz;
-        fr[0 * E * FSTR] = sc * (-(ny * dHz - nz * dHy) + al * (nx * ndE - dEx));
-        fr[1 * E * FSTR] = sc * (-(nz * dHx - nx * dHz) + al * (ny * ndE - dEy));
-        fr[2 * E * FSTR] = sc * (-(nx * dHy - ny * dHx) + al * (nz * ndE - dEz));
-        fr[3 * E * FSTR] = sc * ((ny * dEz - nz * dEy) + al * (nx * ndH - dHx));
-        fr[4 * E * FSTR] = sc * ((nz * dEx - nx * dEz) + al * (ny * ndH - dHy));
-        fr[5 * E * FSTR] = sc * ((nx * dEy - ny * dEx) + al * (nz * ndH - dHz));
-      }
-      tc::mbar_arrive(&s_f_full[fb]);
-    }
   } else {
-    // ============================= builder warps ===============================
-    // Two warps per tensor-memory lane quarter: part 0 builds the g^r, g^s, g^t
-    // blocks of its 32 rows, part 1 the flux block.
-    const int bw = warp - 8;
-    const int quarter = bw & 3, part = bw >> 2;
+    // ============================ producer warps ===============================
+    // Warps 4..15 compute the fluxes of tile t together, then build its A rows:
+    // per tensor-memory lane quarter, role 0 (warps 4-7) the g^t block, role 1
+    // (warps 8-11) the g^r and g^s blocks, role 2 (warps 12-15) the flux block.
+    const int pt = tid - 128;
+    const int role = (warp - 4) >> 2, quarter = warp & 3;
     const int row = quarter * 32 + lane;
     const int rc = row / E, re = row - (row / E) * E;
     const uint32_t lane_off = uint32_t(quarter * 32) << 16;
@@ -434,62 +373,103 @@ __global__ void __launch_bounds__(TcDims<N>::THREADS, 1) tc_stage_kernel(const S
     const int fa = rc < 3 ? 3 + (o + 2) % 3 : (o + 2) % 3;
     const int fb = rc < 3 ? 3 + (o + 1) % 3 : (o + 1) % 3;
     const float sgn = rc < 3 ? 1.f : -1.f;
+    // Item idx = pt + q * 384 is face node m of element e (idx = e * NF + m), so
+    // a warp's items are consecutive face nodes of one or two elements.  Their
+    // tile-independent decode: e | m << 5 | f << 12 | idM << 14, bit 31 past the end.
+    uint32_t item[D::ITEMS];
+#pragma unroll
+    for (int q = 0; q < D::ITEMS; ++q) {
+      const int idx = pt + q * D::PRODUCERS;
+      const int e = idx / NF, m = idx - e * NF;
+      item[q] = idx < E * NF ? uint32_t(e) | uint32_t(m) << 5 | uint32_t(m / Nfp) << 12 |
+                                   uint32_t(sFmask[m]) << 14
+                             : 0x80000000u;
+    }
     for (int t = 0; t < ntiles; ++t) {
       const int tile = blockIdx.x + t * gridDim.x;
-      const int Ev = min(E, K - tile * E);
+      const int k0 = tile * E, Ev = min(E, K - k0);
       const int slot = t % D::NSU, buf = t & 1;
       const float* su = sU + slot * D::U_FLOATS;
       const float* sg = sG + slot * D::G_FLOATS;
+      float* F = sF;
+      wait_or_flag(&s_u_full[slot], (t / D::NSU) & 1, A.status);
+      // ---- fluxes (Alg. 2).  Classify every item (0 none, 1 wall, 2 neighbour in
+      // the tile, 3 neighbour outside it) and start the gathers of kind 3: the six
+      // neighbour values go by 4-byte asynchronous copies into the flux-buffer
+      // words this item's flux will overwrite (no registers, no extra space).
+      // F was last read in the build of tile t-1, before its barrier.
+      const unsigned char* nodes = reinterpret_cast<const unsigned char*>(sg + kTcGeoWords * E);
+      uint32_t info[D::ITEMS];          // kind | ofs << 2
+#pragma unroll
+      for (int q = 0; q < D::ITEMS; ++q) {
+        const uint32_t it = item[q];
+        const int e = it & 31, m = (it >> 5) & 127, f = (it >> 12) & 3, idM = (it >> 14) & 63;
+        const bool ok = !(it >> 31) && e < Ev;
+        const int ec = ok ? e : 0;
+        const unsigned code = (__float_as_uint(sg[9 * E + ec]) >> (8 * f)) & 0xffu;
+        const int k2 = __float_as_int(sg[(26 + f) * E + ec]);
+        const int i2 = nodes[ec * NF + m];
+        const int e2 = k2 - k0;
+        const uint32_t kind = !ok ? 0u : code == 0u ? 1u : unsigned(e2) < unsigned(Ev) ? 2u : 3u;
+        if (kind == 3u) {
+          const float* src = A.u_in + size_t(k2) * Np + i2;
+#pragma unroll
+          for (int c = 0; c < 6; ++c)
+            tc::cp_async4(F + (c * E + e) * FSTR + m, src + size_t(c) * K * Np);
+        }
+        info[q] = kind | uint32_t(kind == 2u ? e2 * Np + i2 : ec * Np + idM) << 2;
+      }
+      tc::cp_async_commit();
+      tc::cp_async_wait_all();
+      // upwind flux of every face node (PEC ghost state E+ = -E-, H+ = H- on walls):
+      // every item's operands are loaded before any store into the flux buffer
+      {
+        float uM[D::ITEMS][6], up[D::ITEMS][6], nv[D::ITEMS][4];
+#pragma unroll
+        for (int q = 0; q < D::ITEMS; ++q) {
+          const uint32_t it = item[q], kind = info[q] & 3u;
+          const int e = kind ? int(it & 31) : 0, m = (it >> 5) & 127, f = (it >> 12) & 3;
+          const int idM = (it >> 14) & 63;
+          const float* pp = kind == 3u ? F + e * FSTR + m : su + (info[q] >> 2);
+          const int ps = kind == 3u ? E * FSTR : E * Np;
+#pragma unroll
+          for (int c = 0; c < 6; ++c) {
+            uM[q][c] = su[c * E * Np + e * Np + idM];
+            up[q][c] = pp[c * ps];
+          }
+#pragma unroll
+          for (int w = 0; w < 4; ++w) nv[q][w] = sg[(10 + 4 * f + w) * E + e];
+        }
+        const float al = A.alpha;
+#pragma unroll
+        for (int q = 0; q < D::ITEMS; ++q) {
+          const uint32_t kind = info[q] & 3u;
+          if (kind == 0u) continue;
+          const int e = item[q] & 31, m = (item[q] >> 5) & 127;
+          const float we = kind == 1u ? -1.f : 1.f;
+          const float nx = nv[q][0], ny = nv[q][1], nz = nv[q][2], sc = 0.5f * nv[q][3];
+          const float dEx = uM[q][0] - we * up[q][0], dEy = uM[q][1] - we * up[q][1];
+          const float dEz = uM[q][2] - we * up[q][2];
+          const float dHx = uM[q][3] - up[q][3], dHy = uM[q][4] - up[q][4];
+          const float dHz = uM[q][5] - up[q][5];
+          const float ndE = nx * dEx + ny * dEy + nz * dEz;
+          const float ndH = nx * dHx + ny * dHy + nz * dHz;
+          float* fr = F + e * FSTR + m;
+          fr[0 * E * FSTR] = sc * (-(ny * dHz - nz * dHy) + al * (nx * ndE - dEx));
+          fr[1 * E * FSTR] = sc * (-(nz * dHx - nx * dHz) + al * (ny * ndE - dEy));
+          fr[2 * E * FSTR] = sc * (-(nx * dHy - ny * dHx) + al * (nz * ndE - dEz));
+          fr[3 * E * FSTR] = sc * ((ny * dEz - nz * dEy) + al * (nx * ndH - dHx));
+          fr[4 * E * FSTR] = sc * ((nz * dEx - nx * dEz) + al * (ny * ndH - dHy));
+          fr[5 * E * FSTR] = sc * ((nx * dEy - ny * dEx) + al * (nz * ndH - dHz));
+        }
+      }
+      // ---- A rows of tile t
       const bool live = row < D::ROWS && re < Ev;
       const uint32_t a_hi = tbase + lane_off + buf * D::BUF_COLS;
       const uint32_t a_lo = a_hi + D::ACOLS;
-      if (part == 0) {
-        // the two fields of the row's curl, kept in registers for all three mu
-        wait_or_flag(&s_u_full[slot], (t / D::NSU) & 1, A.status);
-        float ua[Np], ub[Np];
-        float umax = 0.f, cmax = 0.f;
-        const float* pa = su + (fa * E + re) * Np;
-        const float* pb = su + (fb * E + re) * Np;
-#pragma unroll
-        for (int j = 0; j < Np; ++j) {
-          ua[j] = live ? pa[j] : 0.f;
-          ub[j] = live ? pb[j] : 0.f;
-          umax = fmaxf(umax, fmaxf(fabsf(ua[j]), fabsf(ub[j])));
-        }
-        if (live) {
-#pragma unroll
-          for (int mu = 0; mu < 3; ++mu)
-            cmax = fmaxf(cmax, fabsf(sg[(3 * mu + (o + 1) % 3) * E + re]) +
-                                   fabsf(sg[(3 * mu + (o + 2) % 3) * E + re]));
-        }
-        // |g^mu| <= (|r_mu,a| + |r_mu,b|) max(max|U_a|, max|U_b|)
-        sBound[row] = cmax * umax;
-        named_sync(2, 256);
-        const float s = row_scale(fmaxf(sBound[row], sBound[128 + row]));
-        named_sync(2, 256);                              // bounds read by everyone
-        // A[buf] is free once the MMAs of tile t-2 have completed
-        if (t >= 2) wait_or_flag(&s_mma_done[buf], ((t - 2) >> 1) & 1, A.status);
-        tc::fence_after_sync();
-        sScale[(t & 3) * 128 + row] = s;
-        // the scale goes on the fields, not on the metric terms: s may be as large
-        // as 2^127 for a row of tiny values, while |U s| < 2^15 / (|r_a| + |r_b|)
-#pragma unroll
-        for (int j = 0; j < Np; ++j) {
-          ua[j] *= s;
-          ub[j] *= s;
-        }
-#pragma unroll 1
-        for (int mu = 0; mu < 3; ++mu) {
-          const float ca = live ? sgn * sg[(3 * mu + (o + 1) % 3) * E + re] : 0.f;
-          const float cb = live ? -sgn * sg[(3 * mu + (o + 2) % 3) * E + re] : 0.f;
-          split_store_fn<D::COLS_G>(
-              [&](int j) { return j < Np ? fmaf(ca, ua[j], cb * ub[j]) : 0.f; },
-              a_hi + mu * D::COLS_G, a_lo + mu * D::COLS_G);
-        }
-      } else {
-        // the flux row, kept in registers from the bound to the split
-        wait_or_flag(&s_f_full[buf], (t >> 1) & 1, A.status);
-        const float* frow = sF + buf * D::F_FLOATS + (rc * E + re) * FSTR;
+      if (role == 2) {
+        named_sync(2, D::PRODUCERS);                     // the flux buffer is complete
+        const float* frow = F + (rc * E + re) * FSTR;
         float w[D::KF];
         float fmax = 0.f;
 #pragma unroll
@@ -498,14 +478,58 @@ __global__ void __launch_bounds__(TcDims<N>::THREADS, 1) tc_stage_kernel(const S
           fmax = fmaxf(fmax, fabsf(w[m]));
         }
         sBound[128 + row] = fmax;
-        named_sync(2, 256);
+        named_sync(2, D::PRODUCERS);                     // row bounds published
         const float s = row_scale(fmaxf(sBound[row], sBound[128 + row]));
-        named_sync(2, 256);
-        tc::mbar_arrive(&s_f_empty[buf]);                // flux row now in registers
+        // A[buf] is free once the MMAs of tile t-2 have completed
         if (t >= 2) wait_or_flag(&s_mma_done[buf], ((t - 2) >> 1) & 1, A.status);
         tc::fence_after_sync();
         split_store_fn<D::COLS_F>([&](int m) { return w[m] * s; }, a_hi + 3 * D::COLS_G,
                                   a_lo + 3 * D::COLS_G);
+      } else {
+        // the two fields of the row's curl, in registers
+        float ua[Np], ub[Np];
+        float umax = 0.f;
+        const float* pa = su + (fa * E + re) * Np;
+        const float* pb = su + (fb * E + re) * Np;
+#pragma unroll
+        for (int j = 0; j < Np; ++j) {
+          ua[j] = live ? pa[j] : 0.f;
+          ub[j] = live ? pb[j] : 0.f;
+          umax = fmaxf(umax, fmaxf(fabsf(ua[j]), fabsf(ub[j])));
+        }
+        named_sync(2, D::PRODUCERS);
+        if (role == 0) {
+          // |g^mu| <= (|r_mu,a| + |r_mu,b|) max(max|U_a|, max|U_b|)
+          float cmax = 0.f;
+          if (live) {
+#pragma unroll
+            for (int mu = 0; mu < 3; ++mu)
+              cmax = fmaxf(cmax, fabsf(sg[(3 * mu + (o + 1) % 3) * E + re]) +
+                                     fabsf(sg[(3 * mu + (o + 2) % 3) * E + re]));
+          }
+          sBound[row] = cmax * umax;
+        }
+        named_sync(2, D::PRODUCERS);
+        const float s = row_scale(fmaxf(sBound[row], sBound[128 + row]));
+        if (t >= 2) wait_or_flag(&s_mma_done[buf], ((t - 2) >> 1) & 1, A.status);
+        tc::fence_after_sync();
+        if (role == 0) sScale[(t & 3) * 128 + row] = s;
+        // the scale goes on the fields, not on the metric terms: s may be as large
+        // as 2^127 for a row of tiny values, while |U s| < 2^15 / (|r_a| + |r_b|)
+#pragma unroll
+        for (int j = 0; j < Np; ++j) {
+          ua[j] *= s;
+          ub[j] *= s;
+        }
+        const int mu0 = role == 0 ? 2 : 0, mu1 = role == 0 ? 3 : 2;
+#pragma unroll 1
+        for (int mu = mu0; mu < mu1; ++mu) {
+          const float ca = live ? sgn * sg[(3 * mu + (o + 1) % 3) * E + re] : 0.f;
+          const float cb = live ? -sgn * sg[(3 * mu + (o + 2) % 3) * E + re] : 0.f;
+          split_store_fn<D::COLS_G>(
+              [&](int j) { return j < Np ? fmaf(ca, ua[j], cb * ub[j]) : 0.f; },
+              a_hi + mu * D::COLS_G, a_lo + mu * D::COLS_G);
+        }
       }
       tc::tmem_st_wait();
       tc::fence_before_sync();
