@@ -165,6 +165,23 @@ def dist_setup():
     return world, rank, local
 
 
+def max_over_ranks(dist, x, device):
+    """The largest of every rank's x (x itself on one rank): the job's time is
+    its slowest replica's."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(world, dof_per_stage, stages, seconds):
+    """Whole-job DOF-updates/s: every replica advances its own copy of the
+    workload by `stages` stages in `seconds` (the slowest replica's time)."""
+    return world * dof_per_stage * stages / seconds
+
+
 def run_ours(args):
     import torch
     import paper_0901_1024_gb300 as dg
@@ -207,15 +224,13 @@ def run_ours(args):
     ms = e0.elapsed_time(e1)
     trace_ms, trace_kind = mesh.trace_read()
     mesh.trace_enable(0)
+    ms = max_over_ranks(dist, ms, "cuda")
     if dist:
-        tt = torch.tensor([ms], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms = float(tt.item())
         dist.barrier()
     clocks = sampler.stop(t0, t1) if sampler else None
 
     dof_stage = 6 * K * Np
-    value = world * dof_stage * 5 * args.steps / (ms * 1e-3)
+    value = job_value(world, dof_stage, 5 * args.steps, ms * 1e-3)
     stage_ms = [t for t, k in zip(trace_ms, trace_kind) if k in (0, 4)]
     tc_path = any(k == 4 for k in trace_kind)
     avg_stage_s = statistics.fmean(stage_ms) * 1e-3
@@ -239,13 +254,9 @@ def run_ours(args):
         for _ in range(n_e2e):
             mesh.step_host(uh, rh, dt, 1, with_energy=True)
         h1 = time.perf_counter()
-        el = h1 - h0
-        if dist:
-            tt = torch.tensor([el], device="cuda")
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            el = float(tt.item())
+        el = max_over_ranks(dist, h1 - h0, "cuda")
         nbytes = u0.nbytes
-        e2e = {"value": world * dof_stage * 5 * n_e2e / el, "unit": METRIC,
+        e2e = {"value": job_value(world, dof_stage, 5 * n_e2e, el), "unit": METRIC,
                "h2d_bytes_per_step": 2 * nbytes, "d2h_bytes_per_step": 2 * nbytes + 8,
                "steps": n_e2e, "call": "dg_step_host (pinned host u, res; H2D, 5 stages, D2H, energy)"}
 

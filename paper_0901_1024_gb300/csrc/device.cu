@@ -48,13 +48,76 @@ cudaError_t launch_stage(int N, bool rk, const StageArgs& a, int num_sms, cudaSt
 }
 
 // ------------------------------------------------------------- energy -----
-// E = 1/2 sum_k J_k sum_c u_kc^T M u_kc.  One warp per element: lane i forms
-// (M u_c)_i (M symmetric, read column-wise = coalesced) and u_i (M u_c)_i in
-// FP32; the per-element sum is scaled by J_k and accumulated in FP64.  Each
-// block writes one FP64 partial; a one-thread kernel adds the partials in a
-// fixed order, so the result is deterministic.
+// E = 1/2 sum_k J_k sum_c u_kc^T M u_kc.  Each block writes one FP64 partial
+// (its threads' sums, added in a fixed order) and a one-warp kernel adds the
+// partials in a fixed order, so the result is deterministic.
 constexpr int kEnergyThreads = 256;
+constexpr int kEnergyRows = 128;      // field rows (c, k) per block pass, orders 1..6
 
+// Orders 1..6: a block stages 128 consecutive field rows in shared memory with
+// coalesced loads (row stride NP | 1: conflict-free), then thread r keeps row r
+// in registers and forms u^T M u from M's rows, read as broadcast 16-byte loads.
+template <int NP>
+__global__ void __launch_bounds__(kEnergyRows) energy_rows_kernel(const EnergyArgs A) {
+  constexpr int NP4 = (NP + 3) & ~3, RS = NP | 1;
+  extern __shared__ __align__(16) float esm[];
+  float* sM = esm;                       // [NP][NP4], zero padded
+  float* sU = esm + NP * NP4;            // [kEnergyRows][RS]
+  for (int i = threadIdx.x; i < NP * NP4; i += kEnergyRows) {
+    const int r = i / NP4, c = i - r * NP4;
+    sM[i] = c < NP ? __ldg(A.M + r * NP + c) : 0.f;
+  }
+  const int64_t rows = int64_t(6) * A.K;
+  double acc = 0.0;
+  for (int64_t r0 = int64_t(blockIdx.x) * kEnergyRows; r0 < rows;
+       r0 += int64_t(gridDim.x) * kEnergyRows) {
+    const int nr = int(rows - r0 < kEnergyRows ? rows - r0 : kEnergyRows);
+    __syncthreads();                     // previous pass done with sU (and sM written)
+    const float* src = A.u + r0 * NP;
+    for (int i = threadIdx.x; i < nr * NP; i += kEnergyRows) {
+      const int r = i / NP;
+      sU[r * RS + (i - r * NP)] = __ldg(src + i);
+    }
+    __syncthreads();
+    const int r = threadIdx.x;
+    if (r < nr) {
+      float u[NP4];
+#pragma unroll
+      for (int j = 0; j < NP4; ++j) u[j] = j < NP ? sU[r * RS + j] : 0.f;
+      float e = 0.f;
+#pragma unroll 1
+      for (int i = 0; i < NP; ++i) {
+        const float4* Mi = reinterpret_cast<const float4*>(sM + i * NP4);
+        float s = 0.f;
+#pragma unroll
+        for (int j4 = 0; j4 < NP4 / 4; ++j4) {
+          const float4 m4 = Mi[j4];
+          s = fmaf(m4.x, u[4 * j4], s);
+          s = fmaf(m4.y, u[4 * j4 + 1], s);
+          s = fmaf(m4.z, u[4 * j4 + 2], s);
+          s = fmaf(m4.w, u[4 * j4 + 3], s);
+        }
+        e = fmaf(sU[r * RS + i], s, e);
+      }
+      const int64_t k = (r0 + r) % A.K;
+      const float J = reinterpret_cast<const float*>(A.geo)[k * kGeoWords + 9];
+      acc += double(J) * double(e);
+    }
+  }
+  __shared__ double sw[kEnergyRows / 32];
+#pragma unroll
+  for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) sw[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < kEnergyRows / 32; ++w) t += sw[w];
+    A.partials[blockIdx.x] = t;
+  }
+}
+
+// Any order: one warp per element, lane i forms (M u_c)_i (M symmetric, read
+// column-wise = coalesced) and u_i (M u_c)_i in FP32, scaled by J_k in FP64.
 __global__ void __launch_bounds__(kEnergyThreads) energy_kernel(const EnergyArgs A) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   constexpr int nw = kEnergyThreads / 32;
@@ -84,19 +147,47 @@ __global__ void __launch_bounds__(kEnergyThreads) energy_kernel(const EnergyArgs
   }
 }
 
+// One warp: lane l adds partials l, l + 32, ... in order, then a fixed
+// butterfly adds the lanes.
 __global__ void energy_finalize(const double* partials, int n, double* result) {
-  if (threadIdx.x == 0 && blockIdx.x == 0) {
-    double t = 0.0;
-    for (int i = 0; i < n; ++i) t += partials[i];
-    result[0] = 0.5 * t;
-  }
+  double t = 0.0;
+  for (int i = threadIdx.x; i < n; i += 32) t += partials[i];
+#pragma unroll
+  for (int o = 16; o; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+  if (threadIdx.x == 0) result[0] = 0.5 * t;
 }
 
 int energy_grid(int num_sms) { return 4 * num_sms; }
 
-cudaError_t launch_energy_partials(const EnergyArgs& a, int grid, cudaStream_t s) {
-  energy_kernel<<<grid, kEnergyThreads, 0, s>>>(a);
+template <int NP>
+static cudaError_t launch_energy_rows(const EnergyArgs& a, int grid, cudaStream_t s) {
+  constexpr int bytes = (NP * ((NP + 3) & ~3) + kEnergyRows * (NP | 1)) * 4;
+  static bool attr[16] = {};
+  int dev = 0;
+  cudaError_t err = cudaGetDevice(&dev);
+  if (err != cudaSuccess) return err;
+  if (!attr[dev & 15]) {
+    err = cudaFuncSetAttribute(energy_rows_kernel<NP>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (err != cudaSuccess) return err;
+    attr[dev & 15] = true;
+  }
+  energy_rows_kernel<NP><<<grid, kEnergyRows, bytes, s>>>(a);
   return cudaGetLastError();
+}
+
+cudaError_t launch_energy_partials(const EnergyArgs& a, int grid, cudaStream_t s) {
+  switch (a.Np) {
+    case 4: return launch_energy_rows<4>(a, grid, s);
+    case 10: return launch_energy_rows<10>(a, grid, s);
+    case 20: return launch_energy_rows<20>(a, grid, s);
+    case 35: return launch_energy_rows<35>(a, grid, s);
+    case 56: return launch_energy_rows<56>(a, grid, s);
+    case 84: return launch_energy_rows<84>(a, grid, s);
+    default:
+      energy_kernel<<<grid, kEnergyThreads, 0, s>>>(a);
+      return cudaGetLastError();
+  }
 }
 
 cudaError_t launch_energy_final(const EnergyArgs& a, int grid, cudaStream_t s) {
