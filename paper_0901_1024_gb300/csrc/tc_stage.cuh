@@ -60,7 +60,8 @@ template <int N> struct TcDims {
   static_assert(2 * ACOLS + NN <= BUF_COLS, "tensor-memory buffer overflow");
   static constexpr int COLS_G = KB / 2;               // columns of one mu block
   static constexpr int COLS_F = KF / 2;               // columns of the flux block
-  static constexpr int FSTR = NF | 1;                 // flux buffer row stride (odd)
+  static constexpr int FSTR = NF + 2;                // flux row stride: 8-byte pair reads of
+                                                      // a warp's 32 rows are conflict-free
   static constexpr int THREADS = 512;                 // 4 epilogue + 12 producer warps
   static constexpr int PRODUCERS = 384;
   static constexpr int ITEMS = (E * NF + PRODUCERS - 1) / PRODUCERS;   // flux items per producer
@@ -76,8 +77,8 @@ template <int N> struct TcDims {
   static constexpr int OFF_G = OFF_U + NSU * U_FLOATS * 4;
   static constexpr int OFF_R = OFF_G + NSU * G_FLOATS * 4;   // NSR slots
   static constexpr int OFF_F = OFF_R + NSR * U_FLOATS * 4;   // one flux buffer
-  static constexpr int OFF_BND = OFF_F + F_FLOATS * 4;         // [2 parts][128] row bounds
-  static constexpr int OFF_SC = OFF_BND + 2 * 128 * 4;       // [4][128] row scales
+  static constexpr int OFF_BND = OFF_F + F_FLOATS * 4;         // [3 roles][128] row bounds
+  static constexpr int OFF_SC = OFF_BND + 3 * 128 * 4;       // [4][128] row scales
   static constexpr int OFF_TAB = OFF_SC + 4 * 128 * 4;
   static constexpr int SMEM = OFF_TAB + TAB_BYTES;
   static_assert((U_FLOATS * 4) % 16 == 0 && (E * Np * 4) % 16 == 0, "bulk-copy alignment");
@@ -88,6 +89,7 @@ template <int N> struct TcDims {
 };
 
 static_assert(tc_b_bytes(4) == 2 * TcDims<4>::B_BYTES, "B buffer size formula");
+static_assert(TcDims<1>::FSTR % 4 == 2 && TcDims<4>::FSTR % 4 == 2, "flux row stride");
 static_assert(TcDims<4>::G_FLOATS == kTcGeoWords * kTcTileElems + kTcTileElems * TcDims<4>::NF / 4,
               "geometry block size");
 
@@ -111,32 +113,24 @@ __device__ __forceinline__ void tmem_store_cols(uint32_t taddr, const uint32_t* 
   }
 }
 
-// Scales 2*NC values, splits them into FP16 hi/lo pairs and stores the NC
-// packed columns of each piece, at most 16 columns at a time.
-template <int NC>
-__device__ __forceinline__ void split_store(const float* v, float s, uint32_t t_hi, uint32_t t_lo) {
-  constexpr int CH = NC < 16 ? NC : 16;
-  uint32_t hi[CH], lo[CH];
-#pragma unroll
-  for (int p = 0; p < CH; ++p) tc::split2(v[2 * p] * s, v[2 * p + 1] * s, hi[p], lo[p]);
-  tmem_store_cols<CH>(t_hi, hi);
-  tmem_store_cols<CH>(t_lo, lo);
-  if constexpr (NC > CH) split_store<NC - CH>(v + 2 * CH, s, t_hi + CH, t_lo + CH);
-}
-
-// Columns [C0, C0 + NC) of one row: value j = val(j) for j < 2 NC, split into
-// FP16 hi/lo pairs and stored 8 columns at a time (values are produced only as
-// they are stored, so few registers are live).
+// Columns [C0, C0 + NC) of one row: column p holds the pair val(p) (a float2 of
+// values 2p, 2p + 1), split into FP16 hi/lo and stored 8 columns at a time
+// (pairs are produced only as they are stored, so few registers are live).
 template <int NC, int C0 = 0, typename Val>
 __device__ __forceinline__ void split_store_fn(const Val& val, uint32_t t_hi, uint32_t t_lo) {
   constexpr int CH = NC < 8 ? NC : 8;
   uint32_t hi[CH], lo[CH];
 #pragma unroll
-  for (int p = 0; p < CH; ++p) tc::split2(val(2 * (C0 + p)), val(2 * (C0 + p) + 1), hi[p], lo[p]);
+  for (int p = 0; p < CH; ++p) {
+    const float2 v = val(C0 + p);
+    tc::split2(v.x, v.y, hi[p], lo[p]);
+  }
   tmem_store_cols<CH>(t_hi + C0, hi);
   tmem_store_cols<CH>(t_lo + C0, lo);
   if constexpr (NC > CH) split_store_fn<NC - CH, C0 + CH>(val, t_hi, t_lo);
 }
+
+__device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
 
 template <int NC>
 __device__ __forceinline__ void tmem_load_cols(uint32_t taddr, uint32_t* v) {
@@ -194,6 +188,75 @@ __device__ __forceinline__ void tc_load_res(const StageArgs& A, int tile, float*
   tc::mbar_expect_tx(bar, 6u * fb);
   for (int c = 0; c < 6; ++c)
     tc::bulk_g2s(sr + c * D::E * D::Np, A.res + (size_t(c) * K + k0) * D::Np, fb, bar);
+}
+
+// One g-block builder row (a producer thread of role 0 or 1) of tile t.
+struct GRow {
+  const float* su;
+  const float* sg;
+  float* sBound;
+  float* sScale;
+  int t, row, rc, re, o, fa, fb;
+  float sgn;
+  bool live;
+  uint32_t a_hi, a_lo;
+  uint64_t* mma_done;
+  int* status;
+};
+
+// Node pairs [P0, P0 + NPH) of the three g^mu blocks of one A row: loads that
+// part of the two curl fields, publishes its bound on |g| and, after the flux
+// bound, splits g^mu = sign (r_mu,a U_a - r_mu,b U_b) into tensor memory.
+template <int N, int P0, int NPH>
+__device__ __forceinline__ void build_g_half(const GRow& g, int role) {
+  using D = TcDims<N>;
+  constexpr int E = D::E, Np = D::Np;
+  float2 ua[NPH], ub[NPH];
+  float umax = 0.f;
+  const float* pa = g.su + (g.fa * E + g.re) * Np;
+  const float* pb = g.su + (g.fb * E + g.re) * Np;
+#pragma unroll
+  for (int i = 0; i < NPH; ++i) {
+    const int j = 2 * (P0 + i);
+    ua[i].x = g.live ? pa[j] : 0.f;
+    ub[i].x = g.live ? pb[j] : 0.f;
+    ua[i].y = g.live && j + 1 < Np ? pa[j + 1] : 0.f;
+    ub[i].y = g.live && j + 1 < Np ? pb[j + 1] : 0.f;
+    umax = fmaxf(umax, fmaxf(fmaxf(fabsf(ua[i].x), fabsf(ua[i].y)),
+                             fmaxf(fabsf(ub[i].x), fabsf(ub[i].y))));
+  }
+  float cmax = 0.f;
+  if (g.live) {
+#pragma unroll
+    for (int mu = 0; mu < 3; ++mu)
+      cmax = fmaxf(cmax, fabsf(g.sg[(3 * mu + (g.o + 1) % 3) * E + g.re]) +
+                             fabsf(g.sg[(3 * mu + (g.o + 2) % 3) * E + g.re]));
+  }
+  named_sync(2, D::PRODUCERS);            // everyone read the previous tile's bounds
+  // |g^mu| <= (|r_mu,a| + |r_mu,b|) max(max|U_a|, max|U_b|) over this node range
+  g.sBound[role * 128 + g.row] = cmax * umax;
+  named_sync(2, D::PRODUCERS);            // row bounds published
+  const float s = row_scale(fmaxf(fmaxf(g.sBound[g.row], g.sBound[128 + g.row]),
+                                  g.sBound[256 + g.row]));
+  // A[buf] is free once the MMAs of tile t-2 have completed
+  if (g.t >= 2) wait_or_flag(g.mma_done, ((g.t - 2) >> 1) & 1, g.status);
+  tc::fence_after_sync();
+  if (role == 0) g.sScale[(g.t & 3) * 128 + g.row] = s;
+  // the scale goes on the fields, not on the metric terms: s may be as large
+  // as 2^127 for a row of tiny values, while |U s| < 2^15 / (|r_a| + |r_b|)
+#pragma unroll
+  for (int i = 0; i < NPH; ++i) {
+    ua[i] = __fmul2_rn(ua[i], f2(s));
+    ub[i] = __fmul2_rn(ub[i], f2(s));
+  }
+#pragma unroll 1
+  for (int mu = 0; mu < 3; ++mu) {
+    const float ca = g.live ? g.sgn * g.sg[(3 * mu + (g.o + 1) % 3) * E + g.re] : 0.f;
+    const float cb = g.live ? -g.sgn * g.sg[(3 * mu + (g.o + 2) % 3) * E + g.re] : 0.f;
+    split_store_fn<NPH, P0>(
+        [&](int p) { return __ffma2_rn(f2(ca), ua[p - P0], __fmul2_rn(f2(cb), ub[p - P0])); },
+        g.a_hi + mu * D::COLS_G, g.a_lo + mu * D::COLS_G);
+  }
 }
 
 template <int N, bool RK>
@@ -314,17 +377,27 @@ __global__ void __launch_bounds__(TcDims<N>::THREADS, 1) tc_stage_kernel(const S
                 }
             }
 #pragma unroll
-            for (int i = 0; i < CH; ++i)
-              if (i0 + i < Np) {
-                const float r = __uint_as_float(acc[i0 + i]) * inv;
-                if (RK) {
-                  const float rn = fmaf(A.a, rv[i], A.dt * r);
-                  pr[i0 + i] = rn;
-                  pu[i0 + i] = fmaf(A.b, rn, uv[i]);
-                } else {
-                  pr[i0 + i] = r;
+            for (int i = 0; i < CH; i += 2) {
+              if (i0 + i >= Np) break;
+              // pair (i, i + 1) in packed FP32x2; a lone last node pairs with itself
+              const int i1 = i0 + i + 1 < Np ? i + 1 : i;
+              const float2 r = __fmul2_rn(
+                  make_float2(__uint_as_float(acc[i0 + i]), __uint_as_float(acc[i0 + i1])), f2(inv));
+              if (RK) {
+                const float2 rn = __ffma2_rn(f2(A.a), make_float2(rv[i], rv[i1]),
+                                             __fmul2_rn(f2(A.dt), r));
+                const float2 un = __ffma2_rn(f2(A.b), rn, make_float2(uv[i], uv[i1]));
+                pr[i0 + i] = rn.x;
+                pu[i0 + i] = un.x;
+                if (i1 != i) {
+                  pr[i0 + i1] = rn.y;
+                  pu[i0 + i1] = un.y;
                 }
+              } else {
+                pr[i0 + i] = r.x;
+                if (i1 != i) pr[i0 + i1] = r.y;
               }
+            }
           }
         }
         tc::fence_proxy_async_smem();
@@ -362,8 +435,9 @@ __global__ void __launch_bounds__(TcDims<N>::THREADS, 1) tc_stage_kernel(const S
   } else {
     // ============================ producer warps ===============================
     // Warps 4..15 compute the fluxes of tile t together, then build its A rows:
-    // per tensor-memory lane quarter, role 0 (warps 4-7) the g^t block, role 1
-    // (warps 8-11) the g^r and g^s blocks, role 2 (warps 12-15) the flux block.
+    // per tensor-memory lane quarter, roles 0 and 1 (warps 4-7, 8-11) the first
+    // and second half of the node range of the three g blocks, role 2 (warps
+    // 12-15) the flux block.
     const int pt = tid - 128;
     const int role = (warp - 4) >> 2, quarter = warp & 3;
     const int row = quarter * 32 + lane;
@@ -422,12 +496,24 @@ __global__ void __launch_bounds__(TcDims<N>::THREADS, 1) tc_stage_kernel(const S
       tc::cp_async_commit();
       tc::cp_async_wait_all();
       // upwind flux of every face node (PEC ghost state E+ = -E-, H+ = H- on walls):
-      // every item's operands are loaded before any store into the flux buffer
+      // every item's operands are loaded before any store into the flux buffer,
+      // then items are processed two at a time in packed FP32x2 arithmetic
       {
-        float uM[D::ITEMS][6], up[D::ITEMS][6], nv[D::ITEMS][4];
+        constexpr int NQ = (D::ITEMS + 1) & ~1;
+        float uM[NQ][6], up[NQ][6], nv[NQ][4];
+        uint32_t kinds[NQ];
 #pragma unroll
-        for (int q = 0; q < D::ITEMS; ++q) {
+        for (int q = 0; q < NQ; ++q) {
+          if (q >= D::ITEMS) {
+            kinds[q] = 0u;
+#pragma unroll
+            for (int c = 0; c < 6; ++c) uM[q][c] = up[q][c] = 0.f;
+#pragma unroll
+            for (int w = 0; w < 4; ++w) nv[q][w] = 0.f;
+            continue;
+          }
           const uint32_t it = item[q], kind = info[q] & 3u;
+          kinds[q] = kind;
           const int e = kind ? int(it & 31) : 0, m = (it >> 5) & 127, f = (it >> 12) & 3;
           const int idM = (it >> 14) & 63;
           const float* pp = kind == 3u ? F + e * FSTR + m : su + (info[q] >> 2);
@@ -440,27 +526,45 @@ __global__ void __launch_bounds__(TcDims<N>::THREADS, 1) tc_stage_kernel(const S
 #pragma unroll
           for (int w = 0; w < 4; ++w) nv[q][w] = sg[(10 + 4 * f + w) * E + e];
         }
-        const float al = A.alpha;
+        const float2 m1 = f2(-1.f), nal = f2(-A.alpha), al = f2(A.alpha);
 #pragma unroll
-        for (int q = 0; q < D::ITEMS; ++q) {
-          const uint32_t kind = info[q] & 3u;
-          if (kind == 0u) continue;
-          const int e = item[q] & 31, m = (item[q] >> 5) & 127;
-          const float we = kind == 1u ? -1.f : 1.f;
-          const float nx = nv[q][0], ny = nv[q][1], nz = nv[q][2], sc = 0.5f * nv[q][3];
-          const float dEx = uM[q][0] - we * up[q][0], dEy = uM[q][1] - we * up[q][1];
-          const float dEz = uM[q][2] - we * up[q][2];
-          const float dHx = uM[q][3] - up[q][3], dHy = uM[q][4] - up[q][4];
-          const float dHz = uM[q][5] - up[q][5];
-          const float ndE = nx * dEx + ny * dEy + nz * dEz;
-          const float ndH = nx * dHx + ny * dHy + nz * dHz;
-          float* fr = F + e * FSTR + m;
-          fr[0 * E * FSTR] = sc * (-(ny * dHz - nz * dHy) + al * (nx * ndE - dEx));
-          fr[1 * E * FSTR] = sc * (-(nz * dHx - nx * dHz) + al * (ny * ndE - dEy));
-          fr[2 * E * FSTR] = sc * (-(nx * dHy - ny * dHx) + al * (nz * ndE - dEz));
-          fr[3 * E * FSTR] = sc * ((ny * dEz - nz * dEy) + al * (nx * ndH - dHx));
-          fr[4 * E * FSTR] = sc * ((nz * dEx - nx * dEz) + al * (ny * ndH - dHy));
-          fr[5 * E * FSTR] = sc * ((nx * dEy - ny * dEx) + al * (nz * ndH - dHz));
+        for (int q = 0; q < NQ; q += 2) {
+          const int r = q + 1;
+          auto P = [&](const float (*v)[6], int c) { return make_float2(v[q][c], v[r][c]); };
+          const float2 nwe = make_float2(kinds[q] == 1u ? 1.f : -1.f, kinds[r] == 1u ? 1.f : -1.f);
+          const float2 dEx = __ffma2_rn(nwe, P(up, 0), P(uM, 0));
+          const float2 dEy = __ffma2_rn(nwe, P(up, 1), P(uM, 1));
+          const float2 dEz = __ffma2_rn(nwe, P(up, 2), P(uM, 2));
+          const float2 dHx = __ffma2_rn(m1, P(up, 3), P(uM, 3));
+          const float2 dHy = __ffma2_rn(m1, P(up, 4), P(uM, 4));
+          const float2 dHz = __ffma2_rn(m1, P(up, 5), P(uM, 5));
+          const float2 nx = make_float2(nv[q][0], nv[r][0]), ny = make_float2(nv[q][1], nv[r][1]);
+          const float2 nz = make_float2(nv[q][2], nv[r][2]);
+          const float2 sc = __fmul2_rn(f2(0.5f), make_float2(nv[q][3], nv[r][3]));
+          const float2 mx = __fmul2_rn(m1, nx), my = __fmul2_rn(m1, ny), mz = __fmul2_rn(m1, nz);
+          const float2 aE = __fmul2_rn(al, __ffma2_rn(nz, dEz, __ffma2_rn(ny, dEy, __fmul2_rn(nx, dEx))));
+          const float2 aH = __fmul2_rn(al, __ffma2_rn(nz, dHz, __ffma2_rn(ny, dHy, __fmul2_rn(nx, dHx))));
+          // fluxE = -n x dH + alpha (n (n.dE) - dE), fluxH = n x dE + alpha (n (n.dH) - dH)
+          float2 fl[6];
+          fl[0] = __ffma2_rn(nal, dEx, __ffma2_rn(nx, aE, __ffma2_rn(my, dHz, __fmul2_rn(nz, dHy))));
+          fl[1] = __ffma2_rn(nal, dEy, __ffma2_rn(ny, aE, __ffma2_rn(mz, dHx, __fmul2_rn(nx, dHz))));
+          fl[2] = __ffma2_rn(nal, dEz, __ffma2_rn(nz, aE, __ffma2_rn(mx, dHy, __fmul2_rn(ny, dHx))));
+          fl[3] = __ffma2_rn(nal, dHx, __ffma2_rn(nx, aH, __ffma2_rn(mz, dEy, __fmul2_rn(ny, dEz))));
+          fl[4] = __ffma2_rn(nal, dHy, __ffma2_rn(ny, aH, __ffma2_rn(mx, dEz, __fmul2_rn(nz, dEx))));
+          fl[5] = __ffma2_rn(nal, dHz, __ffma2_rn(nz, aH, __ffma2_rn(my, dEx, __fmul2_rn(nx, dEy))));
+#pragma unroll
+          for (int c = 0; c < 6; ++c) fl[c] = __fmul2_rn(sc, fl[c]);
+          if (kinds[q]) {
+            float* fr = F + int(item[q] & 31) * FSTR + int((item[q] >> 5) & 127);
+#pragma unroll
+            for (int c = 0; c < 6; ++c) fr[c * E * FSTR] = fl[c].x;
+          }
+          if (r < D::ITEMS && kinds[r]) {
+            float* fr = F + int(item[r < D::ITEMS ? r : 0] & 31) * FSTR +
+                        int((item[r < D::ITEMS ? r : 0] >> 5) & 127);
+#pragma unroll
+            for (int c = 0; c < 6; ++c) fr[c * E * FSTR] = fl[c].y;
+          }
         }
       }
       // ---- A rows of tile t
@@ -469,67 +573,35 @@ __global__ void __launch_bounds__(TcDims<N>::THREADS, 1) tc_stage_kernel(const S
       const uint32_t a_lo = a_hi + D::ACOLS;
       if (role == 2) {
         named_sync(2, D::PRODUCERS);                     // the flux buffer is complete
-        const float* frow = F + (rc * E + re) * FSTR;
+        const float2* frow = reinterpret_cast<const float2*>(F + (rc * E + re) * FSTR);
         float w[D::KF];
         float fmax = 0.f;
 #pragma unroll
-        for (int m = 0; m < D::KF; ++m) {
-          w[m] = (live && m < NF) ? frow[m] : 0.f;
-          fmax = fmaxf(fmax, fabsf(w[m]));
+        for (int p = 0; p < D::KF / 2; ++p) {
+          const float2 v = (live && 2 * p < NF) ? frow[p] : make_float2(0.f, 0.f);
+          w[2 * p] = v.x;
+          w[2 * p + 1] = v.y;
+          fmax = fmaxf(fmax, fmaxf(fabsf(v.x), fabsf(v.y)));
         }
-        sBound[128 + row] = fmax;
+        sBound[256 + row] = fmax;
         named_sync(2, D::PRODUCERS);                     // row bounds published
-        const float s = row_scale(fmaxf(sBound[row], sBound[128 + row]));
+        const float s = row_scale(fmaxf(fmaxf(sBound[row], sBound[128 + row]), sBound[256 + row]));
         // A[buf] is free once the MMAs of tile t-2 have completed
         if (t >= 2) wait_or_flag(&s_mma_done[buf], ((t - 2) >> 1) & 1, A.status);
         tc::fence_after_sync();
-        split_store_fn<D::COLS_F>([&](int m) { return w[m] * s; }, a_hi + 3 * D::COLS_G,
-                                  a_lo + 3 * D::COLS_G);
+        split_store_fn<D::COLS_F>(
+            [&](int p) { return __fmul2_rn(make_float2(w[2 * p], w[2 * p + 1]), f2(s)); },
+            a_hi + 3 * D::COLS_G, a_lo + 3 * D::COLS_G);
       } else {
-        // the two fields of the row's curl, in registers
-        float ua[Np], ub[Np];
-        float umax = 0.f;
-        const float* pa = su + (fa * E + re) * Np;
-        const float* pb = su + (fb * E + re) * Np;
-#pragma unroll
-        for (int j = 0; j < Np; ++j) {
-          ua[j] = live ? pa[j] : 0.f;
-          ub[j] = live ? pb[j] : 0.f;
-          umax = fmaxf(umax, fmaxf(fabsf(ua[j]), fabsf(ub[j])));
-        }
-        named_sync(2, D::PRODUCERS);
-        if (role == 0) {
-          // |g^mu| <= (|r_mu,a| + |r_mu,b|) max(max|U_a|, max|U_b|)
-          float cmax = 0.f;
-          if (live) {
-#pragma unroll
-            for (int mu = 0; mu < 3; ++mu)
-              cmax = fmaxf(cmax, fabsf(sg[(3 * mu + (o + 1) % 3) * E + re]) +
-                                     fabsf(sg[(3 * mu + (o + 2) % 3) * E + re]));
-          }
-          sBound[row] = cmax * umax;
-        }
-        named_sync(2, D::PRODUCERS);
-        const float s = row_scale(fmaxf(sBound[row], sBound[128 + row]));
-        if (t >= 2) wait_or_flag(&s_mma_done[buf], ((t - 2) >> 1) & 1, A.status);
-        tc::fence_after_sync();
-        if (role == 0) sScale[(t & 3) * 128 + row] = s;
-        // the scale goes on the fields, not on the metric terms: s may be as large
-        // as 2^127 for a row of tiny values, while |U s| < 2^15 / (|r_a| + |r_b|)
-#pragma unroll
-        for (int j = 0; j < Np; ++j) {
-          ua[j] *= s;
-          ub[j] *= s;
-        }
-        const int mu0 = role == 0 ? 2 : 0, mu1 = role == 0 ? 3 : 2;
-#pragma unroll 1
-        for (int mu = mu0; mu < mu1; ++mu) {
-          const float ca = live ? sgn * sg[(3 * mu + (o + 1) % 3) * E + re] : 0.f;
-          const float cb = live ? -sgn * sg[(3 * mu + (o + 2) % 3) * E + re] : 0.f;
-          split_store_fn<D::COLS_G>(
-              [&](int j) { return j < Np ? fmaf(ca, ua[j], cb * ub[j]) : 0.f; },
-              a_hi + mu * D::COLS_G, a_lo + mu * D::COLS_G);
-        }
+        // roles 0 and 1 split the node range: node pairs [0, H) and [H, KB/2) of
+        // all three g blocks, each loading only its half of the two curl fields
+        constexpr int H = (D::KB / 2 + 1) / 2;
+        const GRow gr{su, sg, sBound, sScale, t, row, rc, re, o, fa, fb, sgn, live, a_hi, a_lo,
+                      &s_mma_done[buf], A.status};
+        if (role == 0)
+          build_g_half<N, 0, H>(gr, 0);
+        else
+          build_g_half<N, H, D::KB / 2 - H>(gr, 1);
       }
       tc::tmem_st_wait();
       tc::fence_before_sync();

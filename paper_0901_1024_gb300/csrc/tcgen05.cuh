@@ -224,17 +224,17 @@ __device__ __forceinline__ void bulk_wait_all() {
 }
 
 // ---- FP16 split ------------------------------------------------------------
-// (x0, x1) -> packed hi, lo with x ~= hi + lo: hi is x rounded (half away from
-// zero) to 11 significant bits in the FP32 bit pattern, lo = x - hi (exact in
-// FP32) rounded to FP16.  For |x| in FP16's normal range hi converts to FP16
-// exactly, so only the two packing conversions remain.
+// (x0, x1) -> packed hi, lo with x ~= hi + lo: hi = x rounded to nearest FP16,
+// lo = x - hi (exact in FP32: hi agrees with x in all but the last bits)
+// rounded to FP16, i.e. about 22 significant bits for |x| in FP16's normal
+// range.  One conversion per pair for each piece and one packed subtraction.
 __device__ __forceinline__ void split2(float x0, float x1, uint32_t& hi, uint32_t& lo) {
-  const float h0 = __uint_as_float((__float_as_uint(x0) + 0x1000u) & 0xFFFFE000u);
-  const float h1 = __uint_as_float((__float_as_uint(x1) + 0x1000u) & 0xFFFFE000u);
-  const __half2 h = __floats2half2_rn(h0, h1);
-  const __half2 l = __floats2half2_rn(x0 - h0, x1 - h1);
+  const __half2 h = __floats2half2_rn(x0, x1);
+  const float2 hf = __half22float2(h);
+  const float2 l = __ffma2_rn(hf, make_float2(-1.f, -1.f), make_float2(x0, x1));
+  const __half2 lh = __float22half2_rn(l);
   hi = *reinterpret_cast<const uint32_t*>(&h);
-  lo = *reinterpret_cast<const uint32_t*>(&l);
+  lo = *reinterpret_cast<const uint32_t*>(&lh);
 }
 
 }  // namespace tc
