@@ -133,7 +133,7 @@ int dg_set_stage_impl(dg_mesh* mesh, int impl);
 /*
  * One evaluation of the semi-discrete operator (Eq. semidiscrete-dg):
  * rhs = curl terms (local differentiation, Alg. 4) + LIFT * flux (flux
- * extraction, Alg. 2, and lifting, Alg. 1).
+ * extraction, Alg. 3, and lifting, Alg. 1).
  *   u   : device, [6][K][Np] FP32, read only.
  *   rhs : device, [6][K][Np] FP32, written; must not overlap u.
  * Asynchronous on `stream`.

@@ -4,7 +4,7 @@
 // Per tile of E consecutive tetrahedra (one CTA, persistent over tiles):
 //   1. stage the six fields u[c][k][0..Np) and the 128-byte geometry records of
 //      the tile in shared memory (coalesced loads);
-//   2. flux extraction (Alg. 2 of the paper): for every face node, u- from the
+//   2. flux extraction (Alg. 3 of the paper): for every face node, u- from the
 //      tile, u+ from the tile when the neighbour is in it and from global
 //      memory otherwise (PEC ghost on walls), the upwind flux of Section 6
 //      scaled by Fscale/2, into a shared flux tile [6][E][4 Nfp];

@@ -16,16 +16,17 @@
 // and B = [Dr Ds Dt LIFT] scaled by a power of two; both scales are removed in
 // the epilogue.
 //
-// One persistent CTA per SM (all 512 tensor-memory columns), three warp groups
+// One persistent CTA per SM (all 512 tensor-memory columns), two warp groups
 // working on different tiles at once, linked by mbarriers:
-//   * flux warps (4): flux extraction (Alg. 2 of the paper) for tile t -- the
-//     neighbour values of faces leaving the tile are loaded into registers
-//     first, then every face node's upwind flux (PEC ghost state on walls) is
-//     written to a double-buffered shared [row][m] buffer;
-//   * builder warps (8, two per tensor-memory lane quarter): the A rows of
-//     tile t -- g^mu from the staged fields, flux rows from the flux buffer,
-//     one power-of-two scale per row, FP16 hi/lo split -- written straight
-//     into a double-buffered A in tensor memory (tcgen05.st);
+//   * producer warps (12): together they compute the fluxes of tile t (flux
+//     extraction, Alg. 3 of the paper; 4 face nodes per thread): neighbour
+//     values outside the tile arrive by 4-byte cp.async copies into the flux
+//     buffer, every face node's upwind flux (PEC ghost state on walls) is
+//     written to a shared [row][m] buffer; after a named barrier they build the
+//     A rows of tile t in tensor memory (tcgen05.st), per lane quarter roles 0
+//     and 1 the two halves of the node range of the g^mu blocks and role 2 the
+//     flux block, with one power-of-two scale per row (published by a second
+//     barrier) and the FP16 hi/lo split;
 //   * MMA/epilogue warps (4): warp 0 issues the 3 x K/16 MMAs of tile t into a
 //     double-buffered FP32 accumulator (elect.sync, commit to an mbarrier) and
 //     all bulk copies; all four then read tile t-1's accumulator rows
@@ -467,7 +468,7 @@ __global__ void __launch_bounds__(TcDims<N>::THREADS, 1) tc_stage_kernel(const S
       const float* sg = sG + slot * D::G_FLOATS;
       float* F = sF;
       wait_or_flag(&s_u_full[slot], (t / D::NSU) & 1, A.status);
-      // ---- fluxes (Alg. 2).  Classify every item (0 none, 1 wall, 2 neighbour in
+      // ---- fluxes (Alg. 3).  Classify every item (0 none, 1 wall, 2 neighbour in
       // the tile, 3 neighbour outside it) and start the gathers of kind 3: the six
       // neighbour values go by 4-byte asynchronous copies into the flux-buffer
       // words this item's flux will overwrite (no registers, no extra space).
