@@ -97,6 +97,24 @@ int dg_nodes(const dg_mesh* mesh, double* xyz);
  */
 int dg_get_connectivity(const dg_mesh* mesh, int32_t* vmapM, int32_t* vmapP);
 
+/*
+ * Element numbering for flux-gather locality (Section 5.2, "Flux Extraction",
+ * Algorithm 2, the greedy breadth-first partition): the face-adjacency graph
+ * is cut into blocks of `block` consecutive positions (the last may be
+ * shorter), each grown from a seed by taking the queued element that shares
+ * the most faces with the block (ties: the one queued first); a full block's
+ * queue head seeds the next block, and an empty queue takes the
+ * lowest-numbered element not yet placed.
+ *   block : elements per block, >= 1; 20 matches the tensor-core stage's tiles.
+ *   perm  : host, [K] int64, written: perm[i] = current index of the element to
+ *           place at position i.  Renumber with tets'[i] = tets[perm[i]] and
+ *           fields u'[c][i] = u[c][perm[i]] (a new mesh from tets'); results are
+ *           the same up to that renumbering.
+ * Needs only dg_mesh_create (no order, no GPU).  Errors: DG_ERR_ARG (NULL
+ * mesh or perm, block < 1).
+ */
+int dg_partition_order(const dg_mesh* mesh, int64_t block, int64_t* perm);
+
 /* Reference operators in FP64, row-major: Dr, Ds, Dt, M are [Np][Np], LIFT is
  * [Np][4*Nfp].  Any pointer may be NULL. */
 int dg_get_operators(const dg_mesh* mesh, double* Dr, double* Ds, double* Dt,

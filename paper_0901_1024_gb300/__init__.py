@@ -109,6 +109,15 @@ class Mesh:
               "dg_get_connectivity")
         return vM, vP
 
+    def partition_order(self, block: int = 20):
+        """Greedy partition numbering (dg_partition_order): perm[i] is the
+        current index of the element to place at position i; renumber with
+        tets[perm] and u[:, perm]."""
+        perm = np.empty(self.K, np.int64)
+        check(self._lib.dg_partition_order(self._h, int(block), _dptr(perm, np.int64)),
+              "dg_partition_order")
+        return perm
+
     def operators(self):
         Np, NF = self.Np, 4 * self.Nfp
         Dr, Ds, Dt, M = (np.empty((Np, Np)) for _ in range(4))

@@ -24,6 +24,7 @@ SIGNATURES = {
     "dg_info": (C.c_int, [_vp, _i64p, _intp, _intp, _dp]),
     "dg_nodes": (C.c_int, [_vp, _dp]),
     "dg_get_connectivity": (C.c_int, [_vp, _ip, _ip]),
+    "dg_partition_order": (C.c_int, [_vp, C.c_int64, _i64p]),
     "dg_get_operators": (C.c_int, [_vp, _dp, _dp, _dp, _dp, _dp]),
     "dg_get_geometry": (C.c_int, [_vp, _dp, _dp, _dp, _dp]),
     "dg_set_flux": (C.c_int, [_vp, C.c_double]),

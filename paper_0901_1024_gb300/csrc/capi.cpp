@@ -125,6 +125,14 @@ int dg_get_connectivity(const dg_mesh* m, int32_t* vmapM, int32_t* vmapP) {
   return DG_OK;
 }
 
+int dg_partition_order(const dg_mesh* m, int64_t block, int64_t* perm) {
+  if (int rc = check_mesh(m, false)) return rc;
+  if (!perm) return fail(DG_ERR_ARG, "perm is NULL");
+  if (block < 1) return fail(DG_ERR_ARG, "block must be at least 1");
+  dg::greedy_partition_order(m->nbr_elem, m->K, block, perm);
+  return DG_OK;
+}
+
 int dg_get_operators(const dg_mesh* m, double* Dr, double* Ds, double* Dt, double* M,
                      double* LIFT) {
   if (int rc = check_mesh(m, true)) return rc;

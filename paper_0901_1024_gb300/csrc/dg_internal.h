@@ -74,6 +74,9 @@ int mesh_build(dg_mesh* m, const double* verts, int64_t nv, const int32_t* tets,
                std::string& err);
 // capi.cpp: sets the message returned by dg_last_error() on this thread
 void set_error(const std::string& msg);
+// perm[i] = element placed at position i by the greedy partition (Alg. 2).
+void greedy_partition_order(const std::vector<int32_t>& nbr, int64_t K, int64_t block,
+                            int64_t* perm);
 // device.cu (stream = cudaStream_t)
 int device_rhs(dg_mesh* m, const float* u, float* rhs, void* stream, std::string& err);
 int device_step(dg_mesh* m, float* u, float* res, double dt, int nsteps, void* stream,

@@ -121,3 +121,30 @@ def test_two_tet_connectivity_matches_hand_count(dg):
     vP = vP.reshape(2, 4, 3)
     assert list(vP[0, 2]) == [4, 5, 6] and list(vP[1, 0]) == [1, 2, 3]
     assert (vP.reshape(-1) != vM).sum() == 6
+
+
+@pytest.mark.parametrize("n,block,seed", [(3, 20, 1), (4, 20, 2), (4, 7, 3), (2, 1, 4), (3, 1000, 5)])
+def test_partition_order_matches_oracle(dg, n, block, seed):
+    """dg_partition_order (C++) against the oracle's greedy partition: the same
+    permutation, element for element, on randomly renumbered box meshes."""
+    from oracle.partition import partition_order
+    verts, tets = kuhn_box_mesh(n, 0.1, seed)
+    tets = tets[np.random.Generator(np.random.PCG64(seed)).permutation(len(tets))]
+    mesh = dg.Mesh(verts, tets, 1)
+    got = mesh.partition_order(block)
+    want = partition_order(oracle.build_mesh(verts, tets, 1).EToE, block)
+    assert got.dtype == np.int64 and np.array_equal(got, want)
+
+
+def test_partition_order_errors(dg):
+    from paper_0901_1024_gb300._capi import load
+    verts, tets = kuhn_box_mesh(1, 0.0, 0)
+    mesh = dg.Mesh(verts, tets, 1)
+    lib = load()
+    perm = np.empty(mesh.K, np.int64)
+    ptr = perm.ctypes.data_as(C.POINTER(C.c_int64))
+    assert lib.dg_partition_order(mesh._h, 0, ptr) == -1
+    assert lib.dg_partition_order(mesh._h, 20, None) == -1
+    assert lib.dg_partition_order(None, 20, ptr) == -1
+    assert lib.dg_partition_order(mesh._h, 4, ptr) == 0
+    assert sorted(perm) == list(range(mesh.K))
