@@ -170,6 +170,23 @@ int dg_rhs(dg_mesh* mesh, const float* u, float* rhs, void* stream);
 int dg_step(dg_mesh* mesh, float* u, float* res, double dt, int nsteps, void* stream);
 
 /*
+ * One LSERK4 stage i (0..4) of size dt, with the coefficients a_i, b_i used by
+ * dg_step:
+ *   res <- a_i res + dt rhs(u_in);  u_out <- u_in + b_i res.
+ *   u_in  : device, [6][K][Np] FP32, read.
+ *   u_out : device, [6][K][Np] FP32, written; must not be u_in (the stage reads
+ *           neighbours' values of u_in while it writes u_out).
+ *   res   : device, [6][K][Np] FP32, in/out; a third buffer.
+ * Stages 0..4 with u_in and u_out swapped after each stage make one step
+ * (bit-identical to dg_step); a caller can act between stages, e.g. refresh
+ * ghost elements' face values in a domain decomposition.
+ * Asynchronous on `stream`.  Errors: DG_ERR_ARG (NULL, aliased buffers, stage
+ * outside 0..4, dt <= 0).
+ */
+int dg_rk_stage(dg_mesh* mesh, const float* u_in, float* u_out, float* res, int stage,
+                double dt, void* stream);
+
+/*
  * Discrete energy 1/2 sum_k J_k sum_c u_kc^T M u_kc (FP32 products, FP64
  * accumulation across elements) written to *out (host).
  *   u : device, [6][K][Np] FP32.

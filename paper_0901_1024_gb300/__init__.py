@@ -142,6 +142,12 @@ class Mesh:
         check(self._lib.dg_step(self._h, _devptr(u), _devptr(res), float(dt), int(nsteps),
                                 _stream_handle(stream)), "dg_step")
 
+    def rk_stage(self, u_in, u_out, res, stage: int, dt: float, stream=None):
+        """One LSERK4 stage (dg_rk_stage): res <- a_i res + dt rhs(u_in),
+        u_out <- u_in + b_i res."""
+        check(self._lib.dg_rk_stage(self._h, _devptr(u_in), _devptr(u_out), _devptr(res),
+                                    int(stage), float(dt), _stream_handle(stream)), "dg_rk_stage")
+
     def energy(self, u, stream=None) -> float:
         out = C.c_double()
         check(self._lib.dg_energy(self._h, _devptr(u), C.byref(out), _stream_handle(stream)),

@@ -31,6 +31,7 @@ SIGNATURES = {
     "dg_set_stage_impl": (C.c_int, [_vp, C.c_int]),
     "dg_rhs": (C.c_int, [_vp, _vp, _vp, _vp]),
     "dg_step": (C.c_int, [_vp, _vp, _vp, C.c_double, C.c_int, _vp]),
+    "dg_rk_stage": (C.c_int, [_vp, _vp, _vp, _vp, C.c_int, C.c_double, _vp]),
     "dg_energy": (C.c_int, [_vp, _vp, _dp, _vp]),
     "dg_energy_noalloc": (C.c_int, [_vp, _vp, _vp, _vp]),
     "dg_step_host": (C.c_int, [_vp, _vp, _vp, C.c_double, C.c_int, _dp, _vp]),

@@ -190,6 +190,19 @@ int dg_step(dg_mesh* m, float* u, float* res, double dt, int nsteps, void* strea
   return DG_OK;
 }
 
+int dg_rk_stage(dg_mesh* m, const float* u_in, float* u_out, float* res, int stage, double dt,
+                void* stream) {
+  if (int rc = check_mesh(m, true)) return rc;
+  if (!u_in || !u_out || !res) return fail(DG_ERR_ARG, "u_in, u_out or res is NULL");
+  if (u_in == u_out || res == u_in || res == u_out)
+    return fail(DG_ERR_ARG, "u_in, u_out and res must be three different buffers");
+  if (stage < 0 || stage > 4) return fail(DG_ERR_ARG, "stage must be 0..4");
+  if (!(dt > 0.0) || !std::isfinite(dt)) return fail(DG_ERR_ARG, "dt must be positive and finite");
+  std::string err;
+  if (int rc = dg::device_stage(m, u_in, u_out, res, stage, dt, stream, err)) return fail(rc, err);
+  return DG_OK;
+}
+
 int dg_energy(dg_mesh* m, const float* u, double* out, void* stream) {
   if (int rc = check_mesh(m, true)) return rc;
   if (!u || !out) return fail(DG_ERR_ARG, "u or out is NULL");

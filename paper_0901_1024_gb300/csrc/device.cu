@@ -537,6 +537,28 @@ static int step_impl(dg_mesh* m, float* u, float* res, double dt, int nsteps, cu
   return DG_OK;
 }
 
+int device_stage(dg_mesh* m, const float* u_in, float* u_out, float* res, int stage, double dt,
+                 void* stream, std::string& err) {
+  int rc = ensure_device(m, err);
+  if (rc) return rc;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  DeviceState* d = m->dev;
+  const bool tc = use_tc(m, {u_in, u_out, res});
+  dgdev::StageArgs a = stage_args(m, tc);
+  a.u_in = u_in;
+  a.u_out = u_out;
+  a.res = res;
+  a.dt = static_cast<float>(dt);
+  a.a = static_cast<float>(kRkA[stage]);
+  a.b = static_cast<float>(kRkB[stage]);
+  DG_CUDA(traced(m, s, tc ? 4 : 0, [&] {
+            return tc ? dgdev::launch_tc_stage(m->N, true, a, d->num_sms, s)
+                      : dgdev::launch_stage(m->N, true, a, d->num_sms, s);
+          }), "stage kernel launch");
+  m->last_launches = 1;
+  return DG_OK;
+}
+
 int device_step(dg_mesh* m, float* u, float* res, double dt, int nsteps, void* stream,
                 std::string& err) {
   int rc = ensure_device(m, err);

@@ -1,0 +1,122 @@
+"""Domain decomposition of one mesh (paper_0901_1024_gb300/domain.py) on CPU
+ranks: plan invariants, and 2- and 3-rank gloo runs whose per-rank stage is the
+FP64 oracle's LSERK4 stage on the rank's local mesh.  After the per-stage
+trace exchange every owned element must follow the single-domain oracle run.
+(The CUDA path runs the same driver with dg_rk_stage per rank; this pool gives
+one GPU per run, so the multi-rank path is tested here.)"""
+import os
+import socket
+
+import numpy as np
+import pytest
+
+import oracle
+from workloads import kuhn_box_mesh, random_fields
+
+torch = pytest.importorskip("torch")
+mp = pytest.importorskip("torch.multiprocessing")
+
+
+@pytest.fixture(scope="module")
+def dg():
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_0901_1024_gb300 as pkg
+    return pkg
+
+
+def _mesh(dg, n=3, N=2, seed=3):
+    verts, tets = kuhn_box_mesh(n, 0.1, seed)
+    tets = tets[np.random.Generator(np.random.PCG64(seed)).permutation(len(tets))]
+    return verts, tets, dg.Mesh(verts, tets, N)
+
+
+@pytest.mark.parametrize("world", [1, 2, 3, 5])
+def test_plans_cover_the_mesh_and_match_pairwise(dg, world):
+    from paper_0901_1024_gb300.domain import build_plans
+    verts, tets, mesh = _mesh(dg)
+    plans = build_plans(mesh, tets, world)
+    K, Np = mesh.K, mesh.Np
+    owned = np.concatenate([p.owned for p in plans])
+    assert sorted(owned) == list(range(K))
+    vM, vP = mesh.connectivity()
+    nb = {}
+    for a, b in zip(vM // Np, vP // Np):
+        nb.setdefault(int(a), set()).add(int(b))
+    for p in plans:
+        mine = set(p.owned.tolist())
+        assert not mine & set(p.ghosts.tolist())
+        assert np.array_equal(p.tets, tets[np.concatenate([p.owned, p.ghosts])])
+        needed = set().union(*(nb[k] for k in p.owned)) - mine
+        traced = {int(g) // Np for idx in p.recv.values() for g in
+                  np.concatenate([p.owned, p.ghosts])[idx // Np] * Np}
+        assert traced == needed <= set(p.ghosts.tolist())
+        assert p.n_local % 4 == 0 or p.n_local == K       # padded for bulk copies
+        assert len(p.ghosts) - len(needed) < 4
+        local = np.concatenate([p.owned, p.ghosts])
+        for q, idx in p.send.items():
+            back = plans[q].recv[p.rank]
+            glob_send = local[idx // Np] * Np + idx % Np
+            ql = np.concatenate([plans[q].owned, plans[q].ghosts])
+            glob_recv = ql[back // Np] * Np + back % Np
+            assert np.array_equal(glob_send, glob_recv)
+            assert np.all(idx // Np < p.n_owned) and np.all(back // Np >= plans[q].n_owned)
+    if world == 1:
+        assert len(plans[0].ghosts) == 0 and not plans[0].send
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank_main(rank, world, port, nsteps, q):
+    import torch.distributed as dist
+    import __graft_entry__  # noqa: F401  (library already built by the parent)
+    import paper_0901_1024_gb300 as dgp
+    from paper_0901_1024_gb300.domain import TraceExchange, build_plans, owned_energy, run_steps
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    verts, tets, mesh = _mesh(dgp)
+    plan = build_plans(mesh, tets, world)[rank]
+    om_glob = oracle.build_mesh(verts, tets, 2)
+    om = oracle.build_mesh(verts, plan.tets, 2)
+    a, b, _ = oracle.lserk4_coefficients()
+
+    def stage(src, dst, res, i, dt):
+        un, rn = oracle.stage_update(src.numpy(), res.numpy(), oracle.rhs(om, src.numpy()),
+                                     a[i], b[i], dt)
+        dst.copy_(torch.from_numpy(un))
+        res.copy_(torch.from_numpy(rn))
+
+    u0 = random_fields(mesh.K, mesh.Np, 17)
+    local = np.concatenate([plan.owned, plan.ghosts])
+    u = torch.from_numpy(np.ascontiguousarray(u0[:, local]))
+    res, work = torch.zeros_like(u), torch.zeros_like(u)
+    dt = oracle.cfl_dt(om_glob)
+    run_steps(TraceExchange(dist, plan, "cpu"), stage, u, res, work, dt, nsteps)
+    e = owned_energy(dist, plan, lambda v: oracle.energy(om, v.numpy()), u)
+    ug, _ = oracle.lserk4_run(om_glob, u0, dt, nsteps)
+    err = float(np.abs(u.numpy()[:, :plan.n_owned] - ug[:, plan.owned]).max() / np.abs(ug).max())
+    q.put((rank, err, e, oracle.energy(om_glob, ug), len(plan.ghosts)))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("world", [2, 3])
+def test_ranks_follow_the_single_domain_oracle(dg, world):
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_rank_main, args=(r, world, port, 2, q)) for r in range(world)]
+    for p in procs:
+        p.start()
+    got = sorted(q.get(timeout=300) for _ in procs)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    for rank, err, e, e_ref, n_ghost in got:
+        assert n_ghost > 0
+        assert err < 1e-13, (rank, err)
+        assert abs(e - e_ref) <= 1e-12 * e_ref

@@ -387,3 +387,71 @@ def test_full_size_step_sampled(env, full):
     ue, _ = oracle.lserk4_run(om, u0[:, patch].astype(np.float64), mesh.dt_cfl, 1)
     pos = np.searchsorted(patch, seeds)
     assert rel(got[:, seeds], ue[:, pos]) < RHS_TOL
+
+
+@pytest.mark.parametrize("impl", [FP32, TC])
+def test_rk_stages_equal_a_step(env, impl):
+    """Five dg_rk_stage calls with swapped buffers are bit-identical to dg_step."""
+    torch, dg = env
+    verts, tets = kuhn_box_mesh(4, 0.1, 3)
+    mesh = dg.Mesh(verts, tets, 4)
+    mesh.set_stage_impl(impl)
+    u0 = torch.from_numpy(random_fields(mesh.K, mesh.Np, 5).astype(np.float32)).cuda()
+    u, res = u0.clone(), torch.zeros_like(u0)
+    mesh.step(u, res, mesh.dt_cfl, 2)
+    a, b, r = u0.clone(), torch.empty_like(u0), torch.zeros_like(u0)
+    for _ in range(2):
+        for i in range(5):
+            mesh.rk_stage(a, b, r, i, mesh.dt_cfl)
+            a, b = b, a
+    mesh.set_stage_impl(0)
+    torch.cuda.synchronize()
+    assert torch.equal(a, u) and torch.equal(r, res)   # after each swap `a` holds the state
+
+
+@pytest.mark.parametrize("impl", [FP32, TC])
+def test_subdomains_in_lockstep_match_the_single_mesh(env, impl):
+    """Three subdomains of one mesh (domain.build_plans), each with its own
+    local mesh, stepped stage by stage on one GPU with their cut-face traces
+    copied between them before every stage: every owned element is bit-identical
+    to the single-mesh run (the same arithmetic, only ghost-held neighbours)."""
+    torch, dg = env
+    from paper_0901_1024_gb300.domain import build_plans
+    verts, tets = kuhn_box_mesh(6, 0.15, 4)
+    glob = dg.Mesh(verts, tets, 4)
+    glob.set_stage_impl(impl)
+    plans = build_plans(glob, tets, 3)
+    u0 = random_fields(glob.K, glob.Np, 21).astype(np.float32)
+    dt = glob.dt_cfl
+    ug, rg = torch.from_numpy(u0).cuda(), torch.zeros(u0.shape, device="cuda")
+    glob.step(ug, rg, dt, 2)
+    meshes, us, works, ress = [], [], [], []
+    for p in plans:
+        m = dg.Mesh(verts, p.tets, 4)
+        m.set_stage_impl(impl)
+        meshes.append(m)
+        us.append(torch.from_numpy(np.ascontiguousarray(u0[:, np.concatenate([p.owned, p.ghosts])])).cuda())
+        works.append(torch.empty_like(us[-1]))
+        ress.append(torch.zeros_like(us[-1]))
+    idx = [{q: torch.as_tensor(v, device="cuda") for q, v in p.send.items()} for p in plans]
+    ridx = [{q: torch.as_tensor(v, device="cuda") for q, v in p.recv.items()} for p in plans]
+    src, dst = us, works
+    for _ in range(2):
+        for i in range(5):
+            for p, u in zip(plans, src):
+                u[:, p.n_owned:, :] = 0
+            for r, p in enumerate(plans):
+                for q, ix in idx[r].items():
+                    src[q].view(6, -1).index_copy_(1, ridx[q][r], src[r].view(6, -1).index_select(1, ix))
+            for r, p in enumerate(plans):
+                ress[r][:, p.n_owned:, :] = 0
+                meshes[r].trace_enable(1)
+                meshes[r].rk_stage(src[r], dst[r], ress[r], i, dt)
+                assert _stage_kinds(meshes[r]) == ({4} if impl == TC else {0})
+            src, dst = dst, src
+    torch.cuda.synchronize()
+    glob.set_stage_impl(0)
+    full = ug.cpu().numpy()
+    for p, u, m in zip(plans, src, meshes):
+        assert p.n_local % 4 == 0
+        assert np.array_equal(u.cpu().numpy()[:, :p.n_owned], full[:, p.owned])
