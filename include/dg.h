@@ -79,6 +79,20 @@ int dg_mesh_create(const double* verts, int64_t nv, const int32_t* tets, int64_t
  */
 int dg_set_order(dg_mesh* mesh, int N);
 
+/*
+ * A new mesh that packs several meshes of the same order into one (the packed
+ * element table of a batch of independent solves): vertices, elements,
+ * geometry and connectivity are concatenated in the given order with vertex
+ * and element indices offset, so the result has count separate components and
+ * element k of meshes[i] becomes element k + (K of meshes[0..i-1]).  No face
+ * matching or geometry is recomputed.  Its dt_cfl is the smallest of theirs.
+ *   meshes : host array of count meshes with an order set (same N and flux).
+ *   out    : receives the new mesh; free it with dg_mesh_destroy().
+ * Errors: DG_ERR_ARG (NULL, count < 1, different orders or fluxes, too many
+ * elements), DG_ERR_STATE (a mesh without an order).  Host only.
+ */
+int dg_mesh_pack(const dg_mesh* const* meshes, int count, dg_mesh** out);
+
 /* K, Np = (N+1)(N+2)(N+3)/6, Nfp = (N+1)(N+2)/2 and the CFL step
  * dt = min_{k,f} (J_k / sJ_{k,f}) * 2/(N+1)^2.  Any output may be NULL. */
 int dg_info(const dg_mesh* mesh, int64_t* K, int* Np, int* Nfp, double* dt_cfl);
@@ -185,6 +199,18 @@ int dg_step(dg_mesh* mesh, float* u, float* res, double dt, int nsteps, void* st
  */
 int dg_rk_stage(dg_mesh* mesh, const float* u_in, float* u_out, float* res, int stage,
                 double dt, void* stream);
+
+/*
+ * dg_rk_stage with a time step per element: element k's update uses
+ * dt_elem[k] in place of dt.
+ *   dt_elem : device, [K] FP32, read; positive.
+ * For several independent solves packed into one mesh (disjoint vertex and
+ * element sets, each solve with its own step): every element's result is bit
+ * for bit its solve's dg_rk_stage result with dt = that float step.
+ * Asynchronous on `stream`.  Errors: as dg_rk_stage; dt_elem NULL.
+ */
+int dg_rk_stage_elem(dg_mesh* mesh, const float* u_in, float* u_out, float* res, int stage,
+                     const float* dt_elem, void* stream);
 
 /*
  * Discrete energy 1/2 sum_k J_k sum_c u_kc^T M u_kc (FP32 products, FP64

@@ -70,6 +70,26 @@ class Mesh:
         if N is not None:
             self.set_order(N)
 
+    @classmethod
+    def pack(cls, meshes):
+        """dg_mesh_pack: one mesh made of `meshes` (same order) side by side;
+        element k of meshes[i] becomes k + sum of the earlier meshes' K."""
+        lib = load()
+        arr = (C.c_void_p * len(meshes))(*[m._h.value for m in meshes])
+        h = C.c_void_p()
+        check(lib.dg_mesh_pack(arr, len(meshes), C.byref(h)), "dg_mesh_pack")
+        self = cls.__new__(cls)
+        self._lib, self._h = lib, h
+        return self._read_info(meshes[0].N)
+
+    def _read_info(self, N):
+        self.N = int(N)
+        K, Np, Nfp, dt = C.c_int64(), C.c_int(), C.c_int(), C.c_double()
+        check(self._lib.dg_info(self._h, C.byref(K), C.byref(Np), C.byref(Nfp), C.byref(dt)),
+              "dg_info")
+        self.K, self.Np, self.Nfp, self.dt_cfl = K.value, Np.value, Nfp.value, dt.value
+        return self
+
     def __del__(self):
         h = getattr(self, "_h", None)
         if h is not None and h.value:
@@ -81,12 +101,7 @@ class Mesh:
     # ---- host setup -------------------------------------------------------
     def set_order(self, N: int):
         check(self._lib.dg_set_order(self._h, int(N)), "dg_set_order")
-        self.N = int(N)
-        K, Np, Nfp, dt = C.c_int64(), C.c_int(), C.c_int(), C.c_double()
-        check(self._lib.dg_info(self._h, C.byref(K), C.byref(Np), C.byref(Nfp), C.byref(dt)),
-              "dg_info")
-        self.K, self.Np, self.Nfp, self.dt_cfl = K.value, Np.value, Nfp.value, dt.value
-        return self
+        return self._read_info(N)
 
     def set_flux(self, alpha: float):
         check(self._lib.dg_set_flux(self._h, float(alpha)), "dg_set_flux")
@@ -147,6 +162,13 @@ class Mesh:
         u_out <- u_in + b_i res."""
         check(self._lib.dg_rk_stage(self._h, _devptr(u_in), _devptr(u_out), _devptr(res),
                                     int(stage), float(dt), _stream_handle(stream)), "dg_rk_stage")
+
+    def rk_stage_elem(self, u_in, u_out, res, stage: int, dt_elem, stream=None):
+        """dg_rk_stage_elem: one LSERK4 stage with the per-element steps dt_elem
+        (a device FP32 tensor of K entries)."""
+        check(self._lib.dg_rk_stage_elem(self._h, _devptr(u_in), _devptr(u_out), _devptr(res),
+                                         int(stage), _devptr(dt_elem), _stream_handle(stream)),
+              "dg_rk_stage_elem")
 
     def energy(self, u, stream=None) -> float:
         out = C.c_double()

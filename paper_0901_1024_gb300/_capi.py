@@ -21,6 +21,7 @@ _vp = C.c_void_p
 SIGNATURES = {
     "dg_mesh_create": (C.c_int, [_dp, C.c_int64, _ip, C.c_int64, C.POINTER(_vp)]),
     "dg_set_order": (C.c_int, [_vp, C.c_int]),
+    "dg_mesh_pack": (C.c_int, [C.POINTER(_vp), C.c_int, C.POINTER(_vp)]),
     "dg_info": (C.c_int, [_vp, _i64p, _intp, _intp, _dp]),
     "dg_nodes": (C.c_int, [_vp, _dp]),
     "dg_get_connectivity": (C.c_int, [_vp, _ip, _ip]),
@@ -32,6 +33,7 @@ SIGNATURES = {
     "dg_rhs": (C.c_int, [_vp, _vp, _vp, _vp]),
     "dg_step": (C.c_int, [_vp, _vp, _vp, C.c_double, C.c_int, _vp]),
     "dg_rk_stage": (C.c_int, [_vp, _vp, _vp, _vp, C.c_int, C.c_double, _vp]),
+    "dg_rk_stage_elem": (C.c_int, [_vp, _vp, _vp, _vp, C.c_int, _vp, _vp]),
     "dg_energy": (C.c_int, [_vp, _vp, _dp, _vp]),
     "dg_energy_noalloc": (C.c_int, [_vp, _vp, _vp, _vp]),
     "dg_step_host": (C.c_int, [_vp, _vp, _vp, C.c_double, C.c_int, _dp, _vp]),

@@ -1,5 +1,6 @@
 // C ABI entry points (include/dg.h): argument checking, error reporting and
 // dispatch to the host setup (refelem.cpp, mesh.cpp) and device code (device.cu).
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -72,6 +73,60 @@ int dg_set_order(dg_mesh* m, int N) {
   double mn = INFINITY;
   for (double f : m->Fscale) mn = std::fmin(mn, 1.0 / f);
   m->dt_cfl = mn * 2.0 / ((N + 1.0) * (N + 1.0));
+  return DG_OK;
+}
+
+int dg_mesh_pack(const dg_mesh* const* meshes, int count, dg_mesh** out) {
+  if (!out) return fail(DG_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (!meshes || count < 1) return fail(DG_ERR_ARG, "need at least one mesh");
+  int64_t K = 0, nv = 0;
+  for (int i = 0; i < count; ++i) {
+    if (int rc = check_mesh(meshes[i], true)) return rc;
+    if (meshes[i]->N != meshes[0]->N) return fail(DG_ERR_ARG, "meshes of different orders");
+    if (meshes[i]->alpha != meshes[0]->alpha) return fail(DG_ERR_ARG, "meshes with different fluxes");
+    K += meshes[i]->K;
+    nv += meshes[i]->nv;
+  }
+  if (K >= (int64_t(1) << 31) / 220) return fail(DG_ERR_ARG, "K too large for 32-bit node ids");
+  dg_mesh* m = new (std::nothrow) dg_mesh();
+  if (!m) return fail(DG_ERR_OOM, "host allocation failed");
+  try {
+    m->K = K;
+    m->nv = nv;
+    m->N = meshes[0]->N;
+    m->ops = meshes[0]->ops;
+    m->alpha = meshes[0]->alpha;
+    m->dt_cfl = INFINITY;
+    m->verts.reserve(3 * nv);
+    m->tets.reserve(4 * K);
+    m->metric.assign(9 * K, 0.0);
+    m->normals.assign(3 * 4 * K, 0.0);
+    int64_t k0 = 0, v0 = 0;
+    for (int i = 0; i < count; ++i) {
+      const dg_mesh* s = meshes[i];
+      const int64_t Ks = s->K;
+      m->verts.insert(m->verts.end(), s->verts.begin(), s->verts.end());
+      for (int32_t v : s->tets) m->tets.push_back(static_cast<int32_t>(v + v0));
+      for (int a = 0; a < 9; ++a)
+        std::copy(s->metric.begin() + a * Ks, s->metric.begin() + (a + 1) * Ks,
+                  m->metric.begin() + a * K + k0);
+      m->J.insert(m->J.end(), s->J.begin(), s->J.end());
+      for (int d = 0; d < 3; ++d)
+        std::copy(s->normals.begin() + d * Ks * 4, s->normals.begin() + (d + 1) * Ks * 4,
+                  m->normals.begin() + (d * K + k0) * 4);
+      m->Fscale.insert(m->Fscale.end(), s->Fscale.begin(), s->Fscale.end());
+      for (int32_t e : s->nbr_elem) m->nbr_elem.push_back(static_cast<int32_t>(e + k0));
+      m->nbr_code.insert(m->nbr_code.end(), s->nbr_code.begin(), s->nbr_code.end());
+      m->dt_cfl = std::fmin(m->dt_cfl, s->dt_cfl);
+      k0 += Ks;
+      v0 += s->nv;
+    }
+  } catch (const std::bad_alloc&) {
+    delete m;
+    return fail(DG_ERR_OOM, "host allocation failed");
+  }
+  *out = m;
   return DG_OK;
 }
 
@@ -199,7 +254,22 @@ int dg_rk_stage(dg_mesh* m, const float* u_in, float* u_out, float* res, int sta
   if (stage < 0 || stage > 4) return fail(DG_ERR_ARG, "stage must be 0..4");
   if (!(dt > 0.0) || !std::isfinite(dt)) return fail(DG_ERR_ARG, "dt must be positive and finite");
   std::string err;
-  if (int rc = dg::device_stage(m, u_in, u_out, res, stage, dt, stream, err)) return fail(rc, err);
+  if (int rc = dg::device_stage(m, u_in, u_out, res, stage, dt, nullptr, stream, err))
+    return fail(rc, err);
+  return DG_OK;
+}
+
+int dg_rk_stage_elem(dg_mesh* m, const float* u_in, float* u_out, float* res, int stage,
+                     const float* dt_elem, void* stream) {
+  if (int rc = check_mesh(m, true)) return rc;
+  if (!u_in || !u_out || !res || !dt_elem)
+    return fail(DG_ERR_ARG, "u_in, u_out, res or dt_elem is NULL");
+  if (u_in == u_out || res == u_in || res == u_out)
+    return fail(DG_ERR_ARG, "u_in, u_out and res must be three different buffers");
+  if (stage < 0 || stage > 4) return fail(DG_ERR_ARG, "stage must be 0..4");
+  std::string err;
+  if (int rc = dg::device_stage(m, u_in, u_out, res, stage, 1.0, dt_elem, stream, err))
+    return fail(rc, err);
   return DG_OK;
 }
 

@@ -538,7 +538,7 @@ static int step_impl(dg_mesh* m, float* u, float* res, double dt, int nsteps, cu
 }
 
 int device_stage(dg_mesh* m, const float* u_in, float* u_out, float* res, int stage, double dt,
-                 void* stream, std::string& err) {
+                 const float* dt_elem, void* stream, std::string& err) {
   int rc = ensure_device(m, err);
   if (rc) return rc;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -549,6 +549,7 @@ int device_stage(dg_mesh* m, const float* u_in, float* u_out, float* res, int st
   a.u_out = u_out;
   a.res = res;
   a.dt = static_cast<float>(dt);
+  a.dt_elem = dt_elem;
   a.a = static_cast<float>(kRkA[stage]);
   a.b = static_cast<float>(kRkB[stage]);
   DG_CUDA(traced(m, s, tc ? 4 : 0, [&] {

@@ -36,6 +36,7 @@ struct StageArgs {
   int K;
   int num_tiles;
   float a, b, dt, alpha;
+  const float* dt_elem;    // RK mode: per-element time step [K], or null for dt
   // tensor-core path only
   const float* tcgeo;       // per tile: [kTcGeoWords][kTcTileElems] word-major geometry
   int tc_geo_stride;        // floats per tile block

@@ -80,7 +80,7 @@ void greedy_partition_order(const std::vector<int32_t>& nbr, int64_t K, int64_t 
 // device.cu (stream = cudaStream_t)
 int device_rhs(dg_mesh* m, const float* u, float* rhs, void* stream, std::string& err);
 int device_stage(dg_mesh* m, const float* u_in, float* u_out, float* res, int stage, double dt,
-                 void* stream, std::string& err);
+                 const float* dt_elem, void* stream, std::string& err);
 int device_step(dg_mesh* m, float* u, float* res, double dt, int nsteps, void* stream,
                 std::string& err);
 int device_energy(dg_mesh* m, const float* u, double* out, void* stream, std::string& err);

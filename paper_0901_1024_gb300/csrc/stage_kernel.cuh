@@ -230,7 +230,8 @@ __global__ void __launch_bounds__(StageDims<N>::T) stage_kernel(const StageArgs 
         const int ee = idx / Np, i = idx - ee * Np;
         const float r = sf[(c * E + ee) * US + i];
         if (RK) {
-          const float rn = fmaf(A.a, A.res[base + idx], A.dt * r);
+          const float dtk = A.dt_elem ? __ldg(A.dt_elem + k0 + ee) : A.dt;
+          const float rn = fmaf(A.a, A.res[base + idx], dtk * r);
           A.res[base + idx] = rn;
           A.u_out[base + idx] = fmaf(A.b, rn, su[(c * E + ee) * US + i]);
         } else {

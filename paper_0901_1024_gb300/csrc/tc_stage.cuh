@@ -361,6 +361,7 @@ __global__ void __launch_bounds__(TcDims<N>::THREADS, 1) tc_stage_kernel(const S
         tc::fence_before_sync();
         if (row < D::ROWS && re < Ev) {
           const float inv = A.tc_inv_bscale / sScale[(t & 3) * 128 + row];
+          const float dte = RK && A.dt_elem ? __ldg(A.dt_elem + k0 + re) : A.dt;
           float* pr = sr + (rc * E + re) * Np;
           float* pu = su + (rc * E + re) * Np;
           // u and res share one shared array, so every batch is loaded before any
@@ -386,7 +387,7 @@ __global__ void __launch_bounds__(TcDims<N>::THREADS, 1) tc_stage_kernel(const S
                   make_float2(__uint_as_float(acc[i0 + i]), __uint_as_float(acc[i0 + i1])), f2(inv));
               if (RK) {
                 const float2 rn = __ffma2_rn(f2(A.a), make_float2(rv[i], rv[i1]),
-                                             __fmul2_rn(f2(A.dt), r));
+                                             __fmul2_rn(f2(dte), r));
                 const float2 un = __ffma2_rn(f2(A.b), rn, make_float2(uv[i], uv[i1]));
                 pr[i0 + i] = rn.x;
                 pu[i0 + i] = un.x;
