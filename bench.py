@@ -377,6 +377,67 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def serve_requests(count, rate, seed):
+    """Seeded request stream: Poisson arrivals at `rate` per second; box meshes
+    of n^3 x 6 tets (n uniform in 4..10, jitter 0.1h), orders N uniform in 1..6,
+    end times T uniform in [0.1, 0.5], Gaussian pulse of width 0.3 at a seeded
+    centre."""
+    from paper_0901_1024_gb300.serve import Request
+    rng = np.random.Generator(np.random.PCG64(seed))
+    t, reqs = 0.0, []
+    for rid in range(count):
+        t += rng.exponential(1.0 / rate)
+        n, N, T = int(rng.integers(4, 11)), int(rng.integers(1, 7)), float(rng.uniform(0.1, 0.5))
+        c = tuple(rng.uniform(-0.5, 0.5, 3))
+        verts, tets = kuhn_box_mesh(n, 0.1, 1000 + rid)
+        reqs.append(Request(rid, verts, tets, N, T,
+                            lambda x, c=c: gaussian_pulse(x[0], x[1], x[2], 0.3, c), arrival=t))
+    return reqs
+
+
+def run_serve(args):
+    """Served solves/s and latency percentiles of a request stream: the
+    continuous-batching server (packed launches, CUDA graphs, autotuned stage
+    kernels) against the plain per-solve form (one solve at a time, its own
+    launches) on the same stream."""
+    import torch
+    from paper_0901_1024_gb300.serve import Server
+    reqs = serve_requests(args.requests, args.rate, 5)
+    Server(autotune=True).run(serve_requests(4, 1e9, 99), max_iterations=10**6)   # warm-up
+
+    def summary(results, wall):
+        lat = np.array([r.latency for r in results])
+        return {"solves_per_s": len(results) / wall, "p50_latency_s": float(np.percentile(lat, 50)),
+                "p99_latency_s": float(np.percentile(lat, 99)), "wall_s": wall,
+                "dof_updates": int(sum(6 * r.K * ((r.N + 1) * (r.N + 2) * (r.N + 3) // 6) * 5 * r.steps
+                                       for r in results))}
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    srv = Server(batch=True, graphs=not args.serve_no_graphs, autotune=True,
+                 rebuild_every=args.rebuild_every)
+    served = srv.run(reqs, max_iterations=10**7)
+    ours = summary(served, time.perf_counter() - t0)
+    ours["host_phases"] = srv.stats
+    t0 = time.perf_counter()
+    one = Server(hbm_budget=1.0, batch=False, graphs=False, autotune=False)
+    plain = one.run(reqs, max_iterations=10**7)
+    base = summary(plain, time.perf_counter() - t0)
+    base["host_phases"] = one.stats
+    worst = max(float(np.linalg.norm(a.fields - b.fields) / max(np.linalg.norm(b.fields), 1e-30))
+                for a, b in zip(served, plain))
+    line = {"metric": "served solves/s", "value": ours["solves_per_s"], "unit": "solves/s",
+            "higher_is_better": True, "n_gpus": 1, "dtype": "f32 (FP16x3 tensor cores for N<=4)",
+            "data": "synthetic", "mode": "serve",
+            "config": {"workload": f"{args.requests} requests, Poisson {args.rate}/s, n in 4..10, "
+                                   "N in 1..6, T in [0.1, 0.5], Gaussian pulse",
+                       "server": "continuous batching: one packed launch per RK stage and order, "
+                                 "CUDA graphs, autotuned stage kernel per (N, K)"},
+            "served": ours, "one_at_a_time": base,
+            "speedup_solves_per_s": ours["solves_per_s"] / base["solves_per_s"],
+            "max_rel_l2_vs_one_at_a_time": worst}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -386,6 +447,13 @@ def main():
     ap.add_argument("--workload", default="pulse_n24_N4", choices=sorted(WORKLOADS))
     ap.add_argument("--order", default="native", choices=["native", "shuffled", "partition"],
                     help="element numbering of the timed mesh (see element_order)")
+    ap.add_argument("--mode", default="stage", choices=["stage", "serve"],
+                    help="stage: the RK-stage benchmark (default); serve: the request-stream benchmark")
+    ap.add_argument("--requests", type=int, default=48)
+    ap.add_argument("--rebuild-every", type=int, default=32,
+                    help="serve mode: steps a pack runs before waiting solves join it")
+    ap.add_argument("--serve-no-graphs", action="store_true")
+    ap.add_argument("--rate", type=float, default=200.0)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
@@ -393,6 +461,8 @@ def main():
     args.warmup = max(args.warmup, 3)          # at least 3 untimed warm-up steps
     if args.impl == "reference":
         run_reference(args)
+    elif args.mode == "serve":
+        run_serve(args)
     else:
         run_ours(args)
 

@@ -221,6 +221,14 @@ int dg_rk_stage_elem(dg_mesh* mesh, const float* u_in, float* u_out, float* res,
 int dg_energy(dg_mesh* mesh, const float* u, double* out, void* stream);
 
 /*
+ * The energy of elements k0 <= k < k1 only, e.g. one solve of a packed mesh
+ * (dg_mesh_pack); the same reduction as dg_energy, which is the range 0..K.
+ * Errors: as dg_energy; DG_ERR_ARG unless 0 <= k0 < k1 <= K.
+ */
+int dg_energy_range(dg_mesh* mesh, const float* u, int64_t k0, int64_t k1, double* out,
+                    void* stream);
+
+/*
  * End-to-end convenience: copy host fields to the device, advance nsteps
  * LSERK4 steps, copy the fields back and (if energy != NULL) compute the
  * energy of the result.

@@ -176,6 +176,13 @@ class Mesh:
               "dg_energy")
         return out.value
 
+    def energy_range(self, u, k0: int, k1: int, stream=None) -> float:
+        """dg_energy_range: the energy of elements k0 <= k < k1."""
+        out = C.c_double()
+        check(self._lib.dg_energy_range(self._h, _devptr(u), int(k0), int(k1), C.byref(out),
+                                        _stream_handle(stream)), "dg_energy_range")
+        return out.value
+
     def energy_noalloc(self, u, out, stream=None):
         """Energy into the device double `out` (a CUDA tensor or pointer); allocates nothing."""
         check(self._lib.dg_energy_noalloc(self._h, _devptr(u), _devptr_any(out),

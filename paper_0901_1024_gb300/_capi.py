@@ -35,6 +35,7 @@ SIGNATURES = {
     "dg_rk_stage": (C.c_int, [_vp, _vp, _vp, _vp, C.c_int, C.c_double, _vp]),
     "dg_rk_stage_elem": (C.c_int, [_vp, _vp, _vp, _vp, C.c_int, _vp, _vp]),
     "dg_energy": (C.c_int, [_vp, _vp, _dp, _vp]),
+    "dg_energy_range": (C.c_int, [_vp, _vp, C.c_int64, C.c_int64, _dp, _vp]),
     "dg_energy_noalloc": (C.c_int, [_vp, _vp, _vp, _vp]),
     "dg_step_host": (C.c_int, [_vp, _vp, _vp, C.c_double, C.c_int, _dp, _vp]),
     "dg_last_launch_count": (C.c_int64, [_vp]),

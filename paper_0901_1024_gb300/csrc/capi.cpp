@@ -3,6 +3,8 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <new>
 #include <string>
 
@@ -62,13 +64,21 @@ int dg_set_order(dg_mesh* m, int N) {
   if (int rc = check_mesh(m, false)) return rc;
   if (N < 1 || N > dg::kMaxOrder) return fail(DG_ERR_ORDER, "order N must be in 1..9");
   std::string err;
-  dg::RefOps ops;
+  // the reference operators depend on N only: built once per order and copied
+  static std::mutex ops_mutex;
+  static std::map<int, dg::RefOps> ops_cache;
   try {
-    if (!dg::build_ref_ops(N, ops, err)) return fail(DG_ERR_ORDER, err);
+    std::lock_guard<std::mutex> lock(ops_mutex);
+    auto it = ops_cache.find(N);
+    if (it == ops_cache.end()) {
+      dg::RefOps ops;
+      if (!dg::build_ref_ops(N, ops, err)) return fail(DG_ERR_ORDER, err);
+      it = ops_cache.emplace(N, std::move(ops)).first;
+    }
+    m->ops = it->second;
   } catch (const std::bad_alloc&) {
     return fail(DG_ERR_OOM, "host allocation failed");
   }
-  m->ops = std::move(ops);
   m->N = N;
   double mn = INFINITY;
   for (double f : m->Fscale) mn = std::fmin(mn, 1.0 / f);
@@ -270,6 +280,16 @@ int dg_rk_stage_elem(dg_mesh* m, const float* u_in, float* u_out, float* res, in
   std::string err;
   if (int rc = dg::device_stage(m, u_in, u_out, res, stage, 1.0, dt_elem, stream, err))
     return fail(rc, err);
+  return DG_OK;
+}
+
+int dg_energy_range(dg_mesh* m, const float* u, int64_t k0, int64_t k1, double* out,
+                    void* stream) {
+  if (int rc = check_mesh(m, true)) return rc;
+  if (!u || !out) return fail(DG_ERR_ARG, "u or out is NULL");
+  if (k0 < 0 || k1 <= k0 || k1 > m->K) return fail(DG_ERR_ARG, "need 0 <= k0 < k1 <= K");
+  std::string err;
+  if (int rc = dg::device_energy_range(m, u, k0, k1, out, stream, err)) return fail(rc, err);
   return DG_OK;
 }
 

@@ -6,6 +6,8 @@
 #include <cmath>
 #include <cstring>
 #include <string>
+#include <map>
+#include <mutex>
 #include <vector>
 
 #include <cuda_fp16.h>
@@ -67,16 +69,17 @@ __global__ void __launch_bounds__(kEnergyRows) energy_rows_kernel(const EnergyAr
     const int r = i / NP4, c = i - r * NP4;
     sM[i] = c < NP ? __ldg(A.M + r * NP + c) : 0.f;
   }
-  const int64_t rows = int64_t(6) * A.K;
+  // rows (c, k) for k0 <= k < k1, numbered c * Kr + (k - k0)
+  const int64_t Kr = A.k1 - A.k0, rows = 6 * Kr;
   double acc = 0.0;
   for (int64_t r0 = int64_t(blockIdx.x) * kEnergyRows; r0 < rows;
        r0 += int64_t(gridDim.x) * kEnergyRows) {
     const int nr = int(rows - r0 < kEnergyRows ? rows - r0 : kEnergyRows);
     __syncthreads();                     // previous pass done with sU (and sM written)
-    const float* src = A.u + r0 * NP;
     for (int i = threadIdx.x; i < nr * NP; i += kEnergyRows) {
       const int r = i / NP;
-      sU[r * RS + (i - r * NP)] = __ldg(src + i);
+      const int64_t g = r0 + r, c = g / Kr;
+      sU[r * RS + (i - r * NP)] = __ldg(A.u + (c * A.K + A.k0 + (g - c * Kr)) * NP + (i - r * NP));
     }
     __syncthreads();
     const int r = threadIdx.x;
@@ -99,7 +102,7 @@ __global__ void __launch_bounds__(kEnergyRows) energy_rows_kernel(const EnergyAr
         }
         e = fmaf(sU[r * RS + i], s, e);
       }
-      const int64_t k = (r0 + r) % A.K;
+      const int64_t k = A.k0 + (r0 + r) % Kr;
       const float J = reinterpret_cast<const float*>(A.geo)[k * kGeoWords + 9];
       acc += double(J) * double(e);
     }
@@ -122,7 +125,7 @@ __global__ void __launch_bounds__(kEnergyThreads) energy_kernel(const EnergyArgs
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   constexpr int nw = kEnergyThreads / 32;
   double acc = 0.0;
-  for (int k = blockIdx.x * nw + warp; k < A.K; k += gridDim.x * nw) {
+  for (int k = A.k0 + blockIdx.x * nw + warp; k < A.k1; k += gridDim.x * nw) {
     float ek = 0.f;
     for (int c = 0; c < 6; ++c) {
       const float* uk = A.u + (size_t(c) * A.K + k) * A.Np;
@@ -219,6 +222,8 @@ struct DeviceState {
   int tc_geo_stride = 0;
   float tc_inv_bscale = 1.f;
   int* status = nullptr;        // pipeline status word (0 = ok)
+  void* arena = nullptr;        // one allocation: geo, tcgeo, status, partials, result
+  // D4, LIFT4, M, fmask, perm and tcB belong to the per-(device, order) cache
   // per-launch tracing: event pair 2i, 2i+1 around launch i
   std::vector<cudaEvent_t> ev;
   std::vector<int> kind;
@@ -230,10 +235,7 @@ void destroy_device_state(DeviceState* d) {
   int cur = -1;
   cudaGetDevice(&cur);
   if (d->device >= 0) cudaSetDevice(d->device);
-  cudaFree(d->geo); cudaFree(d->D4); cudaFree(d->LIFT4); cudaFree(d->M);
-  cudaFree(d->fmask); cudaFree(d->perm); cudaFree(d->u_work); cudaFree(d->h_u);
-  cudaFree(d->h_res); cudaFree(d->partials); cudaFree(d->result);
-  cudaFree(d->tcB); cudaFree(d->tcgeo); cudaFree(d->status);
+  cudaFree(d->arena); cudaFree(d->u_work); cudaFree(d->h_u); cudaFree(d->h_res);
   for (cudaEvent_t e : d->ev) cudaEventDestroy(e);
   if (cur >= 0) cudaSetDevice(cur);
   delete d;
@@ -317,55 +319,39 @@ int device_trace_read(dg_mesh* m, double* ms, int32_t* kind, int64_t cap, int64_
   return DG_OK;
 }
 
-// Creates (or re-creates after an order change) the device copy of the mesh.
-int ensure_device(dg_mesh* m, std::string& err) {
-  if (m->N == 0) { err = "dg_set_order() has not been called"; return DG_ERR_STATE; }
-  int cur = 0;
-  DG_CUDA(cudaGetDevice(&cur), "cudaGetDevice");
-  if (m->dev && m->dev->N == m->N && m->dev->device == cur) return DG_OK;
-  if (m->dev) { dgdev::destroy_device_state(m->dev); m->dev = nullptr; }
-  auto* d = new DeviceState();
-  m->dev = d;
-  d->device = cur;
-  d->N = m->N;
-  d->K = m->K;
-  d->Np = m->ops.Np;
-  d->Nfp = m->ops.Nfp;
-  DG_CUDA(cudaDeviceGetAttribute(&d->num_sms, cudaDevAttrMultiProcessorCount, cur),
-          "cudaDeviceGetAttribute");
-  const int64_t K = m->K;
-  const int Np = d->Np, Nfp = d->Nfp, NF = 4 * Nfp;
+// Order-dependent device operators, shared by every mesh of that order on a
+// device (built once, kept for the life of the process): Dr/Ds/Dt as float4
+// rows, LIFT, M, the face-node tables and the tensor-core B pieces.
+struct OrderOps {
+  float4* D4 = nullptr;
+  float4* LIFT4 = nullptr;
+  float* M = nullptr;
+  unsigned char* fmask = nullptr;
+  unsigned char* perm = nullptr;
+  void* tcB = nullptr;
+  float tc_inv_bscale = 1.f;
+};
 
-  // geometry records
-  std::vector<float> geo(static_cast<size_t>(K) * dgdev::kGeoWords, 0.f);
-  for (int64_t k = 0; k < K; ++k) {
-    float* g = &geo[k * dgdev::kGeoWords];
-    for (int a = 0; a < 9; ++a) g[a] = static_cast<float>(m->metric[a * K + k]);
-    g[9] = static_cast<float>(m->J[k]);
-    uint32_t codes = 0;
-    for (int f = 0; f < 4; ++f) {
-      const int c = m->nbr_code[4 * k + f];
-      codes |= static_cast<uint32_t>(c + 1) << (8 * f);
-      for (int dd = 0; dd < 3; ++dd)
-        g[12 + 4 * f + dd] = static_cast<float>(m->normals[(dd * K + k) * 4 + f]);
-      g[15 + 4 * f] = static_cast<float>(m->Fscale[4 * k + f]);
-      const int32_t nb = m->nbr_elem[4 * k + f];
-      std::memcpy(&g[28 + f], &nb, 4);
-    }
-    std::memcpy(&g[10], &codes, 4);
+static std::mutex g_ops_mutex;
+static std::map<std::pair<int, int>, OrderOps> g_ops;
+
+static int order_ops(const dg_mesh* m, int dev, OrderOps& out, std::string& err) {
+  std::lock_guard<std::mutex> lock(g_ops_mutex);
+  auto it = g_ops.find({dev, m->N});
+  if (it != g_ops.end()) {
+    out = it->second;
+    return DG_OK;
   }
-  std::vector<float4> geo4(static_cast<size_t>(K) * dgdev::kGeoWords / 4);
-  std::memcpy(geo4.data(), geo.data(), geo.size() * sizeof(float));
-  int rc = upload(&d->geo, geo4, err);
-  if (rc) return rc;
-
+  OrderOps o;
+  const int Np = m->ops.Np, NF = 4 * m->ops.Nfp;
   std::vector<float4> D4(static_cast<size_t>(Np) * Np);
   for (int i = 0; i < Np; ++i)
     for (int j = 0; j < Np; ++j)
       D4[i * Np + j] = make_float4(static_cast<float>(m->ops.Dr[i * Np + j]),
                                    static_cast<float>(m->ops.Ds[i * Np + j]),
                                    static_cast<float>(m->ops.Dt[i * Np + j]), 0.f);
-  if ((rc = upload(&d->D4, D4, err))) return rc;
+  int rc;
+  if ((rc = upload(&o.D4, D4, err))) return rc;
   std::vector<float4> L4(static_cast<size_t>(Np) * NF / 4);
   for (int i = 0; i < Np; ++i)
     for (int q = 0; q < NF / 4; ++q)
@@ -373,14 +359,14 @@ int ensure_device(dg_mesh* m, std::string& err) {
                                          static_cast<float>(m->ops.LIFT[i * NF + 4 * q + 1]),
                                          static_cast<float>(m->ops.LIFT[i * NF + 4 * q + 2]),
                                          static_cast<float>(m->ops.LIFT[i * NF + 4 * q + 3]));
-  if ((rc = upload(&d->LIFT4, L4, err))) return rc;
+  if ((rc = upload(&o.LIFT4, L4, err))) return rc;
   std::vector<float> Mf(m->ops.M.begin(), m->ops.M.end());
-  if ((rc = upload(&d->M, Mf, err))) return rc;
+  if ((rc = upload(&o.M, Mf, err))) return rc;
   std::vector<unsigned char> fm(m->ops.Fmask.begin(), m->ops.Fmask.end());
-  if ((rc = upload(&d->fmask, fm, err))) return rc;
+  if ((rc = upload(&o.fmask, fm, err))) return rc;
   std::vector<unsigned char> pm(m->ops.perm.begin(), m->ops.perm.end());
-  if ((rc = upload(&d->perm, pm, err))) return rc;
-  if (d->N <= dgdev::kTcMaxOrder) {
+  if ((rc = upload(&o.perm, pm, err))) return rc;
+  if (m->N <= dgdev::kTcMaxOrder) {
     // B = [Dr Ds Dt LIFT] (Np x KT, zero padded), scaled by 2^p, split into FP16
     // hi + lo, stored in the canonical K-major core-matrix layout.
     const int KB = (Np + 1) & ~1, KT = (3 * KB + NF + 15) & ~15, NN = (Np + 15) & ~15;
@@ -400,7 +386,7 @@ int ensure_device(dg_mesh* m, std::string& err) {
         mx = std::max(mx, std::fabs(v));
       }
     const double sB = std::ldexp(1.0, static_cast<int>(std::floor(std::log2(16384.0 / mx))));
-    d->tc_inv_bscale = static_cast<float>(1.0 / sB);
+    o.tc_inv_bscale = static_cast<float>(1.0 / sB);
     const size_t piece = static_cast<size_t>(NN) * KT;
     std::vector<__half> P(2 * piece);
     for (int n = 0; n < NN; ++n)
@@ -412,15 +398,82 @@ int ensure_device(dg_mesh* m, std::string& err) {
         P[off] = hi;
         P[piece + off] = lo;
       }
-    if ((rc = upload(reinterpret_cast<__half**>(&d->tcB), P, err))) return rc;
+    if ((rc = upload(reinterpret_cast<__half**>(&o.tcB), P, err))) return rc;
+  }
+  g_ops[{dev, m->N}] = o;
+  out = o;
+  return DG_OK;
+}
+
+// Creates (or re-creates after an order change) the device copy of the mesh:
+// the shared order operators plus one arena holding this mesh's geometry
+// records, its tiled tensor-core geometry, the status word and the energy
+// partial sums (one allocation, one copy).
+int ensure_device(dg_mesh* m, std::string& err) {
+  if (m->N == 0) { err = "dg_set_order() has not been called"; return DG_ERR_STATE; }
+  int cur = 0;
+  DG_CUDA(cudaGetDevice(&cur), "cudaGetDevice");
+  if (m->dev && m->dev->N == m->N && m->dev->device == cur) return DG_OK;
+  if (m->dev) { dgdev::destroy_device_state(m->dev); m->dev = nullptr; }
+  auto* d = new DeviceState();
+  m->dev = d;
+  d->device = cur;
+  d->N = m->N;
+  d->K = m->K;
+  d->Np = m->ops.Np;
+  d->Nfp = m->ops.Nfp;
+  DG_CUDA(cudaDeviceGetAttribute(&d->num_sms, cudaDevAttrMultiProcessorCount, cur),
+          "cudaDeviceGetAttribute");
+  OrderOps ops;
+  int rc = order_ops(m, cur, ops, err);
+  if (rc) return rc;
+  d->D4 = ops.D4;
+  d->LIFT4 = ops.LIFT4;
+  d->M = ops.M;
+  d->fmask = ops.fmask;
+  d->perm = ops.perm;
+  d->tcB = ops.tcB;
+  d->tc_inv_bscale = ops.tc_inv_bscale;
+  const int64_t K = m->K;
+  const int Nfp = d->Nfp, NF = 4 * Nfp;
+  const bool tc = d->N <= dgdev::kTcMaxOrder;
+  constexpr int E = dgdev::kTcTileElems;
+  const int64_t ntiles = (K + E - 1) / E;
+  d->tc_geo_stride = tc ? dgdev::tc_geo_floats(d->N) : 0;
+  d->egrid = dgdev::energy_grid(d->num_sms);
+  // arena layout (bytes, each part 256-byte aligned)
+  auto up = [](size_t x) { return (x + 255) & ~size_t(255); };
+  const size_t geo_b = static_cast<size_t>(K) * dgdev::kGeoWords * 4;
+  const size_t tcg_b = tc ? static_cast<size_t>(ntiles) * d->tc_geo_stride * 4 : 0;
+  const size_t o_tcg = up(geo_b), o_part = o_tcg + up(tcg_b);
+  const size_t o_res = o_part + up(sizeof(double) * d->egrid), o_stat = o_res + 256;
+  const size_t total = o_stat + 256;
+  std::vector<unsigned char> host(o_part, 0);
+
+  // geometry records
+  float* geo = reinterpret_cast<float*>(host.data());
+  for (int64_t k = 0; k < K; ++k) {
+    float* g = &geo[k * dgdev::kGeoWords];
+    for (int a = 0; a < 9; ++a) g[a] = static_cast<float>(m->metric[a * K + k]);
+    g[9] = static_cast<float>(m->J[k]);
+    uint32_t codes = 0;
+    for (int f = 0; f < 4; ++f) {
+      const int c = m->nbr_code[4 * k + f];
+      codes |= static_cast<uint32_t>(c + 1) << (8 * f);
+      for (int dd = 0; dd < 3; ++dd)
+        g[12 + 4 * f + dd] = static_cast<float>(m->normals[(dd * K + k) * 4 + f]);
+      g[15 + 4 * f] = static_cast<float>(m->Fscale[4 * k + f]);
+      const int32_t nb = m->nbr_elem[4 * k + f];
+      std::memcpy(&g[28 + f], &nb, 4);
+    }
+    std::memcpy(&g[10], &codes, 4);
+  }
+  if (tc) {
     // tiled geometry, one contiguous block per tile: word-major [kTcGeoWords][E]
     // (record words {0..8 metric, 10 codes, 12..27 faces, 28..31 neighbours} ->
     // words {0..8, 9, 10..25, 26..29}), then one byte per face node (e, m):
     // the node of the neighbour across face m / Nfp that matches it (0 on walls)
-    constexpr int E = dgdev::kTcTileElems;
-    const int64_t ntiles = (K + E - 1) / E;
-    d->tc_geo_stride = dgdev::tc_geo_floats(d->N);
-    std::vector<float> tg(static_cast<size_t>(ntiles) * d->tc_geo_stride, 0.f);
+    float* tg = reinterpret_cast<float*>(host.data() + o_tcg);
     for (int64_t k = 0; k < K; ++k) {
       float* blk = &tg[(k / E) * d->tc_geo_stride];
       for (int w = 0; w < dgdev::kTcGeoWords; ++w) {
@@ -435,13 +488,16 @@ int ensure_device(dg_mesh* m, std::string& err) {
               c < 0 ? 0 : static_cast<unsigned char>(m->ops.perm[(f * 24 + c) * Nfp + j]);
       }
     }
-    if ((rc = upload(&d->tcgeo, tg, err))) return rc;
   }
-  DG_CUDA(cudaMalloc(&d->status, sizeof(int)), "cudaMalloc");
-  DG_CUDA(cudaMemset(d->status, 0, sizeof(int)), "cudaMemset");
-  d->egrid = dgdev::energy_grid(d->num_sms);
-  DG_CUDA(cudaMalloc(&d->partials, sizeof(double) * d->egrid), "cudaMalloc");
-  DG_CUDA(cudaMalloc(&d->result, sizeof(double)), "cudaMalloc");
+  DG_CUDA(cudaMalloc(&d->arena, total), "cudaMalloc");
+  unsigned char* base = static_cast<unsigned char*>(d->arena);
+  DG_CUDA(cudaMemcpy(base, host.data(), host.size(), cudaMemcpyHostToDevice), "cudaMemcpy H2D");
+  DG_CUDA(cudaMemset(base + o_stat, 0, 256), "cudaMemset");
+  d->geo = reinterpret_cast<float4*>(base);
+  d->tcgeo = tc ? reinterpret_cast<float*>(base + o_tcg) : nullptr;
+  d->partials = reinterpret_cast<double*>(base + o_part);
+  d->result = reinterpret_cast<double*>(base + o_res);
+  d->status = reinterpret_cast<int*>(base + o_stat);
   return DG_OK;
 }
 
@@ -580,9 +636,10 @@ static int check_status(dg_mesh* m, std::string& err) {
 }
 
 static int energy_impl(dg_mesh* m, const float* u, double* out, cudaStream_t s,
-                       std::string& err) {
+                       std::string& err, int64_t k0 = 0, int64_t k1 = -1) {
   DeviceState* d = m->dev;
-  dgdev::EnergyArgs a{u, d->M, d->geo, static_cast<int>(d->K), d->Np, d->partials, d->result};
+  dgdev::EnergyArgs a{u, d->M, d->geo, static_cast<int>(d->K), d->Np, d->partials, d->result,
+                      static_cast<int>(k0), static_cast<int>(k1 < 0 ? d->K : k1)};
   DG_CUDA(traced(m, s, 2, [&] { return dgdev::launch_energy_partials(a, d->egrid, s); }),
           "energy kernel launch");
   DG_CUDA(traced(m, s, 3, [&] { return dgdev::launch_energy_final(a, d->egrid, s); }),
@@ -613,6 +670,13 @@ int device_resident(const dg_mesh* m, const float** M, const void** geo, int64_t
   *K = d->K;
   *Np = d->Np;
   return DG_OK;
+}
+
+int device_energy_range(dg_mesh* m, const float* u, int64_t k0, int64_t k1, double* out,
+                        void* stream, std::string& err) {
+  int rc = ensure_device(m, err);
+  if (rc) return rc;
+  return energy_impl(m, u, out, static_cast<cudaStream_t>(stream), err, k0, k1);
 }
 
 int device_energy(dg_mesh* m, const float* u, double* out, void* stream, std::string& err) {

@@ -75,6 +75,7 @@ struct EnergyArgs {
   int K, Np;
   double* partials;    // [grid]
   double* result;      // [1]
+  int k0, k1;          // elements k0 <= k < k1 (0, K: the whole mesh)
 };
 int energy_grid(int num_sms);
 cudaError_t launch_energy_partials(const EnergyArgs& a, int grid, cudaStream_t s);

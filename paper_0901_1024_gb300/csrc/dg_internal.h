@@ -84,6 +84,8 @@ int device_stage(dg_mesh* m, const float* u_in, float* u_out, float* res, int st
 int device_step(dg_mesh* m, float* u, float* res, double dt, int nsteps, void* stream,
                 std::string& err);
 int device_energy(dg_mesh* m, const float* u, double* out, void* stream, std::string& err);
+int device_energy_range(dg_mesh* m, const float* u, int64_t k0, int64_t k1, double* out,
+                        void* stream, std::string& err);
 int device_step_host(dg_mesh* m, float* u, float* res, double dt, int nsteps, double* energy,
                      void* stream, std::string& err);
 int device_trace_reset(dg_mesh* m, int reserve, std::string& err);

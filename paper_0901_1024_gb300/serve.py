@@ -79,6 +79,7 @@ class _Live:
         self.admitted = now
         self.u0 = np.ascontiguousarray(req.init(self.mesh.nodes()), dtype=np.float32)
         self.offset = 0
+        self.finished = False
         self.bytes = solve_bytes(self.K, self.Np)
 
 
@@ -87,6 +88,8 @@ class _Pack:
 
     def __init__(self, torch, N, solves, old, padding, impl, graphs, stream):
         self.N, self.solves = N, list(solves)
+        self.alive = len(self.solves)
+        self.built_at = 0
         meshes = [s.mesh for s in self.solves]
         Np = meshes[0].Np
         K = sum(m.K for m in meshes)
@@ -165,17 +168,24 @@ class Server:
     graphs     : replay each pack's step from a CUDA graph.
     autotune   : pick each pack's stage implementation by timing; else `impl`.
     keep_fields: return every solve's final fields (host FP32) in its Result.
+    rebuild_every: steps a pack runs before waiting solves may join it.
     """
 
     def __init__(self, hbm_budget: float = 150e9, batch: bool = True, graphs: bool = True,
-                 autotune: bool = True, impl: int = Mesh.STAGE_AUTO, keep_fields: bool = True):
+                 autotune: bool = True, impl: int = Mesh.STAGE_AUTO, keep_fields: bool = True,
+                 rebuild_every: int = 32):
         import torch
         self.torch = torch
         self.budget, self.batch, self.graphs = hbm_budget, batch, graphs
+        self.rebuild_every = rebuild_every
         self.autotune, self.impl, self.keep = autotune, impl, keep_fields
         self.stream = torch.cuda.Stream()
         self._padding = {}
         self._tuned = {}
+        # host seconds per phase of the last run: admitting (mesh setup),
+        # packing (pack build, device setup, graph capture, tuning), stepping,
+        # retiring (energy, copy-out); and how many packs were built
+        self.stats = {}
 
     # ---- stage implementation per (N, K) ---------------------------------
     def _pad_mesh(self, N):
@@ -190,7 +200,7 @@ class Server:
         if N > 4:
             return Mesh.STAGE_FP32
         K = sum(s.K for s in solves)
-        key = (N, int(round(math.log2(max(K, 1)) * 2)))
+        key = (N, min(3, int(math.log10(max(K, 1))) - 2))     # <1e3, <1e4, <1e5, more
         if key not in self._tuned:
             torch = self.torch
             times = {}
@@ -209,70 +219,119 @@ class Server:
         return self._tuned[key]
 
     # ---- the loop ----------------------------------------------------------
-    def run(self, requests):
+    def _build(self, N, members, old, st):
+        """A pack of `members` (live solves of order N), continuing from the
+        old pack's state for those that were in it."""
         torch = self.torch
+        carry = {}
+        if old is not None:
+            state = old.state()
+            for s in old.solves:
+                if s in members:
+                    sl = slice(s.offset, s.offset + s.K)
+                    carry[id(s)] = (state[:, sl].clone(), old.res[:, sl].clone())
+        impl = self._choose_impl(N, members)
+        p = _Pack(torch, N, members, carry, self._pad_mesh(N), impl, self.graphs, self.stream)
+        p.built_at = st["iterations"]
+        st["packs_built"] += 1
+        return p
+
+    def _admit(self, req, now):
+        return _Live(req, now)
+
+    def _retire(self, p, s, now):
+        state = p.state()
+        sl = slice(s.offset, s.offset + s.K)
+        energy = p.mesh.energy_range(state, s.offset, s.offset + s.K, stream=self.stream)
+        fields = state[:, sl].cpu().numpy() if self.keep else None
+        return Result(s.req.rid, s.K, s.req.N, s.steps, s.dt, energy, fields, s.req.arrival,
+                      s.admitted, now())
+
+    def _device_context(self):
+        return self.torch.cuda.stream(self.stream)
+
+    def run(self, requests, max_iterations: int | None = None):
+        """Serve `requests` (arriving at their `arrival` times) to completion;
+        returns their Results in rid order.
+
+        A pack of order N is rebuilt when solves of that order wait to join it
+        and it has run at least `rebuild_every` steps since it was built (at once
+        when there is no pack), or when most of its solves have finished.  A
+        finished solve's fields and energy are taken at its last step; its
+        elements keep stepping, unread, until its pack is rebuilt; a pack with
+        no unfinished solve is dropped at the start of the next iteration.
+        `max_iterations` bounds the loop (RuntimeError when exceeded)."""
         pending = sorted(requests, key=lambda r: (r.arrival, r.rid))
-        live, packs, results = [], {}, []
+        waiting, packs, results = [], [], []
         held = 0
         t0 = time.perf_counter()
-        dirty = set()
-        while pending or live:
-            now = time.perf_counter() - t0
-            while pending and pending[0].arrival <= now:
+        now = lambda: time.perf_counter() - t0  # noqa: E731
+        st = self.stats = dict(admit_s=0.0, pack_s=0.0, step_s=0.0, retire_s=0.0, packs_built=0,
+                               iterations=0)
+        every = self.rebuild_every if self.batch else 0
+        while pending or waiting or packs:
+            if max_iterations is not None and st["iterations"] > max_iterations:
+                raise RuntimeError("serve loop exceeded max_iterations")
+            for p in [p for p in packs if not p.alive]:     # finished packs free their memory
+                packs.remove(p)
+                held -= sum(s.bytes for s in p.solves)
+            while pending and pending[0].arrival <= now():
                 req = pending[0]
                 need = solve_bytes(len(req.tets), (req.N + 1) * (req.N + 2) * (req.N + 3) // 6)
-                if live and held + need > self.budget:
+                if held > 0 and held + need > self.budget:
                     break                                # first come, first served
                 pending.pop(0)
-                s = _Live(req, time.perf_counter() - t0)
-                live.append(s)
+                ta = time.perf_counter()
+                s = self._admit(req, now())
+                st["admit_s"] += time.perf_counter() - ta
+                waiting.append(s)
                 held += s.bytes
-                dirty.add(req.N)
-            if not live:
-                time.sleep(max(0.0, pending[0].arrival - (time.perf_counter() - t0)))
+            if not waiting and not packs:
+                if not pending:
+                    break                                # the last packs just finished
+                time.sleep(max(0.0, pending[0].arrival - now()))
                 continue
-            with torch.cuda.stream(self.stream):
-                for N in sorted(dirty):
-                    members = [s for s in live if s.req.N == N]
-                    old = packs.pop(N, None)
-                    carry = {}
-                    for op in (old if isinstance(old, list) else [old] if old else []):
-                        st = op.state()
-                        for s in op.solves:
-                            if s in members:
-                                sl = slice(s.offset, s.offset + s.K)
-                                carry[id(s)] = (st[:, sl].clone(), op.res[:, sl].clone())
-                    if not members:
-                        continue
-                    groups = [members] if self.batch else [[s] for s in members]
-                    built = []
-                    for g in groups:
-                        impl = self._choose_impl(N, g)
-                        built.append(_Pack(torch, N, g, carry, self._pad_mesh(N), impl,
-                                           self.graphs, self.stream))
-                    packs[N] = built[0] if self.batch else built
-                dirty.clear()
-                all_packs = [p for v in packs.values() for p in (v if isinstance(v, list) else [v])]
-                for p in all_packs:
+            with self._device_context():
+                tp = time.perf_counter()
+                it = st["iterations"]
+                if self.batch:
+                    for N in sorted({s.req.N for s in waiting} | {p.N for p in packs}):
+                        old = next((p for p in packs if p.N == N), None)
+                        new = [s for s in waiting if s.req.N == N]
+                        aged = old is not None and it - old.built_at >= every
+                        if old is not None and not new and not (old.alive * 2 <= len(old.solves)
+                                                                 and aged):
+                            continue
+                        if old is not None and new and not aged:
+                            continue
+                        keep = [s for s in old.solves if not s.finished] if old is not None else []
+                        if old is not None:
+                            packs.remove(old)
+                            held -= sum(s.bytes for s in old.solves if s.finished)
+                        packs.append(self._build(N, keep + new, old, st))
+                        waiting = [s for s in waiting if s.req.N != N]
+                else:
+                    for s in waiting:
+                        packs.append(self._build(s.req.N, [s], None, st))
+                    waiting = []
+                ts = time.perf_counter()
+                st["pack_s"] += ts - tp
+                for p in packs:
                     p.step()
-                finished = []
-                for p in all_packs:
+                st["iterations"] += 1
+                tr = time.perf_counter()
+                st["step_s"] += tr - ts
+                for p in packs:
                     for s in p.solves:
+                        if s.finished:
+                            continue
                         s.done += 1
-                        if s.done == s.steps:
-                            finished.append((p, s))
-                for p, s in finished:
-                    st = p.state()
-                    sl = slice(s.offset, s.offset + s.K)
-                    tmp = torch.zeros_like(st)
-                    tmp[:, sl].copy_(st[:, sl])
-                    energy = p.mesh.energy(tmp, stream=self.stream)
-                    fields = st[:, sl].cpu().numpy() if self.keep else None
-                    results.append(Result(s.req.rid, s.K, s.req.N, s.steps, s.dt, energy, fields,
-                                          s.req.arrival, s.admitted, time.perf_counter() - t0))
-                    live.remove(s)
-                    held -= s.bytes
-                    dirty.add(s.req.N)
+                        if s.done < s.steps:
+                            continue
+                        results.append(self._retire(p, s, now))
+                        s.finished = True
+                        p.alive -= 1
+                st["retire_s"] += time.perf_counter() - tr
         return sorted(results, key=lambda r: r.rid)
 
 

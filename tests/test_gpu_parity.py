@@ -455,3 +455,36 @@ def test_subdomains_in_lockstep_match_the_single_mesh(env, impl):
     for p, u, m in zip(plans, src, meshes):
         assert p.n_local % 4 == 0
         assert np.array_equal(u.cpu().numpy()[:, :p.n_owned], full[:, p.owned])
+
+
+@pytest.mark.parametrize("N", [2, 4, 7])
+def test_packed_mesh_stages_and_range_energies(env, N):
+    """dg_mesh_pack of two meshes: a packed stage with per-element steps
+    (dg_rk_stage_elem) is bit for bit each mesh's own stage with its own step,
+    and dg_energy_range over each part matches that mesh's dg_energy."""
+    torch, dg = env
+    va, ta = kuhn_box_mesh(2, 0.1, 1)
+    vb, tb = kuhn_box_mesh(2, 0.15, 2)
+    a, b = dg.Mesh(va, ta, N), dg.Mesh(vb, tb, N)
+    p = dg.Mesh.pack([a, b])
+    assert p.K == a.K + b.K
+    ua = random_fields(a.K, a.Np, 31).astype(np.float32)
+    ub = random_fields(b.K, b.Np, 32).astype(np.float32)
+    dta, dtb = np.float32(0.7 * a.dt_cfl), np.float32(0.4 * b.dt_cfl)
+    up = torch.from_numpy(np.concatenate([ua, ub], axis=1)).cuda()
+    dts = torch.from_numpy(np.concatenate([np.full(a.K, dta), np.full(b.K, dtb)])).cuda()
+    out, res = torch.empty_like(up), torch.zeros_like(up)
+    p.rk_stage_elem(up, out, res, 1, dts)
+    want = []
+    for m, u, dt in ((a, ua, dta), (b, ub, dtb)):
+        x = torch.from_numpy(u).cuda()
+        y, r = torch.empty_like(x), torch.zeros_like(x)
+        m.rk_stage(x, y, r, 1, float(dt))
+        want.append(y.cpu().numpy())
+    torch.cuda.synchronize()
+    assert np.array_equal(out.cpu().numpy(), np.concatenate(want, axis=1))
+    ea = p.energy_range(up, 0, a.K)
+    eb = p.energy_range(up, a.K, p.K)
+    assert abs(ea - a.energy(torch.from_numpy(ua).cuda())) <= 1e-12 * ea
+    assert abs(eb - b.energy(torch.from_numpy(ub).cuda())) <= 1e-12 * eb
+    assert p.energy_range(up, 0, p.K) == p.energy(up)

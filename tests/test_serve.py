@@ -8,7 +8,7 @@ import pytest
 
 from workloads import gaussian_pulse, kuhn_box_mesh, random_fields
 
-pytestmark = pytest.mark.gpu
+pytestmark = [pytest.mark.gpu, pytest.mark.timeout(120)]
 
 
 @pytest.fixture(scope="module")
@@ -51,7 +51,7 @@ def test_same_alone_and_in_the_mix(env, batch, graphs):
     torch, dg, serve = env
     reqs = _requests(serve)
     srv = serve.Server(batch=batch, graphs=graphs, autotune=False, impl=dg.Mesh.STAGE_TC)
-    results = srv.run(reqs)
+    results = srv.run(reqs, max_iterations=200_000)
     _check_against_alone(serve, dg, results, reqs, dg.Mesh.STAGE_TC)
 
 
@@ -60,7 +60,7 @@ def test_small_budget_admits_one_at_a_time(env):
     reqs = _requests(serve, spread=0.0)
     srv = serve.Server(hbm_budget=1.0, batch=True, graphs=True, autotune=False,
                        impl=dg.Mesh.STAGE_TC)
-    results = sorted(srv.run(reqs), key=lambda r: r.admitted)
+    results = sorted(srv.run(reqs, max_iterations=200_000), key=lambda r: r.admitted)
     for a, b in zip(results, results[1:]):
         assert b.admitted >= a.finished - 1e-6
     _check_against_alone(serve, dg, sorted(results, key=lambda r: r.rid), reqs, dg.Mesh.STAGE_TC)
@@ -69,7 +69,7 @@ def test_small_budget_admits_one_at_a_time(env):
 def test_autotuned_packs_stay_within_the_parity_tolerance(env):
     torch, dg, serve = env
     reqs = _requests(serve)
-    results = serve.Server(autotune=True).run(reqs)
+    results = serve.Server(autotune=True).run(reqs, max_iterations=200_000)
     for res, req in zip(results, reqs):
         u, _, _, _ = serve.run_alone(req, impl=dg.Mesh.STAGE_FP32)
         assert np.linalg.norm(res.fields - u) <= 1e-5 * np.linalg.norm(u), req.rid

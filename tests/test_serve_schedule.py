@@ -1,0 +1,100 @@
+"""Scheduling logic of the serving loop (serve.Server.run) on the CPU: the
+real loop with fake solves and packs (no GPU), bounded by max_iterations so
+that a scheduling bug fails instead of hanging.  Checks completion, exact step
+counts, budget-limited one-at-a-time admission, rebuild pacing and per-solve
+packs."""
+import contextlib
+
+import numpy as np
+import pytest
+
+from paper_0901_1024_gb300 import serve
+
+
+class FakeLive:
+    def __init__(self, req, now):
+        self.req, self.K, self.steps, self.dt = req, len(req.tets), int(req.T), 1.0
+        self.done, self.admitted, self.offset, self.finished = 0, now, 0, False
+        self.stepped = 0
+        self.bytes = serve.solve_bytes(self.K, (req.N + 1) * (req.N + 2) * (req.N + 3) // 6)
+
+
+class FakePack:
+    def __init__(self, N, solves, built_at):
+        self.N, self.solves, self.alive, self.built_at = N, list(solves), len(solves), built_at
+
+    def step(self):
+        for s in self.solves:
+            if not s.finished:
+                s.stepped += 1
+
+
+class FakeServer(serve.Server):
+    def __init__(self, budget=1e18, batch=True, rebuild_every=4):
+        self.budget, self.batch, self.rebuild_every = budget, batch, rebuild_every
+        self.graphs, self.autotune, self.keep = False, False, False
+        self.stats, self.live_log = {}, []
+
+    def _admit(self, req, now):
+        return FakeLive(req, now)
+
+    def _build(self, N, members, old, st):
+        assert members and all(s.req.N == N and not s.finished for s in members)
+        st["packs_built"] += 1
+        self.live_log.append(len(members))
+        return FakePack(N, members, st["iterations"])
+
+    def _retire(self, p, s, now):
+        assert s.stepped == s.steps
+        return serve.Result(s.req.rid, s.K, s.req.N, s.steps, s.dt, 0.0, None, s.req.arrival,
+                            s.admitted, now())
+
+    def _device_context(self):
+        return contextlib.nullcontext()
+
+
+def requests(count=20, seed=0, spread=0.0):
+    rng = np.random.Generator(np.random.PCG64(seed))
+    out = []
+    for rid in range(count):
+        K = int(rng.integers(6, 60))
+        out.append(serve.Request(rid, None, np.zeros((K, 4)), int(rng.integers(1, 4)),
+                                 float(rng.integers(1, 15)), None, arrival=spread * rid))
+    return out
+
+
+@pytest.mark.parametrize("batch,every", [(True, 1), (True, 4), (True, 50), (False, 0)])
+def test_every_solve_finishes_with_its_step_count(batch, every):
+    reqs = requests()
+    res = FakeServer(batch=batch, rebuild_every=every).run(reqs, max_iterations=10_000)
+    assert [r.rid for r in res] == list(range(len(reqs)))
+    assert all(r.steps == int(q.T) for r, q in zip(res, reqs))
+
+
+def test_small_budget_admits_one_solve_at_a_time():
+    srv = FakeServer(budget=1.0)
+    res = sorted(srv.run(requests(8), max_iterations=10_000), key=lambda r: r.admitted)
+    for a, b in zip(res, res[1:]):
+        assert b.admitted >= a.finished
+    assert max(srv.live_log) == 1
+
+
+def test_arrivals_in_the_future_are_waited_for():
+    res = FakeServer().run(requests(5, spread=0.002), max_iterations=10_000)
+    assert all(r.admitted >= r.arrival for r in res)
+
+
+def test_rebuilds_are_paced_and_unbatched_packs_are_per_solve():
+    paced = FakeServer(rebuild_every=8)
+    paced.run(requests(30), max_iterations=10_000)
+    eager = FakeServer(rebuild_every=1)
+    eager.run(requests(30), max_iterations=10_000)
+    assert paced.stats["packs_built"] <= eager.stats["packs_built"]
+    single = FakeServer(batch=False)
+    single.run(requests(12), max_iterations=10_000)
+    assert single.stats["packs_built"] == 12 and max(single.live_log) == 1
+
+
+def test_loop_bound_raises():
+    with pytest.raises(RuntimeError):
+        FakeServer().run(requests(3), max_iterations=1)
