@@ -438,6 +438,49 @@ def run_serve(args):
     print(json.dumps(line), flush=True)
 
 
+def run_sweep(args):
+    """Roofline curve over the order: for N = 1..9 a pulse workload on a box mesh
+    with n chosen so that 6 K Np is about 1.7e7, timed per stage launch (CUDA
+    events) after warm-up, for the default stage kernel (tensor cores for
+    N <= 4, FP32 CUDA cores above) and, for N <= 4, the FP32 kernel as well."""
+    import torch
+    import paper_0901_1024_gb300 as dg
+    peaks, _ = load_peaks()
+    fp32_peak = 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+    rows = []
+    for N in range(1, 10):
+        Np, Nfp = (N + 1) * (N + 2) * (N + 3) // 6, (N + 1) * (N + 2) // 2
+        n = max(2, round((1.7e7 / (36 * Np)) ** (1 / 3)))
+        verts, tets = kuhn_box_mesh(n, 0.15, 0)
+        mesh = dg.Mesh(verts, tets, N)
+        x = mesh.nodes()
+        u0 = gaussian_pulse(x[0], x[1], x[2], 0.2, pulse_center(1)).astype(np.float32)
+        for impl in ([0, 1] if N <= 4 else [0]):
+            mesh.set_stage_impl(impl)
+            u = torch.from_numpy(u0).cuda()
+            res = torch.zeros_like(u)
+            mesh.step(u, res, mesh.dt_cfl, 3)
+            mesh.trace_enable(5 * args.sweep_steps)
+            mesh.step(u, res, mesh.dt_cfl, args.sweep_steps)
+            torch.cuda.synchronize()
+            ms, kinds = mesh.trace_read()
+            mesh.trace_enable(0)
+            stage = statistics.fmean(t for t, k in zip(ms, kinds) if k in (0, 4)) * 1e-3
+            K = mesh.K
+            gbs = stage_bytes_per_elem(Np) * K / stage / 1e9
+            tf = flops_per_elem_stage(N, Np, Nfp) * K / stage / 1e12
+            rows.append({"N": N, "n": n, "K": K, "Np": Np, "dofs": 6 * K * Np,
+                         "kernel": "tensor cores (FP16x3)" if 4 in kinds else "FP32 CUDA cores",
+                         "stage_us": stage * 1e6, "dof_updates_per_s": 6 * K * Np / stage,
+                         "hbm_gbs": gbs, "hbm_frac": gbs / peaks["hbm_gbs"],
+                         "tflops": tf, "fp32_frac": tf / fp32_peak})
+        del mesh
+    print(json.dumps({"mode": "sweep", "metric": "DOF-updates/s and % HBM roofline per RK stage",
+                      "unit": "DOF-updates/s", "peak_hbm_gbs": peaks["hbm_gbs"],
+                      "fp32_peak_tflops": fp32_peak, "steps": args.sweep_steps, "orders": rows}),
+          flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -447,8 +490,10 @@ def main():
     ap.add_argument("--workload", default="pulse_n24_N4", choices=sorted(WORKLOADS))
     ap.add_argument("--order", default="native", choices=["native", "shuffled", "partition"],
                     help="element numbering of the timed mesh (see element_order)")
-    ap.add_argument("--mode", default="stage", choices=["stage", "serve"],
-                    help="stage: the RK-stage benchmark (default); serve: the request-stream benchmark")
+    ap.add_argument("--mode", default="stage", choices=["stage", "serve", "sweep"],
+                    help="stage: the RK-stage benchmark (default); serve: the request-stream "
+                         "benchmark; sweep: stage throughput for N = 1..9")
+    ap.add_argument("--sweep-steps", type=int, default=20)
     ap.add_argument("--requests", type=int, default=48)
     ap.add_argument("--rebuild-every", type=int, default=32,
                     help="serve mode: steps a pack runs before waiting solves join it")
@@ -463,6 +508,8 @@ def main():
         run_reference(args)
     elif args.mode == "serve":
         run_serve(args)
+    elif args.mode == "sweep":
+        run_sweep(args)
     else:
         run_ours(args)
 

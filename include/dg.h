@@ -146,7 +146,8 @@ int dg_set_flux(dg_mesh* mesh, double alpha);
 /*
  * Implementation of the RK-stage operator (the paper notes that each operator
  * part may need its own strategy on the GPU, Section 4):
- *   DG_STAGE_AUTO   tensor cores for N <= 4, FP32 CUDA cores above (default);
+ *   DG_STAGE_AUTO   tensor cores for N = 2..4, FP32 CUDA cores for N = 1 and
+ *                   above 4 (the faster kernel of each order on GB300; default);
  *   DG_STAGE_FP32   FP32 CUDA cores for every order;
  *   DG_STAGE_TC     tensor cores (tcgen05): the volume and lifting contractions
  *                   as one GEMM per tile with three FP16 products

@@ -109,7 +109,7 @@ class Mesh:
     STAGE_AUTO, STAGE_FP32, STAGE_TC = 0, 1, 2
 
     def set_stage_impl(self, impl: int):
-        """0 = auto (tensor cores for N <= 4), 1 = FP32 CUDA cores, 2 = tensor cores."""
+        """0 = auto (tensor cores for N = 2..4), 1 = FP32 CUDA cores, 2 = tensor cores."""
         check(self._lib.dg_set_stage_impl(self._h, int(impl)), "dg_set_stage_impl")
 
     def nodes(self) -> np.ndarray:

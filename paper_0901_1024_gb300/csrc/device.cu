@@ -501,11 +501,14 @@ int ensure_device(dg_mesh* m, std::string& err) {
   return DG_OK;
 }
 
-// Tensor cores for orders <= kTcMaxOrder unless the CUDA-core path is forced.
+// Tensor cores for orders 2..kTcMaxOrder (and 1 on request) unless the CUDA-core
+// path is forced.
 // The tensor-core kernel moves whole tiles with bulk copies, which need every
 // field chunk 16-byte aligned: (K * Np) % 4 == 0 and 16-byte aligned buffers.
 static bool use_tc(const dg_mesh* m, std::initializer_list<const void*> bufs) {
   if (m->stage_impl == DG_STAGE_FP32 || m->N > dgdev::kTcMaxOrder) return false;
+  // at N = 1 (Np = 4) the FP32 kernel is faster unless tensor cores are asked for
+  if (m->stage_impl == DG_STAGE_AUTO && m->N == 1) return false;
   if ((m->K * m->ops.Np) % 4 != 0) return false;
   for (const void* p : bufs)
     if (reinterpret_cast<uintptr_t>(p) % 16 != 0) return false;

@@ -20,7 +20,8 @@ constexpr int kGeoWords = 32;
 // one CTA stay near 100 KB.
 __host__ __device__ constexpr int stage_tile_elems(int N) { return N <= 5 ? 32 : (N <= 7 ? 16 : 8); }
 __host__ __device__ constexpr int stage_row_groups(int N) {
-  return N == 1 ? 4 : N <= 3 ? 5 : N == 4 ? 7 : N == 5 ? 8 : N == 6 ? 12 : N == 7 ? 18 : N == 8 ? 28 : 32;
+  // 3 (N = 5..7) or 4 (N = 8, 9) matrix rows per thread: measured fastest on GB300
+  return N == 1 ? 4 : N <= 3 ? 5 : N == 4 ? 7 : N == 5 ? 19 : N == 6 ? 28 : N == 7 ? 40 : N == 8 ? 42 : 55;
 }
 
 struct StageArgs {
