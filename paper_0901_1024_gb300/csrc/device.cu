@@ -65,6 +65,7 @@ __global__ void __launch_bounds__(kEnergyRows) energy_rows_kernel(const EnergyAr
   extern __shared__ __align__(16) float esm[];
   float* sM = esm;                       // [NP][NP4], zero padded
   float* sU = esm + NP * NP4;            // [kEnergyRows][RS]
+  __shared__ int64_t sRow[kEnergyRows], sElem[kEnergyRows];
   for (int i = threadIdx.x; i < NP * NP4; i += kEnergyRows) {
     const int r = i / NP4, c = i - r * NP4;
     sM[i] = c < NP ? __ldg(A.M + r * NP + c) : 0.f;
@@ -75,11 +76,16 @@ __global__ void __launch_bounds__(kEnergyRows) energy_rows_kernel(const EnergyAr
   for (int64_t r0 = int64_t(blockIdx.x) * kEnergyRows; r0 < rows;
        r0 += int64_t(gridDim.x) * kEnergyRows) {
     const int nr = int(rows - r0 < kEnergyRows ? rows - r0 : kEnergyRows);
-    __syncthreads();                     // previous pass done with sU (and sM written)
+    __syncthreads();                     // previous pass done with sU, sRow (and sM written)
+    if (threadIdx.x < nr) {              // one division per row: its field and element
+      const int64_t g = r0 + threadIdx.x, c = g / Kr, k = A.k0 + (g - c * Kr);
+      sRow[threadIdx.x] = (c * A.K + k) * NP;
+      sElem[threadIdx.x] = k;
+    }
+    __syncthreads();
     for (int i = threadIdx.x; i < nr * NP; i += kEnergyRows) {
       const int r = i / NP;
-      const int64_t g = r0 + r, c = g / Kr;
-      sU[r * RS + (i - r * NP)] = __ldg(A.u + (c * A.K + A.k0 + (g - c * Kr)) * NP + (i - r * NP));
+      sU[r * RS + (i - r * NP)] = __ldg(A.u + sRow[r] + (i - r * NP));
     }
     __syncthreads();
     const int r = threadIdx.x;
@@ -102,8 +108,7 @@ __global__ void __launch_bounds__(kEnergyRows) energy_rows_kernel(const EnergyAr
         }
         e = fmaf(sU[r * RS + i], s, e);
       }
-      const int64_t k = A.k0 + (r0 + r) % Kr;
-      const float J = reinterpret_cast<const float*>(A.geo)[k * kGeoWords + 9];
+      const float J = reinterpret_cast<const float*>(A.geo)[sElem[r] * kGeoWords + 9];
       acc += double(J) * double(e);
     }
   }
