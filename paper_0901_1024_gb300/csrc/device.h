@@ -18,7 +18,9 @@ constexpr int kGeoWords = 32;
 // Stage-kernel tiling per order N: tile of E tetrahedra, G row groups (threads
 // = E * G).  Chosen so a thread holds at most 7 rows and the shared tiles of
 // one CTA stay near 100 KB.
-__host__ __device__ constexpr int stage_tile_elems(int N) { return N <= 5 ? 32 : (N <= 7 ? 16 : 8); }
+__host__ __device__ constexpr int stage_tile_elems(int N) {
+  return N <= 5 ? 32 : N == 6 ? 12 : N == 7 ? 16 : 8;     // N = 6: room for its operators
+}
 __host__ __device__ constexpr int stage_row_groups(int N) {
   // 3 (N = 5..7) or 4 (N = 8, 9) matrix rows per thread: measured fastest on GB300
   return N == 1 ? 4 : N <= 3 ? 5 : N == 4 ? 7 : N == 5 ? 19 : N == 6 ? 28 : N == 7 ? 40 : N == 8 ? 42 : 55;

@@ -43,7 +43,12 @@ template <int N> struct StageDims {
   static constexpr int UT = 6 * E * US;
   static constexpr int FT = 6 * E * (FS > US ? FS : US);     // flux tile, reused for rhs
   static constexpr int GT = E * kGeoWords;
-  static constexpr size_t smem_bytes = size_t(UT + FT + GT) * sizeof(float);
+  // orders 5 and 6: Dr/Ds/Dt (float4 rows) and LIFT staged in shared memory once
+  // per CTA, next to the tile (they fit there; above N = 6 they are read through L1)
+  static constexpr bool OPS_SMEM = N == 5 || N == 6;
+  static constexpr int OT = OPS_SMEM ? 4 * Np * Np + Np * NF : 0;
+  static constexpr size_t smem_bytes = size_t(UT + FT + GT + OT) * sizeof(float);
+  static_assert(smem_bytes <= 227 * 1024, "shared memory budget");
   static_assert((UT % 4) == 0 && (FT % 4) == 0, "tiles must stay 16-byte aligned");
 };
 
@@ -56,7 +61,17 @@ __global__ void __launch_bounds__(StageDims<N>::T) stage_kernel(const StageArgs 
   float* su = reinterpret_cast<float*>(smem4);
   float* sf = su + D::UT;
   float* sg = sf + D::FT;
+  const float4* D4 = A.D4;
+  const float4* LIFT4 = A.LIFT4;
   const int tid = threadIdx.x;
+  if constexpr (D::OPS_SMEM) {
+    float4* sops = reinterpret_cast<float4*>(sg + D::GT);
+    for (int i = tid; i < Np * Np; i += D::T) sops[i] = __ldg(A.D4 + i);
+    for (int i = tid; i < Np * NF / 4; i += D::T) sops[Np * Np + i] = __ldg(A.LIFT4 + i);
+    D4 = sops;
+    LIFT4 = sops + Np * Np;
+    // the first tile's __syncthreads (after its staging) publishes the copy
+  }
   const int e = tid % E, g = tid / E;
   const int K = A.K;
 
@@ -155,7 +170,7 @@ __global__ void __launch_bounds__(StageDims<N>::T) stage_kernel(const StageArgs 
           const float v0 = u0[j], v1 = u1[j], v2 = u2[j];
 #pragma unroll
           for (int q = 0; q < R; ++q) {
-            const float4 dm = __ldg(&A.D4[row[q] * Np + j]);
+            const float4 dm = D::OPS_SMEM ? D4[row[q] * Np + j] : __ldg(&A.D4[row[q] * Np + j]);
             acc[0][0][q] = fmaf(dm.x, v0, acc[0][0][q]);
             acc[0][1][q] = fmaf(dm.y, v0, acc[0][1][q]);
             acc[0][2][q] = fmaf(dm.z, v0, acc[0][2][q]);
@@ -198,7 +213,8 @@ __global__ void __launch_bounds__(StageDims<N>::T) stage_kernel(const StageArgs 
         for (int c = 0; c < 6; ++c) fv[c] = f4[c][m4];
 #pragma unroll
         for (int q = 0; q < R; ++q) {
-          const float4 L = __ldg(&A.LIFT4[row[q] * (NF / 4) + m4]);
+          const float4 L = D::OPS_SMEM ? LIFT4[row[q] * (NF / 4) + m4]
+                                       : __ldg(&A.LIFT4[row[q] * (NF / 4) + m4]);
 #pragma unroll
           for (int c = 0; c < 6; ++c) {
             float s = rhs[c][q];
