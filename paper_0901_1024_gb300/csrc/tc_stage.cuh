@@ -18,15 +18,15 @@
 //
 // One persistent CTA per SM (all 512 tensor-memory columns), two warp groups
 // working on different tiles at once, linked by mbarriers:
-//   * producer warps (12): together they compute the fluxes of tile t (flux
-//     extraction, Alg. 3 of the paper; 4 face nodes per thread): neighbour
+//   * producer warps (16): together they compute the fluxes of tile t (flux
+//     extraction, Alg. 3 of the paper; up to 3 face nodes per thread): neighbour
 //     values outside the tile arrive by 4-byte cp.async copies into the flux
 //     buffer, every face node's upwind flux (PEC ghost state on walls) is
 //     written to a shared [row][m] buffer; after a named barrier they build the
 //     A rows of tile t in tensor memory (tcgen05.st), per lane quarter roles 0
-//     and 1 the two halves of the node range of the g^mu blocks and role 2 the
-//     flux block, with one power-of-two scale per row (published by a second
-//     barrier) and the FP16 hi/lo split;
+//     and 1 the two halves of the node range of the g^mu blocks and roles 2
+//     and 3 the two halves of the flux block, with one power-of-two scale per
+//     row (published by a second barrier) and the FP16 hi/lo split;
 //   * MMA/epilogue warps (4): warp 0 issues the 3 x K/16 MMAs of tile t into a
 //     double-buffered FP32 accumulator (elect.sync, commit to an mbarrier) and
 //     all bulk copies; all four then read tile t-1's accumulator rows
@@ -63,8 +63,8 @@ template <int N> struct TcDims {
   static constexpr int COLS_F = KF / 2;               // columns of the flux block
   static constexpr int FSTR = NF + 2;                // flux row stride: 8-byte pair reads of
                                                       // a warp's 32 rows are conflict-free
-  static constexpr int THREADS = 512;                 // 4 epilogue + 12 producer warps
-  static constexpr int PRODUCERS = 384;
+  static constexpr int THREADS = 640;                 // 4 epilogue + 16 producer warps
+  static constexpr int PRODUCERS = 512;
   static constexpr int ITEMS = (E * NF + PRODUCERS - 1) / PRODUCERS;   // flux items per producer
   static constexpr int NSU = 5, NSR = 2;              // ring slots: fields+geometry, RK register
   // shared memory (bytes)
@@ -78,8 +78,8 @@ template <int N> struct TcDims {
   static constexpr int OFF_G = OFF_U + NSU * U_FLOATS * 4;
   static constexpr int OFF_R = OFF_G + NSU * G_FLOATS * 4;   // NSR slots
   static constexpr int OFF_F = OFF_R + NSR * U_FLOATS * 4;   // one flux buffer
-  static constexpr int OFF_BND = OFF_F + F_FLOATS * 4;         // [3 roles][128] row bounds
-  static constexpr int OFF_SC = OFF_BND + 3 * 128 * 4;       // [4][128] row scales
+  static constexpr int OFF_BND = OFF_F + F_FLOATS * 4;         // [4 roles][128] row bounds
+  static constexpr int OFF_SC = OFF_BND + 4 * 128 * 4;       // [4][128] row scales
   static constexpr int OFF_TAB = OFF_SC + 4 * 128 * 4;
   static constexpr int SMEM = OFF_TAB + TAB_BYTES;
   static_assert((U_FLOATS * 4) % 16 == 0 && (E * Np * 4) % 16 == 0, "bulk-copy alignment");
@@ -238,7 +238,7 @@ __device__ __forceinline__ void build_g_half(const GRow& g, int role) {
   g.sBound[role * 128 + g.row] = cmax * umax;
   named_sync(2, D::PRODUCERS);            // row bounds published
   const float s = row_scale(fmaxf(fmaxf(g.sBound[g.row], g.sBound[128 + g.row]),
-                                  g.sBound[256 + g.row]));
+                                  fmaxf(g.sBound[256 + g.row], g.sBound[384 + g.row])));
   // A[buf] is free once the MMAs of tile t-2 have completed
   if (g.t >= 2) wait_or_flag(g.mma_done, ((g.t - 2) >> 1) & 1, g.status);
   tc::fence_after_sync();
@@ -258,6 +258,43 @@ __device__ __forceinline__ void build_g_half(const GRow& g, int role) {
         [&](int p) { return __ffma2_rn(f2(ca), ua[p - P0], __fmul2_rn(f2(cb), ub[p - P0])); },
         g.a_hi + mu * D::COLS_G, g.a_lo + mu * D::COLS_G);
   }
+}
+
+// One flux-block builder row (a producer thread of role 2 or 3) of tile t.
+struct FRow {
+  const float* frow;      // the row's flux values in the flux buffer
+  float* sBound;
+  int t, row;
+  bool live;
+  uint32_t a_hi, a_lo;    // tensor-memory columns of the flux block
+  uint64_t* mma_done;
+  int* status;
+};
+
+// Columns [P0, P0 + NPH) of the flux block of one A row: loads those flux values
+// (8-byte pairs), publishes their maximum, and after the barrier splits them,
+// scaled by the row's power of two, into tensor memory.
+template <int N, int P0, int NPH>
+__device__ __forceinline__ void build_flux_half(const FRow& g, int role) {
+  using D = TcDims<N>;
+  constexpr int NF = D::NF;
+  named_sync(2, D::PRODUCERS);                     // the flux buffer is complete
+  const float2* frow = reinterpret_cast<const float2*>(g.frow);
+  float2 w[NPH];
+  float fmax = 0.f;
+#pragma unroll
+  for (int i = 0; i < NPH; ++i) {
+    w[i] = (g.live && 2 * (P0 + i) < NF) ? frow[P0 + i] : make_float2(0.f, 0.f);
+    fmax = fmaxf(fmax, fmaxf(fabsf(w[i].x), fabsf(w[i].y)));
+  }
+  g.sBound[role * 128 + g.row] = fmax;
+  named_sync(2, D::PRODUCERS);                     // row bounds published
+  const float s = row_scale(fmaxf(fmaxf(g.sBound[g.row], g.sBound[128 + g.row]),
+                                  fmaxf(g.sBound[256 + g.row], g.sBound[384 + g.row])));
+  // A[buf] is free once the MMAs of tile t-2 have completed
+  if (g.t >= 2) wait_or_flag(g.mma_done, ((g.t - 2) >> 1) & 1, g.status);
+  tc::fence_after_sync();
+  split_store_fn<NPH, P0>([&](int p) { return __fmul2_rn(w[p - P0], f2(s)); }, g.a_hi, g.a_lo);
 }
 
 template <int N, bool RK>
@@ -436,10 +473,10 @@ __global__ void __launch_bounds__(TcDims<N>::THREADS, 1) tc_stage_kernel(const S
     __syncwarp();
   } else {
     // ============================ producer warps ===============================
-    // Warps 4..15 compute the fluxes of tile t together, then build its A rows:
+    // Warps 4..19 compute the fluxes of tile t together, then build its A rows:
     // per tensor-memory lane quarter, roles 0 and 1 (warps 4-7, 8-11) the first
-    // and second half of the node range of the three g blocks, role 2 (warps
-    // 12-15) the flux block.
+    // and second half of the node range of the three g blocks, roles 2 and 3
+    // (warps 12-15, 16-19) the first and second half of the flux block.
     const int pt = tid - 128;
     const int role = (warp - 4) >> 2, quarter = warp & 3;
     const int row = quarter * 32 + lane;
@@ -449,7 +486,7 @@ __global__ void __launch_bounds__(TcDims<N>::THREADS, 1) tc_stage_kernel(const S
     const int fa = rc < 3 ? 3 + (o + 2) % 3 : (o + 2) % 3;
     const int fb = rc < 3 ? 3 + (o + 1) % 3 : (o + 1) % 3;
     const float sgn = rc < 3 ? 1.f : -1.f;
-    // Item idx = pt + q * 384 is face node m of element e (idx = e * NF + m), so
+    // Item idx = pt + q * PRODUCERS is face node m of element e (idx = e * NF + m), so
     // a warp's items are consecutive face nodes of one or two elements.  Their
     // tile-independent decode: e | m << 5 | f << 12 | idM << 14, bit 31 past the end.
     uint32_t item[D::ITEMS];
@@ -573,27 +610,15 @@ __global__ void __launch_bounds__(TcDims<N>::THREADS, 1) tc_stage_kernel(const S
       const bool live = row < D::ROWS && re < Ev;
       const uint32_t a_hi = tbase + lane_off + buf * D::BUF_COLS;
       const uint32_t a_lo = a_hi + D::ACOLS;
-      if (role == 2) {
-        named_sync(2, D::PRODUCERS);                     // the flux buffer is complete
-        const float2* frow = reinterpret_cast<const float2*>(F + (rc * E + re) * FSTR);
-        float w[D::KF];
-        float fmax = 0.f;
-#pragma unroll
-        for (int p = 0; p < D::KF / 2; ++p) {
-          const float2 v = (live && 2 * p < NF) ? frow[p] : make_float2(0.f, 0.f);
-          w[2 * p] = v.x;
-          w[2 * p + 1] = v.y;
-          fmax = fmaxf(fmax, fmaxf(fabsf(v.x), fabsf(v.y)));
-        }
-        sBound[256 + row] = fmax;
-        named_sync(2, D::PRODUCERS);                     // row bounds published
-        const float s = row_scale(fmaxf(fmaxf(sBound[row], sBound[128 + row]), sBound[256 + row]));
-        // A[buf] is free once the MMAs of tile t-2 have completed
-        if (t >= 2) wait_or_flag(&s_mma_done[buf], ((t - 2) >> 1) & 1, A.status);
-        tc::fence_after_sync();
-        split_store_fn<D::COLS_F>(
-            [&](int p) { return __fmul2_rn(make_float2(w[2 * p], w[2 * p + 1]), f2(s)); },
-            a_hi + 3 * D::COLS_G, a_lo + 3 * D::COLS_G);
+      if (role >= 2) {
+        // roles 2 and 3: the first and second half of the flux block's columns
+        constexpr int HC = (D::COLS_F + 1) / 2;
+        const FRow fr{F + (rc * E + re) * FSTR, sBound, t, row, live, a_hi + 3 * D::COLS_G,
+                      a_lo + 3 * D::COLS_G, &s_mma_done[buf], A.status};
+        if (role == 2)
+          build_flux_half<N, 0, HC>(fr, 2);
+        else
+          build_flux_half<N, HC, D::COLS_F - HC>(fr, 3);
       } else {
         // roles 0 and 1 split the node range: node pairs [0, H) and [H, KB/2) of
         // all three g blocks, each loading only its half of the two curl fields
