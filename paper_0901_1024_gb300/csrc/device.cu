@@ -15,6 +15,7 @@
 
 #include "device.h"
 #include "dg_internal.h"
+#include "tcgen05.cuh"
 
 namespace dgdev {
 
@@ -56,62 +57,140 @@ cudaError_t launch_stage(int N, bool rk, const StageArgs& a, int num_sms, cudaSt
 constexpr int kEnergyThreads = 256;
 constexpr int kEnergyRows = 128;      // field rows (c, k) per block pass, orders 1..6
 
-// Orders 1..6: a block stages 128 consecutive field rows in shared memory with
-// coalesced loads (row stride NP | 1: conflict-free), then thread r keeps row r
+// Orders 1..6: a block stages 128 consecutive field rows (c, k) in shared
+// memory per pass (row stride NP | 1: conflict-free), thread r then keeps row r
 // in registers and forms u^T M u from M's rows, read as broadcast 16-byte loads.
+// The rows arrive by 4-byte cp.async copies (a pass's copies are all in flight
+// at once, coalesced); where shared memory allows four blocks per SM the next
+// pass's copies are issued before the current pass is computed.
+template <int NP>
+struct EnergyRowsShape {
+  static constexpr int NP4 = (NP + 3) & ~3, RS = NP | 1;
+  // Up to 56 nodes M is used as its upper triangle (M symmetric:
+  // u^T M u = sum_i u_i (M_ii u_i + 2 sum_{j>i} M_ij u_j)), row i holding
+  // M_ii, 2 M_i,i+1, ..., 2 M_i,NP-1 from a 16-byte boundary; above that the
+  // full matrix, row-padded to NP4.
+  static constexpr bool TRI = NP <= 56;
+  __host__ __device__ static constexpr int tri_off(int i) {
+    int o = 0;
+    for (int r = 0; r < i; ++r) o += (NP - r + 3) & ~3;
+    return o;
+  }
+  static constexpr int M_FLOATS = TRI ? tri_off(NP) : NP * NP4, U_FLOATS = kEnergyRows * RS;
+  static constexpr int NBUF = (M_FLOATS + 2 * U_FLOATS) * 4 <= 56 * 1024 ? 2 : 1;
+  static constexpr int BYTES = (M_FLOATS + NBUF * U_FLOATS) * 4;
+};
+
 template <int NP>
 __global__ void __launch_bounds__(kEnergyRows) energy_rows_kernel(const EnergyArgs A) {
-  constexpr int NP4 = (NP + 3) & ~3, RS = NP | 1;
+  using S = EnergyRowsShape<NP>;
+  constexpr int NP4 = S::NP4, RS = S::RS, NBUF = S::NBUF;
   extern __shared__ __align__(16) float esm[];
   float* sM = esm;                       // [NP][NP4], zero padded
-  float* sU = esm + NP * NP4;            // [kEnergyRows][RS]
-  __shared__ int64_t sRow[kEnergyRows], sElem[kEnergyRows];
-  for (int i = threadIdx.x; i < NP * NP4; i += kEnergyRows) {
-    const int r = i / NP4, c = i - r * NP4;
-    sM[i] = c < NP ? __ldg(A.M + r * NP + c) : 0.f;
+  float* sU = esm + S::M_FLOATS;         // [NBUF][kEnergyRows][RS]
+  __shared__ int64_t sRow[NBUF][kEnergyRows];
+  if constexpr (S::TRI) {
+    for (int r = 0; r < NP; ++r)         // row r: columns r .. NP-1, zero padded
+      for (int c = threadIdx.x; c < ((NP - r + 3) & ~3); c += kEnergyRows)
+        sM[S::tri_off(r) + c] = r + c < NP ? (c ? 2.f : 1.f) * __ldg(A.M + r * NP + r + c) : 0.f;
+  } else {
+    for (int i = threadIdx.x; i < NP * NP4; i += kEnergyRows) {
+      const int r = i / NP4, c = i - r * NP4;
+      sM[i] = c < NP ? __ldg(A.M + r * NP + c) : 0.f;
+    }
   }
-  // rows (c, k) for k0 <= k < k1, numbered c * Kr + (k - k0)
+  // rows (c, k) for k0 <= k < k1, numbered c * Kr + (k - k0); pass p of this
+  // block covers rows [r0(p), r0(p) + 128)
   const int64_t Kr = A.k1 - A.k0, rows = 6 * Kr;
+  const int64_t first = int64_t(blockIdx.x) * kEnergyRows, stride = int64_t(gridDim.x) * kEnergyRows;
+  // thread t's row of a pass: its global offset (published for the copies);
+  // returns its element's Jacobian (loaded a pass ahead with two buffers; J > 0),
+  // or -1 for no row
+  auto row_of = [&](int64_t r0, int b) -> float {
+    const int64_t g = r0 + threadIdx.x;
+    if (g >= rows) return -1.f;
+    const int64_t c = g / Kr, k = A.k0 + (g - c * Kr);
+    sRow[b][threadIdx.x] = (c * A.K + k) * NP;
+    return __ldg(reinterpret_cast<const float*>(A.geo) + k * kGeoWords + 9);
+  };
+  auto issue = [&](int64_t r0, int b) {
+    if (r0 < rows) {
+      const int nr = int(rows - r0 < kEnergyRows ? rows - r0 : kEnergyRows);
+      float* dst = sU + b * S::U_FLOATS;
+      for (int i = threadIdx.x; i < nr * NP; i += kEnergyRows) {
+        const int r = i / NP, j = i - r * NP;
+        tc::cp_async4(dst + r * RS + j, A.u + sRow[b][r] + j);
+      }
+    }
+    tc::cp_async_commit();               // possibly empty: keeps the group count uniform
+  };
   double acc = 0.0;
-  for (int64_t r0 = int64_t(blockIdx.x) * kEnergyRows; r0 < rows;
-       r0 += int64_t(gridDim.x) * kEnergyRows) {
-    const int nr = int(rows - r0 < kEnergyRows ? rows - r0 : kEnergyRows);
-    __syncthreads();                     // previous pass done with sU, sRow (and sM written)
-    if (threadIdx.x < nr) {              // one division per row: its field and element
-      const int64_t g = r0 + threadIdx.x, c = g / Kr, k = A.k0 + (g - c * Kr);
-      sRow[threadIdx.x] = (c * A.K + k) * NP;
-      sElem[threadIdx.x] = k;
-    }
+  float J_cur = -1.f;
+  if constexpr (NBUF == 2) {
+    J_cur = row_of(first, 0);
     __syncthreads();
-    for (int i = threadIdx.x; i < nr * NP; i += kEnergyRows) {
-      const int r = i / NP;
-      sU[r * RS + (i - r * NP)] = __ldg(A.u + sRow[r] + (i - r * NP));
+    issue(first, 0);
+  }
+  for (int p = 0;; ++p) {
+    const int64_t r0 = first + p * stride;
+    const int b = NBUF == 2 ? (p & 1) : 0;
+    float J_next = -1.f;
+    // row offsets of the pass to issue (the next one with two buffers, else
+    // this one); its buffer was last read before the previous barrier
+    if constexpr (NBUF == 2) {
+      if (r0 + stride < rows) J_next = row_of(r0 + stride, b ^ 1);
+    } else {
+      if (r0 < rows) J_cur = row_of(r0, 0);
     }
-    __syncthreads();
-    const int r = threadIdx.x;
-    if (r < nr) {
+    __syncthreads();                     // offsets visible; the previous pass is consumed
+    if constexpr (NBUF == 2) issue(r0 + stride, b ^ 1);
+    else issue(r0, 0);
+    tc::cp_async_wait_group<NBUF - 1>(); // this thread's copies of pass p have landed
+    __syncthreads();                     // everyone's have
+    if (r0 >= rows) break;
+    const float* su = sU + b * S::U_FLOATS + threadIdx.x * RS;
+    if (J_cur >= 0.f) {
       float u[NP4];
 #pragma unroll
-      for (int j = 0; j < NP4; ++j) u[j] = j < NP ? sU[r * RS + j] : 0.f;
+      for (int j = 0; j < NP4; ++j) u[j] = j < NP ? su[j] : 0.f;
       float e = 0.f;
-#pragma unroll 1
-      for (int i = 0; i < NP; ++i) {
-        const float4* Mi = reinterpret_cast<const float4*>(sM + i * NP4);
-        float s = 0.f;
+      if constexpr (S::TRI) {
 #pragma unroll
-        for (int j4 = 0; j4 < NP4 / 4; ++j4) {
-          const float4 m4 = Mi[j4];
-          s = fmaf(m4.x, u[4 * j4], s);
-          s = fmaf(m4.y, u[4 * j4 + 1], s);
-          s = fmaf(m4.z, u[4 * j4 + 2], s);
-          s = fmaf(m4.w, u[4 * j4 + 3], s);
+        for (int i = 0; i < NP; ++i) {
+          const float4* Mi = reinterpret_cast<const float4*>(sM + S::tri_off(i));
+          float s0 = 0.f, s1 = 0.f;
+#pragma unroll
+          for (int q = 0; q < (NP - i + 3) / 4; ++q) {
+            const float4 m4 = Mi[q];
+            const int j = i + 4 * q;
+            s0 = fmaf(m4.x, u[j], s0);
+            if (j + 1 < NP) s1 = fmaf(m4.y, u[j + 1], s1);
+            if (j + 2 < NP) s0 = fmaf(m4.z, u[j + 2], s0);
+            if (j + 3 < NP) s1 = fmaf(m4.w, u[j + 3], s1);
+          }
+          e = fmaf(u[i], s0 + s1, e);
         }
-        e = fmaf(sU[r * RS + i], s, e);
+      } else {
+#pragma unroll 1
+        for (int i = 0; i < NP; ++i) {
+          const float4* Mi = reinterpret_cast<const float4*>(sM + i * NP4);
+          float s0 = 0.f, s1 = 0.f;        // two chains for instruction-level parallelism
+#pragma unroll
+          for (int j4 = 0; j4 < NP4 / 4; ++j4) {
+            const float4 m4 = Mi[j4];
+            s0 = fmaf(m4.x, u[4 * j4], s0);
+            s1 = fmaf(m4.y, u[4 * j4 + 1], s1);
+            s0 = fmaf(m4.z, u[4 * j4 + 2], s0);
+            s1 = fmaf(m4.w, u[4 * j4 + 3], s1);
+          }
+          e = fmaf(su[i], s0 + s1, e);
+        }
       }
-      const float J = reinterpret_cast<const float*>(A.geo)[sElem[r] * kGeoWords + 9];
-      acc += double(J) * double(e);
+      acc += double(J_cur) * double(e);
     }
+    if constexpr (NBUF == 2) J_cur = J_next;
   }
+  tc::cp_async_wait_all();
   __shared__ double sw[kEnergyRows / 32];
 #pragma unroll
   for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
@@ -169,7 +248,7 @@ int energy_grid(int num_sms) { return 4 * num_sms; }
 
 template <int NP>
 static cudaError_t launch_energy_rows(const EnergyArgs& a, int grid, cudaStream_t s) {
-  constexpr int bytes = (NP * ((NP + 3) & ~3) + kEnergyRows * (NP | 1)) * 4;
+  constexpr int bytes = EnergyRowsShape<NP>::BYTES;
   static bool attr[16] = {};
   int dev = 0;
   cudaError_t err = cudaGetDevice(&dev);
