@@ -292,7 +292,9 @@ def run_ours(args):
                        "element_order": args.order},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                          "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
-                         "kernel": (f"tc_stage_kernel<N={w['N']},RK> (tcgen05, FP16x3 split)" if tc_path
+                         "kernel": ((f"tc_stage_kernel<N={w['N']},RK> (tcgen05, FP16x3 split)" if w["N"] <= 4
+                                     else f"tt_stage_kernel<N={w['N']},RK> (tcgen05, FP16x3 split, "
+                                          "operator in tensor memory)") if tc_path
                                     else f"stage_kernel<N={w['N']},RK> (FP32 CUDA cores)"),
                          "algorithmic_bytes_per_launch": algo_bytes,
                          "avg_launch_ms": avg_stage_s * 1e3, "launches_timed": len(stage_ms),
@@ -426,7 +428,7 @@ def run_serve(args):
     worst = max(float(np.linalg.norm(a.fields - b.fields) / max(np.linalg.norm(b.fields), 1e-30))
                 for a, b in zip(served, plain))
     line = {"metric": "served solves/s", "value": ours["solves_per_s"], "unit": "solves/s",
-            "higher_is_better": True, "n_gpus": 1, "dtype": "f32 (FP16x3 tensor cores for N<=4)",
+            "higher_is_better": True, "n_gpus": 1, "dtype": "f32 (FP16x3 tensor cores for N<=6)",
             "data": "synthetic", "mode": "serve",
             "config": {"workload": f"{args.requests} requests, Poisson {args.rate}/s, n in 4..10, "
                                    "N in 1..6, T in [0.1, 0.5], Gaussian pulse",
@@ -442,7 +444,7 @@ def run_sweep(args):
     """Roofline curve over the order: for N = 1..9 a pulse workload on a box mesh
     with n chosen so that 6 K Np is about 1.7e7, timed per stage launch (CUDA
     events) after warm-up, for the default stage kernel (tensor cores for
-    N <= 4, FP32 CUDA cores above) and, for N <= 4, the FP32 kernel as well."""
+    N = 2..6, FP32 CUDA cores otherwise) and, for N = 2..6, the FP32 kernel as well."""
     import torch
     import paper_0901_1024_gb300 as dg
     peaks, _ = load_peaks()
@@ -455,7 +457,7 @@ def run_sweep(args):
         mesh = dg.Mesh(verts, tets, N)
         x = mesh.nodes()
         u0 = gaussian_pulse(x[0], x[1], x[2], 0.2, pulse_center(1)).astype(np.float32)
-        for impl in ([0, 1] if N <= 4 else [0]):
+        for impl in ([0, 1] if 2 <= N <= 6 else [0]):
             mesh.set_stage_impl(impl)
             u = torch.from_numpy(u0).cuda()
             res = torch.zeros_like(u)

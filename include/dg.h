@@ -146,16 +146,17 @@ int dg_set_flux(dg_mesh* mesh, double alpha);
 /*
  * Implementation of the RK-stage operator (the paper notes that each operator
  * part may need its own strategy on the GPU, Section 4):
- *   DG_STAGE_AUTO   tensor cores for N = 2..4, FP32 CUDA cores for N = 1 and
- *                   above 4 (the faster kernel of each order on GB300; default);
+ *   DG_STAGE_AUTO   tensor cores for N = 2..6, FP32 CUDA cores for N = 1 and
+ *                   above 6 (the faster kernel of each order on GB300; default);
  *   DG_STAGE_FP32   FP32 CUDA cores for every order;
  *   DG_STAGE_TC     tensor cores (tcgen05): the volume and lifting contractions
  *                   as one GEMM per tile with three FP16 products
  *                   (A_hi B_hi + A_hi B_lo + A_lo B_hi, power-of-two row
- *                   scaling, FP32 accumulation), FP32 elsewhere; orders 1..4.
+ *                   scaling, FP32 accumulation), FP32 elsewhere; orders 1..6
+ *                   (orders 5, 6 with [Dr Ds Dt LIFT] held in tensor memory).
  *                   Its tiles move by bulk copies, so it also needs K*Np to
  *                   be a multiple of 4 and 16-byte aligned field buffers;
- *                   otherwise (and for N > 4) the call runs DG_STAGE_FP32.
+ *                   otherwise (and for N > 6) the call runs DG_STAGE_FP32.
  * Host only.  Errors: DG_ERR_ARG for an unknown value.
  */
 #define DG_STAGE_AUTO 0

@@ -24,6 +24,8 @@ cudaError_t launch_stage_n(bool rk, const StageArgs& a, int num_sms, cudaStream_
 
 template <int N>
 cudaError_t launch_tc_stage_n(bool rk, const StageArgs& a, int num_sms, cudaStream_t s);
+template <int N>
+cudaError_t launch_tt_stage_n(bool rk, const StageArgs& a, int num_sms, cudaStream_t s);
 
 cudaError_t launch_tc_stage(int N, bool rk, const StageArgs& a, int num_sms, cudaStream_t s) {
   switch (N) {
@@ -31,6 +33,8 @@ cudaError_t launch_tc_stage(int N, bool rk, const StageArgs& a, int num_sms, cud
     case 2: return launch_tc_stage_n<2>(rk, a, num_sms, s);
     case 3: return launch_tc_stage_n<3>(rk, a, num_sms, s);
     case 4: return launch_tc_stage_n<4>(rk, a, num_sms, s);
+    case 5: return launch_tt_stage_n<5>(rk, a, num_sms, s);
+    case 6: return launch_tt_stage_n<6>(rk, a, num_sms, s);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -450,7 +454,42 @@ static int order_ops(const dg_mesh* m, int dev, OrderOps& out, std::string& err)
   if ((rc = upload(&o.fmask, fm, err))) return rc;
   std::vector<unsigned char> pm(m->ops.perm.begin(), m->ops.perm.end());
   if ((rc = upload(&o.perm, pm, err))) return rc;
-  if (m->N <= dgdev::kTcMaxOrder) {
+  if (m->N > 4 && m->N <= dgdev::kTcMaxOrder) {
+    // Orders 5, 6: Op = [Dr Ds Dt LIFT] (Np x KT, each derivative block padded
+    // to KB columns, zero padded), scaled by 2^p, split into FP16 hi + lo, as
+    // tensor-memory rows: [piece][lane = node, 128][KT / 2] words, word p of a
+    // row holding columns 2p (low half) and 2p + 1.
+    const int KB = dgdev::tt_kb(m->N), KT = dgdev::tt_kt(m->N), AC = dgdev::tt_acols(m->N);
+    std::vector<double> Op(static_cast<size_t>(Np) * KT, 0.0);
+    double mx = 0.0;
+    for (int n = 0; n < Np; ++n)
+      for (int k = 0; k < KT; ++k) {
+        double v = 0.0;
+        if (k < 3 * KB) {
+          const int mu = k / KB, j = k % KB;
+          const std::vector<double>& Dm = mu == 0 ? m->ops.Dr : mu == 1 ? m->ops.Ds : m->ops.Dt;
+          if (j < Np) v = Dm[n * Np + j];
+        } else if (k < 3 * KB + NF) {
+          v = m->ops.LIFT[n * NF + (k - 3 * KB)];
+        }
+        Op[n * KT + k] = v;
+        mx = std::max(mx, std::fabs(v));
+      }
+    const double sB = std::ldexp(1.0, static_cast<int>(std::floor(std::log2(16384.0 / mx))));
+    o.tc_inv_bscale = static_cast<float>(1.0 / sB);
+    const size_t piece = static_cast<size_t>(128) * AC * 2;      // halves
+    std::vector<__half> P(2 * piece, __float2half_rn(0.f));
+    for (int n = 0; n < Np; ++n)
+      for (int k = 0; k < KT; ++k) {
+        const float x = static_cast<float>(Op[n * KT + k] * sB);
+        const __half hi = __float2half_rn(x);
+        const __half lo = __float2half_rn(x - __half2float(hi));
+        const size_t off = static_cast<size_t>(n) * AC * 2 + k;   // word k / 2, half k % 2
+        P[off] = hi;
+        P[piece + off] = lo;
+      }
+    if ((rc = upload(reinterpret_cast<__half**>(&o.tcB), P, err))) return rc;
+  } else if (m->N <= 4) {
     // B = [Dr Ds Dt LIFT] (Np x KT, zero padded), scaled by 2^p, split into FP16
     // hi + lo, stored in the canonical K-major core-matrix layout.
     const int KB = (Np + 1) & ~1, KT = (3 * KB + NF + 15) & ~15, NN = (Np + 15) & ~15;
@@ -521,7 +560,7 @@ int ensure_device(dg_mesh* m, std::string& err) {
   const int64_t K = m->K;
   const int Nfp = d->Nfp, NF = 4 * Nfp;
   const bool tc = d->N <= dgdev::kTcMaxOrder;
-  constexpr int E = dgdev::kTcTileElems;
+  const int E = dgdev::tc_tile_elems(d->N);
   const int64_t ntiles = (K + E - 1) / E;
   d->tc_geo_stride = tc ? dgdev::tc_geo_floats(d->N) : 0;
   d->egrid = dgdev::energy_grid(d->num_sms);
@@ -614,7 +653,7 @@ static dgdev::StageArgs stage_args(dg_mesh* m, bool tc) {
   a.perm = d->perm;
   a.K = static_cast<int>(d->K);
   a.alpha = static_cast<float>(m->alpha);
-  const int E = tc ? dgdev::kTcTileElems : dgdev::stage_tile_elems(d->N);
+  const int E = tc ? dgdev::tc_tile_elems(d->N) : dgdev::stage_tile_elems(d->N);
   a.num_tiles = static_cast<int>((d->K + E - 1) / E);
   return a;
 }

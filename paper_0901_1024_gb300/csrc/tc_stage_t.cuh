@@ -1,0 +1,505 @@
+// Tensor-core RK stage for orders 5 and 6: the operator lives in tensor memory.
+//
+// The same contraction as the order <= 4 kernel (tc_stage.cuh), transposed:
+//     rhs^T[i, (c,e)] = sum_k Op[i, k] X[(c,e), k],
+//     Op = [Dr Ds Dt LIFT]  (Np x KT),   X = [g^r g^s g^t flux]  (one row per
+//     field c and element e of the tile, g^mu_c = sign_c (r_mu,a U_a - r_mu,b U_b)),
+// i.e. the volume term and the lifted surface term of Eq. semidiscrete-dg with
+// the chain rule applied before differentiating (Eq. dg-reference-matrices,
+// Eq. maxwells-claws).  From N = 5 on, the two FP16 pieces of Op (2 x Np x KT
+// halves, 147 KB at N = 6) no longer fit shared memory beside the field tiles;
+// they do fit tensor memory.  So Op is the MMA's A operand (M = 128 lanes =
+// nodes i < Np, KT / 2 columns per piece), written to tensor memory once per
+// CTA, and X is the B operand (N = 6 E = 48 rows), built per tile by the
+// producer warps in shared memory in the canonical K-major layout.  FP32-class
+// accuracy as in the other kernel: three FP16 products Op_hi X_hi + Op_hi X_lo
+// + Op_lo X_hi, every X row scaled by a power of two, Op by 2^p, FP32
+// accumulation.  The accumulator (lane = node i, column = (c,e)) is double
+// buffered in the remaining tensor-memory columns, so lane i of the epilogue
+// warps owns node i of every (c,e) of the tile -- the shared-memory order of
+// the RK update.
+//
+// One persistent 512-thread CTA per SM:
+//   * producer warps (12): the fluxes of tile t (Alg. 3: face-node gathers by
+//     4-byte cp.async, upwind flux with the PEC ghost state), then, after a
+//     named barrier, the 48 x KT values of X(t) -- producer p builds the 8-value
+//     chunks p / 48 + 8 q of row p % 48 -- a second barrier publishes the row
+//     maxima (row scale), and once the MMAs of tile t-1 have read the single X
+//     buffer, the scaled values are split into FP16 hi/lo and stored;
+//   * MMA/epilogue warps (4): warp 0 issues the 3 x KT/16 MMAs of tile t into
+//     accumulator t & 1 and all bulk copies; all four then read tile t-1's
+//     accumulator (tcgen05.ld), remove the scales and apply the LSERK4 update
+//     res <- a res + dt rhs, u <- u + b res in place in shared memory, and bulk
+//     copies write u_out and res back.
+// Fields and geometry arrive by bulk copies NSU - 1 tiles ahead, the RK
+// register one tile ahead.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "device.h"
+#include "tc_stage.cuh"
+#include "tcgen05.cuh"
+
+namespace dgdev {
+
+template <int N> struct TtDims {
+  static constexpr int Np = (N + 1) * (N + 2) * (N + 3) / 6;
+  static constexpr int Nfp = (N + 1) * (N + 2) / 2;
+  static constexpr int NF = 4 * Nfp;
+  static constexpr int E = kTtTileElems;              // elements per tile
+  static constexpr int ROWS = 6 * E;                  // X rows = MMA N
+  static constexpr int NN = ROWS;
+  static constexpr int KB = tt_kb(N);                 // one mu block (whole 8-value chunks)
+  static constexpr int KG = 3 * KB;
+  static constexpr int KT = tt_kt(N);                 // total K, multiple of 16
+  static constexpr int KSTEPS = KT / 16;
+  static constexpr int KCH = KT / 8;                  // 16-byte chunks of an X row
+  static constexpr int CG = KB / 8;                   // chunks per mu block
+  static constexpr int CF = KG / 8;                   // first flux chunk
+  static constexpr int ACOLS = tt_acols(N);           // tensor-memory columns per Op piece
+  static constexpr int ACC0 = 2 * ACOLS;              // first accumulator column
+  static constexpr int THREADS = 512;                 // 4 epilogue + 12 producer warps
+  static constexpr int PRODUCERS = 384;
+  static constexpr int QR = PRODUCERS / ROWS;         // producers per X row
+  static constexpr int CPT = (KCH + QR - 1) / QR;     // X chunks per producer
+  static constexpr int ITEMS = (E * NF + PRODUCERS - 1) / PRODUCERS;   // flux items per producer
+  static constexpr int FSTR = ((NF / 4) | 1) * 4;     // flux row stride: 16-byte row reads of
+                                                      // 8 consecutive rows are conflict-free
+  static constexpr int NSU = 5, NSR = 2;              // ring slots: fields+geometry, RK register
+  // shared memory (bytes)
+  static constexpr int U_FLOATS = 6 * E * Np;
+  static constexpr int G_FLOATS = tc_geo_floats(N);
+  static constexpr int X_BYTES = NN * KT * 2;         // one FP16 piece of X
+  static constexpr int OFF_X = 0;                     // 2 pieces
+  static constexpr int OFF_U = OFF_X + 2 * X_BYTES;   // NSU slots
+  static constexpr int OFF_G = OFF_U + NSU * U_FLOATS * 4;
+  static constexpr int OFF_R = OFF_G + NSU * G_FLOATS * 4;   // NSR slots
+  static constexpr int OFF_F = OFF_R + NSR * U_FLOATS * 4;   // one flux buffer
+  static constexpr int OFF_BND = OFF_F + ROWS * FSTR * 4;    // [QR][ROWS] partial row maxima
+  static constexpr int OFF_SC = OFF_BND + QR * ROWS * 4;     // [4][ROWS] row scales
+  static constexpr int OFF_TAB = OFF_SC + 4 * ROWS * 4;      // face-node table (NF bytes)
+  static constexpr int SMEM = OFF_TAB + ((NF + 15) & ~15);
+  static_assert(NN % 16 == 0 && NN <= 256, "MMA N");
+  static_assert(PRODUCERS % ROWS == 0 && CPT * QR == KCH, "X chunk split");
+  static_assert(ACC0 + 2 * NN <= 512, "tensor-memory budget");
+  static_assert(ACOLS % 16 == 0, "operator columns are written 16 at a time");
+  static_assert(Np <= 128 && NF < 128 && Np < 128 && E <= 32, "item encoding");
+  static_assert((E * Np * 4) % 16 == 0 && (U_FLOATS * 4) % 16 == 0 && (G_FLOATS * 4) % 16 == 0,
+                "bulk-copy alignment");
+  static_assert((Np * 4) % 16 == 0 && (FSTR * 4) % 16 == 0, "16-byte row chunks");
+  static_assert(OFF_U % 16 == 0 && OFF_G % 16 == 0 && OFF_R % 16 == 0 && OFF_F % 16 == 0,
+                "alignment");
+  static_assert(SMEM <= 226 * 1024, "shared memory budget");
+};
+
+// One thread: bulk copies of tile `tile`'s fields and geometry block.
+template <int N>
+__device__ __forceinline__ void tt_load_u(const StageArgs& A, int tile, float* su, float* sg,
+                                          uint64_t* bar) {
+  using D = TtDims<N>;
+  const int K = A.K, k0 = tile * D::E, Ev = min(D::E, K - k0);
+  const uint32_t fb = uint32_t(Ev) * D::Np * 4;
+  constexpr uint32_t gb = D::G_FLOATS * 4;
+  tc::mbar_expect_tx(bar, 6u * fb + gb);
+  for (int c = 0; c < 6; ++c)
+    tc::bulk_g2s(su + c * D::E * D::Np, A.u_in + (size_t(c) * K + k0) * D::Np, fb, bar);
+  tc::bulk_g2s(sg, A.tcgeo + size_t(tile) * A.tc_geo_stride, gb, bar);
+}
+
+// One thread: bulk copies of tile `tile`'s RK register.
+template <int N>
+__device__ __forceinline__ void tt_load_res(const StageArgs& A, int tile, float* sr, uint64_t* bar) {
+  using D = TtDims<N>;
+  const int K = A.K, k0 = tile * D::E, Ev = min(D::E, K - k0);
+  const uint32_t fb = uint32_t(Ev) * D::Np * 4;
+  tc::mbar_expect_tx(bar, 6u * fb);
+  for (int c = 0; c < 6; ++c)
+    tc::bulk_g2s(sr + c * D::E * D::Np, A.res + (size_t(c) * K + k0) * D::Np, fb, bar);
+}
+
+// 8 consecutive floats from a 16-byte aligned shared address.
+__device__ __forceinline__ void lds8(const float* p, float* v) {
+  const float4 a = reinterpret_cast<const float4*>(p)[0];
+  const float4 b = reinterpret_cast<const float4*>(p)[1];
+  v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+  v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+}
+
+template <int N, bool RK>
+__global__ void __launch_bounds__(TtDims<N>::THREADS, 1) tt_stage_kernel(const StageArgs A) {
+  using D = TtDims<N>;
+  constexpr int E = D::E, Np = D::Np, Nfp = D::Nfp, NF = D::NF, FSTR = D::FSTR, ROWS = D::ROWS;
+  extern __shared__ __align__(1024) unsigned char smem[];
+  __shared__ uint32_t s_tmem;
+  __shared__ __align__(8) uint64_t s_u_full[D::NSU];
+  __shared__ __align__(8) uint64_t s_r_full[D::NSR];
+  __shared__ __align__(8) uint64_t s_x_full, s_mma_done[2];
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int K = A.K;
+  const int ntiles = (A.num_tiles - int(blockIdx.x) + int(gridDim.x) - 1) / int(gridDim.x);
+  if (ntiles <= 0) return;
+
+  unsigned char* sXhi = smem + D::OFF_X;
+  unsigned char* sXlo = sXhi + D::X_BYTES;
+  float* sU = reinterpret_cast<float*>(smem + D::OFF_U);
+  float* sG = reinterpret_cast<float*>(smem + D::OFF_G);
+  float* sR = reinterpret_cast<float*>(smem + D::OFF_R);
+  float* sF = reinterpret_cast<float*>(smem + D::OFF_F);
+  float* sBound = reinterpret_cast<float*>(smem + D::OFF_BND);
+  float* sScale = reinterpret_cast<float*>(smem + D::OFF_SC);
+  unsigned char* sFmask = smem + D::OFF_TAB;
+
+  // ---- set-up: face-node table, tensor memory, barriers, Op -------------------
+  for (int i = tid; i < NF; i += D::THREADS) sFmask[i] = __ldg(A.fmask + i);
+  if (warp == 0) tc::tmem_alloc(&s_tmem, 512);
+  if (tid == 0) {
+    for (int i = 0; i < D::NSU; ++i) tc::mbar_init(&s_u_full[i], 1);
+    for (int i = 0; i < D::NSR; ++i) tc::mbar_init(&s_r_full[i], 1);
+    tc::mbar_init(&s_x_full, D::PRODUCERS);        // every producer thread stores X chunks
+    for (int i = 0; i < 2; ++i) tc::mbar_init(&s_mma_done[i], 1);
+    tc::fence_mbar_init();
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tbase = s_tmem;
+  if (warp < 4) {
+    // lane = node row of Op: both pieces, 16 columns per tensor-memory store
+    const uint4* src = reinterpret_cast<const uint4*>(A.tcB) + size_t(warp * 32 + lane) * (D::ACOLS / 4);
+    const uint32_t trow = tbase + (uint32_t(warp * 32) << 16);
+#pragma unroll 1
+    for (int piece = 0; piece < 2; ++piece) {
+#pragma unroll 1
+      for (int c0 = 0; c0 < D::ACOLS; c0 += 16) {
+        uint32_t v[16];
+        const uint4* s4 = src + size_t(piece) * 128 * (D::ACOLS / 4) + c0 / 4;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const uint4 w = __ldg(s4 + q);
+          v[4 * q] = w.x; v[4 * q + 1] = w.y; v[4 * q + 2] = w.z; v[4 * q + 3] = w.w;
+        }
+        tc::tmem_st<16>(trow + piece * D::ACOLS + c0, v);
+      }
+    }
+    tc::tmem_st_wait();
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+
+  if (warp < 4) {
+    // ======================= MMA issue + epilogue warps ========================
+    const int node = warp * 32 + lane;
+    const uint32_t lane_off = uint32_t(warp * 32) << 16;
+    if (warp == 0 && tc::elect_one()) {   // first loads: fields of tiles 0..NSU-2, res of tile 0
+      for (int t = 0; t < D::NSU - 1 && t < ntiles; ++t)
+        tt_load_u<N>(A, blockIdx.x + t * gridDim.x, sU + t * D::U_FLOATS, sG + t * D::G_FLOATS,
+                     &s_u_full[t]);
+      if (RK) tt_load_res<N>(A, blockIdx.x, sR, &s_r_full[0]);
+    }
+    __syncwarp();
+    constexpr uint32_t IDESC = tc::idesc_f16(128, D::NN);
+    constexpr uint32_t LBO = (D::NN / 8) * 128;
+    for (int j = 0; j <= ntiles; ++j) {
+      if (j < ntiles) {
+        // every epilogue warp observes X(j) complete (this also publishes tile j's
+        // row scales) before the MMAs start, so no waiter can fall a phase behind
+        wait_or_flag(&s_x_full, j & 1, A.status);
+        named_sync(1, 128);
+      }
+      if (j < ntiles && warp == 0) {                 // MMAs of tile j
+        tc::fence_after_sync();
+        const uint32_t d_acc = tbase + D::ACC0 + (j & 1) * D::NN;
+        const uint64_t b_hi = tc::smem_desc(tc::smem_u32(sXhi), LBO, 128);
+        const uint64_t b_lo = b_hi + uint64_t(D::X_BYTES >> 4);
+#pragma unroll 1
+        for (int i = 0; i < 3 * D::KSTEPS; ++i) {
+          const int p = i / D::KSTEPS, ks = i - p * D::KSTEPS;   // passes: hi.hi, hi.lo, lo.hi
+          const uint64_t bd = (p == 1 ? b_lo : b_hi) + uint64_t((ks * 2 * LBO) >> 4);
+          const uint32_t ad = tbase + (p == 2 ? D::ACOLS : 0) + ks * 8;
+          tc::mma_f16_ts_warp(d_acc, ad, bd, IDESC, i > 0 ? 1u : 0u);
+        }
+        tc::mma_commit_warp(&s_mma_done[j & 1]);
+        __syncwarp();
+      }
+      if (j >= 1) {                                  // epilogue of tile t = j - 1
+        const int t = j - 1, buf = t & 1;
+        const int tile = blockIdx.x + t * gridDim.x;
+        const int k0 = tile * E, Ev = min(E, K - k0);
+        float* su = sU + (t % D::NSU) * D::U_FLOATS;
+        float* sr = sR + (t % D::NSR) * D::U_FLOATS;
+        wait_or_flag(&s_mma_done[buf], (t >> 1) & 1, A.status);
+        if (RK) wait_or_flag(&s_r_full[t % D::NSR], (t / D::NSR) & 1, A.status);
+        tc::fence_after_sync();
+        uint32_t acc[D::NN];
+        tmem_load_cols<D::NN>(tbase + lane_off + D::ACC0 + buf * D::NN, acc);
+        tc::tmem_ld_wait();
+        tc::fence_before_sync();
+        if (node < Np) {
+          const float* scl = sScale + (t & 3) * ROWS;
+          float dte[E];
+#pragma unroll
+          for (int e = 0; e < E; ++e)
+            dte[e] = RK && A.dt_elem && e < Ev ? __ldg(A.dt_elem + k0 + e) : A.dt;
+          // column n = (c, e) is the tile row n * Np + node; u and res share one
+          // shared array, so every batch is loaded before any of its stores
+          constexpr int CH = 12;
+          static_assert(ROWS % CH == 0, "epilogue batches");
+#pragma unroll
+          for (int n0 = 0; n0 < ROWS; n0 += CH) {
+            float rv[CH], uv[CH];
+            if (RK) {
+#pragma unroll
+              for (int q = 0; q < CH; ++q) {
+                rv[q] = sr[(n0 + q) * Np + node];
+                uv[q] = su[(n0 + q) * Np + node];
+              }
+            }
+#pragma unroll
+            for (int q = 0; q < CH; ++q) {
+              const int n = n0 + q, e = n % E;
+              if (e >= Ev) continue;
+              const float r = __uint_as_float(acc[n]) * (A.tc_inv_bscale / scl[n]);
+              if (RK) {
+                const float rn = fmaf(A.a, rv[q], dte[e] * r);
+                sr[n * Np + node] = rn;
+                su[n * Np + node] = fmaf(A.b, rn, uv[q]);
+              } else {
+                sr[n * Np + node] = r;
+              }
+            }
+          }
+        }
+        tc::fence_proxy_async_smem();
+        named_sync(1, 128);
+        if (warp == 0 && tc::elect_one()) {
+          const uint32_t fb = uint32_t(Ev) * Np * 4;
+          for (int c = 0; c < 6; ++c) {
+            const size_t g = (size_t(c) * K + k0) * Np;
+            if (RK) {
+              tc::bulk_s2g(A.u_out + g, su + c * E * Np, fb);
+              tc::bulk_s2g(A.res + g, sr + c * E * Np, fb);
+            } else {
+              tc::bulk_s2g(A.rhs + g, sr + c * E * Np, fb);
+            }
+          }
+          tc::bulk_commit();
+          // slots of tile t-1 (stored one round ago) take tiles t+NSU-1 and t+1
+          asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
+          tc::fence_proxy_async_smem();
+          if (t + D::NSU - 1 < ntiles) {
+            const int s = (t + D::NSU - 1) % D::NSU;
+            tt_load_u<N>(A, tile + (D::NSU - 1) * gridDim.x, sU + s * D::U_FLOATS,
+                         sG + s * D::G_FLOATS, &s_u_full[s]);
+          }
+          if (RK && t + 1 < ntiles) {
+            const int s = (t + 1) % D::NSR;
+            tt_load_res<N>(A, tile + gridDim.x, sR + s * D::U_FLOATS, &s_r_full[s]);
+          }
+        }
+        __syncwarp();
+      }
+    }
+    if (warp == 0 && tc::elect_one()) tc::bulk_wait_all();
+    __syncwarp();
+  } else {
+    // ============================ producer warps ===============================
+    const int pt = tid - 128;
+    // X row xn = (c, e) of this producer and its chunks xq + QR q
+    const int xn = pt % ROWS, xq = pt / ROWS;
+    const int xc = xn / E, xe = xn - (xn / E) * E;
+    const int o = xc % 3;                                 // curl: field c takes fields fa, fb
+    const int fa = xc < 3 ? 3 + (o + 2) % 3 : (o + 2) % 3;
+    const int fb = xc < 3 ? 3 + (o + 1) % 3 : (o + 1) % 3;
+    const float sgn = xc < 3 ? 1.f : -1.f;
+    // Item idx = pt + q * PRODUCERS is face node m of element e (idx = e * NF + m).
+    // Tile-independent decode: e | m << 5 | f << 12 | idM << 14, bit 31 past the end.
+    uint32_t item[D::ITEMS];
+#pragma unroll
+    for (int q = 0; q < D::ITEMS; ++q) {
+      const int idx = pt + q * D::PRODUCERS;
+      const int e = idx / NF, m = idx - e * NF;
+      item[q] = idx < E * NF ? uint32_t(e) | uint32_t(m) << 5 | uint32_t(m / Nfp) << 12 |
+                                   uint32_t(sFmask[m]) << 14
+                             : 0x80000000u;
+    }
+    float* F = sF;
+    for (int t = 0; t < ntiles; ++t) {
+      const int tile = blockIdx.x + t * gridDim.x;
+      const int k0 = tile * E, Ev = min(E, K - k0);
+      const int slot = t % D::NSU;
+      const float* su = sU + slot * D::U_FLOATS;
+      const float* sg = sG + slot * D::G_FLOATS;
+      wait_or_flag(&s_u_full[slot], (t / D::NSU) & 1, A.status);
+      // ---- fluxes (Alg. 3).  Classify every item (0 none, 1 wall, 2 neighbour in
+      // the tile, 3 neighbour outside it) and start the gathers of kind 3 into the
+      // flux-buffer words this item's flux will overwrite.  F was last read in the
+      // X values of tile t-1, before its second barrier.
+      const unsigned char* nodes = reinterpret_cast<const unsigned char*>(sg + kTcGeoWords * E);
+      uint32_t info[D::ITEMS];          // kind | ofs << 2
+#pragma unroll
+      for (int q = 0; q < D::ITEMS; ++q) {
+        const uint32_t it = item[q];
+        const int e = it & 31, m = (it >> 5) & 127, f = (it >> 12) & 3, idM = (it >> 14) & 127;
+        const bool ok = !(it >> 31) && e < Ev;
+        const int ec = ok ? e : 0;
+        const unsigned code = (__float_as_uint(sg[9 * E + ec]) >> (8 * f)) & 0xffu;
+        const int k2 = __float_as_int(sg[(26 + f) * E + ec]);
+        const int i2 = nodes[ec * NF + m];
+        const int e2 = k2 - k0;
+        const uint32_t kind = !ok ? 0u : code == 0u ? 1u : unsigned(e2) < unsigned(Ev) ? 2u : 3u;
+        if (kind == 3u) {
+          const float* src = A.u_in + size_t(k2) * Np + i2;
+#pragma unroll
+          for (int c = 0; c < 6; ++c)
+            tc::cp_async4(F + (c * E + e) * FSTR + m, src + size_t(c) * K * Np);
+        }
+        info[q] = kind | uint32_t(kind == 2u ? e2 * Np + i2 : ec * Np + idM) << 2;
+      }
+      tc::cp_async_commit();
+      tc::cp_async_wait_all();
+      // upwind flux of every face node (PEC ghost state E+ = -E-, H+ = H- on walls),
+      // all operands loaded before any store into the flux buffer
+      {
+        float uM[D::ITEMS][6], up[D::ITEMS][6], nv[D::ITEMS][4];
+#pragma unroll
+        for (int q = 0; q < D::ITEMS; ++q) {
+          const uint32_t it = item[q], kind = info[q] & 3u;
+          const int e = kind ? int(it & 31) : 0, m = (it >> 5) & 127, f = (it >> 12) & 3;
+          const int idM = (it >> 14) & 127;
+          const float* pp = kind == 3u ? F + e * FSTR + m : su + (info[q] >> 2);
+          const int ps = kind == 3u ? E * FSTR : E * Np;
+#pragma unroll
+          for (int c = 0; c < 6; ++c) {
+            uM[q][c] = su[c * E * Np + e * Np + idM];
+            up[q][c] = pp[c * ps];
+          }
+#pragma unroll
+          for (int w = 0; w < 4; ++w) nv[q][w] = sg[(10 + 4 * f + w) * E + e];
+        }
+#pragma unroll
+        for (int q = 0; q < D::ITEMS; ++q) {
+          const uint32_t kind = info[q] & 3u;
+          if (!kind) continue;
+          const float nwe = kind == 1u ? 1.f : -1.f;      // E+ = -E- on walls
+          const float dEx = fmaf(nwe, up[q][0], uM[q][0]);
+          const float dEy = fmaf(nwe, up[q][1], uM[q][1]);
+          const float dEz = fmaf(nwe, up[q][2], uM[q][2]);
+          const float dHx = uM[q][3] - up[q][3], dHy = uM[q][4] - up[q][4];
+          const float dHz = uM[q][5] - up[q][5];
+          const float nx = nv[q][0], ny = nv[q][1], nz = nv[q][2], sc = 0.5f * nv[q][3];
+          const float al = A.alpha;
+          const float aE = al * fmaf(nz, dEz, fmaf(ny, dEy, nx * dEx));
+          const float aH = al * fmaf(nz, dHz, fmaf(ny, dHy, nx * dHx));
+          // fluxE = -n x dH + alpha (n (n.dE) - dE), fluxH = n x dE + alpha (n (n.dH) - dH)
+          float fl[6];
+          fl[0] = fmaf(-al, dEx, fmaf(nx, aE, fmaf(-ny, dHz, nz * dHy)));
+          fl[1] = fmaf(-al, dEy, fmaf(ny, aE, fmaf(-nz, dHx, nx * dHz)));
+          fl[2] = fmaf(-al, dEz, fmaf(nz, aE, fmaf(-nx, dHy, ny * dHx)));
+          fl[3] = fmaf(-al, dHx, fmaf(nx, aH, fmaf(-nz, dEy, ny * dEz)));
+          fl[4] = fmaf(-al, dHy, fmaf(ny, aH, fmaf(-nx, dEz, nz * dEx)));
+          fl[5] = fmaf(-al, dHz, fmaf(nz, aH, fmaf(-ny, dEx, nx * dEy)));
+          float* fr = F + int(item[q] & 31) * FSTR + int((item[q] >> 5) & 127);
+#pragma unroll
+          for (int c = 0; c < 6; ++c) fr[c * E * FSTR] = sc * fl[c];
+        }
+      }
+      named_sync(2, D::PRODUCERS);                     // the flux buffer is complete
+      // ---- X(t): row xn, chunks xq + QR q (8 values each), and the row maximum
+      const bool live = xe < Ev;
+      float x[D::CPT][8];
+      float xmax = 0.f;
+#pragma unroll
+      for (int q = 0; q < D::CPT; ++q) {
+        const int ch = xq + D::QR * q;
+        float v[8];
+        if (ch < D::CF) {                              // g^mu, nodes j0 .. j0 + 7
+          const int mu = ch / D::CG, j0 = (ch - mu * D::CG) * 8;
+          const float ca = sgn * sg[(3 * mu + (o + 1) % 3) * E + xe];
+          const float cb = -sgn * sg[(3 * mu + (o + 2) % 3) * E + xe];
+          float va[8], vb[8];
+          lds8(su + (fa * E + xe) * Np + j0, va);
+          lds8(su + (fb * E + xe) * Np + j0, vb);
+#pragma unroll
+          for (int j = 0; j < 8; ++j) v[j] = j0 + j < Np ? fmaf(ca, va[j], cb * vb[j]) : 0.f;
+        } else {                                       // flux, face nodes m0 .. m0 + 7
+          const int m0 = (ch - D::CF) * 8;
+          if (m0 < NF) {
+            lds8(F + xn * FSTR + m0, v);
+#pragma unroll
+            for (int j = 0; j < 8; ++j) v[j] = m0 + j < NF ? v[j] : 0.f;
+          } else {
+#pragma unroll
+            for (int j = 0; j < 8; ++j) v[j] = 0.f;
+          }
+        }
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          x[q][j] = live ? v[j] : 0.f;
+          xmax = fmaxf(xmax, fabsf(x[q][j]));
+        }
+      }
+      sBound[xq * ROWS + xn] = xmax;
+      named_sync(2, D::PRODUCERS);                     // row maxima published
+      float rmax = 0.f;
+#pragma unroll
+      for (int q = 0; q < D::QR; ++q) rmax = fmaxf(rmax, sBound[q * ROWS + xn]);
+      const float s = row_scale(rmax);
+      if (xq == 0) sScale[(t & 3) * ROWS + xn] = s;
+      // the single X buffer is free once the MMAs of tile t-1 have completed
+      if (t >= 1) wait_or_flag(&s_mma_done[(t - 1) & 1], ((t - 1) >> 1) & 1, A.status);
+#pragma unroll
+      for (int q = 0; q < D::CPT; ++q) {
+        const int ch = xq + D::QR * q;
+        uint32_t hi[4], lo[4];
+#pragma unroll
+        for (int p = 0; p < 4; ++p) {
+          const float2 w = __fmul2_rn(make_float2(x[q][2 * p], x[q][2 * p + 1]), f2(s));
+          tc::split2(w.x, w.y, hi[p], lo[p]);
+        }
+        // canonical K-major layout: chunk ch of row n at byte (ch * NN + n) * 16
+        const int off = (ch * D::NN + xn) * 16;
+        *reinterpret_cast<uint4*>(sXhi + off) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+        *reinterpret_cast<uint4*>(sXlo + off) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+      }
+      tc::fence_proxy_async_smem();                    // X stores -> tensor-core reads
+      tc::mbar_arrive(&s_x_full);
+    }
+  }
+
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) tc::tmem_dealloc(tbase, 512);
+}
+
+template <int N>
+cudaError_t launch_tt_stage_n(bool rk, const StageArgs& a, int num_sms, cudaStream_t s) {
+  using D = TtDims<N>;
+  static bool attr[2][16] = {};
+  int dev = 0;
+  cudaError_t err = cudaGetDevice(&dev);
+  if (err != cudaSuccess) return err;
+  dev &= 15;
+  auto kern = rk ? tt_stage_kernel<N, true> : tt_stage_kernel<N, false>;
+  // at least 120 KB of shared memory: never two CTAs (each takes all 512
+  // tensor-memory columns) on one SM
+  constexpr int smem = D::SMEM > 120 * 1024 ? D::SMEM : 120 * 1024;
+  if (!attr[rk ? 1 : 0][dev]) {
+    err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (err != cudaSuccess) return err;
+    attr[rk ? 1 : 0][dev] = true;
+  }
+  const int grid = a.num_tiles < num_sms ? a.num_tiles : num_sms;
+  if (grid <= 0) return cudaSuccess;
+  kern<<<grid, D::THREADS, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace dgdev
+
+#define DG_INSTANTIATE_TT_STAGE(NN)                                                        \
+  namespace dgdev {                                                                         \
+  template cudaError_t launch_tt_stage_n<NN>(bool, const StageArgs&, int, cudaStream_t);    \
+  }

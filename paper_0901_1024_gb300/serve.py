@@ -197,7 +197,7 @@ class Server:
     def _choose_impl(self, N, solves):
         if not self.autotune:
             return self.impl
-        if N > 4:
+        if N > 6:
             return Mesh.STAGE_FP32
         K = sum(s.K for s in solves)
         key = (N, min(3, int(math.log10(max(K, 1))) - 2))     # <1e3, <1e4, <1e5, more

@@ -83,6 +83,111 @@ def test_rhs_parity_both_implementations(env, N, impl):
     assert rel(got, oracle.rhs(om, u32.astype(np.float64))) < RHS_TOL
 
 
+@pytest.mark.parametrize("N", [5, 6])
+def test_tc_operator_in_tensor_memory_rhs_parity(env, N):
+    """Orders 5, 6 on the tensor cores (operator in tensor memory, tiles of 8):
+    K = 162 = 20 tiles + a ragged tile of 2, rows of very different scales."""
+    torch, dg = env
+    verts, tets = kuhn_box_mesh(3, 0.15, 40 + N)
+    mesh, om = _setup(dg, verts, tets, N)
+    u32 = random_fields(om.K, om.Np, 50 + N).astype(np.float32)
+    u32[:, ::7] *= 1e-6
+    mesh.trace_enable(4)
+    got = _gpu_rhs(torch, mesh, u32, impl=TC)
+    mesh.set_stage_impl(0)
+    assert _stage_kinds(mesh) == {5}
+    assert np.isfinite(got).all()
+    assert rel(got, oracle.rhs(om, u32.astype(np.float64))) < RHS_TOL
+
+
+@pytest.mark.parametrize("N", [5, 6])
+def test_tc_operator_in_tensor_memory_step_parity(env, N):
+    """20 LSERK4 steps of the cavity mode on the tensor cores at orders 5, 6."""
+    torch, dg = env
+    verts, tets = kuhn_box_mesh(2, 0.1, 0)
+    mesh, om = _setup(dg, verts, tets, N)
+    mesh.set_stage_impl(TC)
+    u0 = cavity_mode(om.x, om.y, om.z, 0.0).astype(np.float32)
+    u = torch.from_numpy(u0).cuda()
+    res = torch.zeros_like(u)
+    mesh.trace_enable(200)
+    mesh.step(u, res, mesh.dt_cfl, 20)
+    torch.cuda.synchronize()
+    mesh.set_stage_impl(0)
+    assert _stage_kinds(mesh) == {4}
+    ue, re_ = oracle.lserk4_run(om, u0.astype(np.float64), mesh.dt_cfl, 20)
+    assert rel(u.cpu().numpy(), ue) < STEP_TOL
+    assert rel(res.cpu().numpy(), re_) < 10 * STEP_TOL
+
+
+def test_tc_operator_in_tensor_memory_several_tiles_per_cta(env):
+    """N = 6, K = 3 072 = 384 tiles of 8: every persistent CTA runs its
+    pipeline over two or three tiles; two steps against the oracle."""
+    torch, dg = env
+    verts, tets = kuhn_box_mesh(8, 0.15, 5)
+    mesh, om = _setup(dg, verts, tets, 6)
+    mesh.set_stage_impl(TC)
+    u0 = random_fields(om.K, om.Np, 43).astype(np.float32)
+    u = torch.from_numpy(u0).cuda()
+    res = torch.zeros_like(u)
+    mesh.trace_enable(10)
+    mesh.step(u, res, mesh.dt_cfl, 2)
+    torch.cuda.synchronize()
+    mesh.set_stage_impl(0)
+    assert _stage_kinds(mesh) == {4}
+    ue, _ = oracle.lserk4_run(om, u0.astype(np.float64), mesh.dt_cfl, 2)
+    assert rel(u.cpu().numpy(), ue) < STEP_TOL
+
+
+@pytest.mark.parametrize("N", [5, 6])
+def test_tc_operator_in_tensor_memory_every_magnitude(env, N):
+    """Per-element magnitudes from zero through 1e-37 to 1e20: finite, and each
+    magnitude class within the one-RHS tolerance."""
+    torch, dg = env
+    verts, tets = kuhn_box_mesh(4, 0.15, 6)
+    mesh, om = _setup(dg, verts, tets, N)
+    rng = np.random.Generator(np.random.PCG64(33))
+    scales = np.array([0.0, 1e-37, 1e-30, 1e-3, 1.0, 1e20])
+    cls = rng.integers(0, len(scales), om.K)
+    u32 = (random_fields(om.K, om.Np, 34) * scales[cls][None, :, None]).astype(np.float32)
+    got = _gpu_rhs(torch, mesh, u32, impl=TC)
+    mesh.set_stage_impl(0)
+    want = oracle.rhs(om, u32.astype(np.float64))
+    assert np.isfinite(got).all()
+    for k in range(len(scales)):
+        sel = cls == k
+        if np.any(want[:, sel]):
+            assert rel(got[:, sel], want[:, sel]) < RHS_TOL, scales[k]
+
+
+def test_tc_operator_in_tensor_memory_full_size_n6(env):
+    """The N = 6 workload (16^3 x 6 = 24 576 tets, cavity mode plus noise):
+    tensor-core and FP32 stages agree everywhere after one step, and sampled
+    elements match the oracle on a 5-ring patch."""
+    torch, dg = env
+    verts, tets = kuhn_box_mesh(16, 0.15, 0)
+    mesh = dg.Mesh(verts, tets, 6)
+    x = mesh.nodes()
+    u0 = (cavity_mode(x[0], x[1], x[2], 0.0) +
+          1e-3 * random_fields(mesh.K, mesh.Np, 12)).astype(np.float32)
+    out = []
+    for impl in (TC, FP32):
+        mesh.set_stage_impl(impl)
+        u = torch.from_numpy(u0).cuda()
+        res = torch.zeros_like(u)
+        mesh.step(u, res, mesh.dt_cfl, 1)
+        out.append(u.cpu().numpy())
+    mesh.set_stage_impl(0)
+    assert np.isfinite(out[0]).all()
+    assert rel(out[0], out[1].astype(np.float64)) < RHS_TOL
+    seeds = np.array([mesh.K // 2 + 3, 6 * (16 * 16 * 8 + 16 * 5 + 7) + 2])
+    patch = _vertex_rings(tets, seeds, 5)
+    om = _oracle_on_patch(verts, tets, patch, 6)
+    ue, _ = oracle.lserk4_run(om, u0[:, patch].astype(np.float64), mesh.dt_cfl, 1)
+    pos = np.searchsorted(patch, seeds)
+    assert rel(out[0][:, seeds], ue[:, pos]) < RHS_TOL
+
+
 def test_tc_falls_back_when_tiles_are_not_aligned(env):
     """K * Np not a multiple of 4 (K = 162, N = 4): the FP32 kernel runs."""
     torch, dg = env
@@ -389,12 +494,12 @@ def test_full_size_step_sampled(env, full):
     assert rel(got[:, seeds], ue[:, pos]) < RHS_TOL
 
 
-@pytest.mark.parametrize("impl", [FP32, TC])
-def test_rk_stages_equal_a_step(env, impl):
+@pytest.mark.parametrize("impl,N", [(FP32, 4), (TC, 4), (TC, 6)])
+def test_rk_stages_equal_a_step(env, impl, N):
     """Five dg_rk_stage calls with swapped buffers are bit-identical to dg_step."""
     torch, dg = env
     verts, tets = kuhn_box_mesh(4, 0.1, 3)
-    mesh = dg.Mesh(verts, tets, 4)
+    mesh = dg.Mesh(verts, tets, N)
     mesh.set_stage_impl(impl)
     u0 = torch.from_numpy(random_fields(mesh.K, mesh.Np, 5).astype(np.float32)).cuda()
     u, res = u0.clone(), torch.zeros_like(u0)
