@@ -26,11 +26,11 @@
 //     chunks p / 48 + 8 q of row p % 48 -- a second barrier publishes the row
 //     maxima (row scale), and once the MMAs of tile t-1 have read the single X
 //     buffer, the scaled values are split into FP16 hi/lo and stored;
-//   * MMA/epilogue warps (4): warp 0 issues the 3 x KT/16 MMAs of tile t into
-//     accumulator t & 1 and all bulk copies; all four then read tile t-1's
-//     accumulator (tcgen05.ld), remove the scales and apply the LSERK4 update
-//     res <- a res + dt rhs, u <- u + b res in place in shared memory, and bulk
-//     copies write u_out and res back.
+//   * MMA/epilogue warps (4): warp 3 (its tensor-memory lanes hold no node)
+//     issues the 3 x KT/16 MMAs of tile t into accumulator t & 1 and all bulk
+//     copies, while warps 0..2 read tile t-1's accumulator (tcgen05.ld), remove
+//     the scales and apply the LSERK4 update res <- a res + dt rhs,
+//     u <- u + b res in place in shared memory; bulk copies write u_out and res.
 // Fields and geometry arrive by bulk copies NSU - 1 tiles ahead, the RK
 // register one tile ahead.
 #pragma once
@@ -77,7 +77,7 @@ template <int N> struct TtDims {
   static constexpr int OFF_R = OFF_G + NSU * G_FLOATS * 4;   // NSR slots
   static constexpr int OFF_F = OFF_R + NSR * U_FLOATS * 4;   // one flux buffer
   static constexpr int OFF_BND = OFF_F + ROWS * FSTR * 4;    // [QR][ROWS] partial row maxima
-  static constexpr int OFF_SC = OFF_BND + QR * ROWS * 4;     // [4][ROWS] row scales
+  static constexpr int OFF_SC = OFF_BND + QR * ROWS * 4;     // [4][ROWS] column factors
   static constexpr int OFF_TAB = OFF_SC + 4 * ROWS * 4;      // face-node table (NF bytes)
   static constexpr int SMEM = OFF_TAB + ((NF + 15) & ~15);
   static_assert(NN % 16 == 0 && NN <= 256, "MMA N");
@@ -91,6 +91,11 @@ template <int N> struct TtDims {
   static_assert(OFF_U % 16 == 0 && OFF_G % 16 == 0 && OFF_R % 16 == 0 && OFF_F % 16 == 0,
                 "alignment");
   static_assert(SMEM <= 226 * 1024, "shared memory budget");
+  // set-up: Op staged row by row (16-byte padded rows: the lane-per-row reads of
+  // a warp are conflict-free) in the X / U region, before the ring starts
+  static constexpr int OPW = ACOLS + 4;               // staged row stride (words)
+  static constexpr int OP_VEC = 128 * ACOLS / 4;      // 16-byte words of one piece
+  static_assert(128 * OPW * 4 <= OFF_R, "operator staging area");
 };
 
 // One thread: bulk copies of tile `tile`'s fields and geometry block.
@@ -165,35 +170,61 @@ __global__ void __launch_bounds__(TtDims<N>::THREADS, 1) tt_stage_kernel(const S
   __syncthreads();
   tc::fence_after_sync();
   const uint32_t tbase = s_tmem;
-  if (warp < 4) {
-    // lane = node row of Op: both pieces, 16 columns per tensor-memory store
-    const uint4* src = reinterpret_cast<const uint4*>(A.tcB) + size_t(warp * 32 + lane) * (D::ACOLS / 4);
-    const uint32_t trow = tbase + (uint32_t(warp * 32) << 16);
+  // Op into tensor memory, one piece at a time: all threads copy the piece to
+  // shared memory (coalesced, every load in flight at once), then lane r of
+  // warps 0..3 writes row r (16 columns per tensor-memory store)
 #pragma unroll 1
-    for (int piece = 0; piece < 2; ++piece) {
+  for (int piece = 0; piece < 2; ++piece) {
+    const uint4* src = reinterpret_cast<const uint4*>(A.tcB) + size_t(piece) * D::OP_VEC;
+    uint4* stage = reinterpret_cast<uint4*>(smem);
+    constexpr int PER = (D::OP_VEC + D::THREADS - 1) / D::THREADS;
+    uint4 w[PER];
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
+      const int i = tid + q * D::THREADS;
+      if (i < D::OP_VEC) w[q] = __ldg(src + i);
+    }
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
+      const int i = tid + q * D::THREADS;
+      if (i < D::OP_VEC) {
+        const int r = i / (D::ACOLS / 4), c4 = i - r * (D::ACOLS / 4);
+        stage[r * (D::OPW / 4) + c4] = w[q];
+      }
+    }
+    __syncthreads();
+    if (warp < 4) {
+      const uint4* row = stage + (warp * 32 + lane) * (D::OPW / 4);
+      const uint32_t trow = tbase + (uint32_t(warp * 32) << 16) + piece * D::ACOLS;
 #pragma unroll 1
       for (int c0 = 0; c0 < D::ACOLS; c0 += 16) {
         uint32_t v[16];
-        const uint4* s4 = src + size_t(piece) * 128 * (D::ACOLS / 4) + c0 / 4;
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-          const uint4 w = __ldg(s4 + q);
-          v[4 * q] = w.x; v[4 * q + 1] = w.y; v[4 * q + 2] = w.z; v[4 * q + 3] = w.w;
+          const uint4 x = row[c0 / 4 + q];
+          v[4 * q] = x.x; v[4 * q + 1] = x.y; v[4 * q + 2] = x.z; v[4 * q + 3] = x.w;
         }
-        tc::tmem_st<16>(trow + piece * D::ACOLS + c0, v);
+        tc::tmem_st<16>(trow + c0, v);
       }
+      tc::tmem_st_wait();
     }
-    tc::tmem_st_wait();
+    tc::fence_before_sync();
+    __syncthreads();                                 // staging area free again
+    tc::fence_after_sync();
   }
-  tc::fence_before_sync();
-  __syncthreads();
-  tc::fence_after_sync();
 
   if (warp < 4) {
     // ======================= MMA issue + epilogue warps ========================
+    // Nodes i < Np <= 84 sit in tensor-memory lanes 0..95, so warp 3 (lanes
+    // 96..127) holds none: it issues the MMAs and all bulk copies while warps
+    // 0..2 apply the RK update.  Named barrier 1 (these 128 threads) closes
+    // iteration j: the update of tile j-1 is done (its tiles may be stored and
+    // its accumulator reused), and warp 3 has acquired X(j) -- which carries
+    // tile j's column factors to warps 0..2.
+    static_assert(Np <= 96, "warp 3 holds no node");
     const int node = warp * 32 + lane;
     const uint32_t lane_off = uint32_t(warp * 32) << 16;
-    if (warp == 0 && tc::elect_one()) {   // first loads: fields of tiles 0..NSU-2, res of tile 0
+    if (warp == 3 && tc::elect_one()) {   // first loads: fields of tiles 0..NSU-2, res of tile 0
       for (int t = 0; t < D::NSU - 1 && t < ntiles; ++t)
         tt_load_u<N>(A, blockIdx.x + t * gridDim.x, sU + t * D::U_FLOATS, sG + t * D::G_FLOATS,
                      &s_u_full[t]);
@@ -203,31 +234,28 @@ __global__ void __launch_bounds__(TtDims<N>::THREADS, 1) tt_stage_kernel(const S
     constexpr uint32_t IDESC = tc::idesc_f16(128, D::NN);
     constexpr uint32_t LBO = (D::NN / 8) * 128;
     for (int j = 0; j <= ntiles; ++j) {
-      if (j < ntiles) {
-        // every epilogue warp observes X(j) complete (this also publishes tile j's
-        // row scales) before the MMAs start, so no waiter can fall a phase behind
-        wait_or_flag(&s_x_full, j & 1, A.status);
-        named_sync(1, 128);
-      }
-      if (j < ntiles && warp == 0) {                 // MMAs of tile j
-        tc::fence_after_sync();
-        const uint32_t d_acc = tbase + D::ACC0 + (j & 1) * D::NN;
-        const uint64_t b_hi = tc::smem_desc(tc::smem_u32(sXhi), LBO, 128);
-        const uint64_t b_lo = b_hi + uint64_t(D::X_BYTES >> 4);
-#pragma unroll 1
-        for (int i = 0; i < 3 * D::KSTEPS; ++i) {
-          const int p = i / D::KSTEPS, ks = i - p * D::KSTEPS;   // passes: hi.hi, hi.lo, lo.hi
-          const uint64_t bd = (p == 1 ? b_lo : b_hi) + uint64_t((ks * 2 * LBO) >> 4);
-          const uint32_t ad = tbase + (p == 2 ? D::ACOLS : 0) + ks * 8;
-          tc::mma_f16_ts_warp(d_acc, ad, bd, IDESC, i > 0 ? 1u : 0u);
+      const int t = j - 1, buf = t & 1;               // tile whose update runs in iteration j
+      const int tile = blockIdx.x + t * gridDim.x;
+      const int k0 = tile * E, Ev = min(E, K - k0);
+      if (warp == 3) {
+        if (j < ntiles) {                              // MMAs of tile j into accumulator j & 1
+          wait_or_flag(&s_x_full, j & 1, A.status);
+          tc::fence_after_sync();
+          const uint32_t d_acc = tbase + D::ACC0 + (j & 1) * D::NN;
+          const uint64_t b_hi = tc::smem_desc(tc::smem_u32(sXhi), LBO, 128);
+          const uint64_t b_lo = b_hi + uint64_t(D::X_BYTES >> 4);
+          // fully unrolled: warp-uniform operands (base + constant) issue cheaply
+#pragma unroll
+          for (int i = 0; i < 3 * D::KSTEPS; ++i) {
+            const int p = i / D::KSTEPS, ks = i - p * D::KSTEPS;   // passes: hi.hi, hi.lo, lo.hi
+            const uint64_t bd = (p == 1 ? b_lo : b_hi) + uint64_t((ks * 2 * LBO) >> 4);
+            const uint32_t ad = tbase + (p == 2 ? D::ACOLS : 0) + ks * 8;
+            tc::mma_f16_ts_warp(d_acc, ad, bd, IDESC, i > 0 ? 1u : 0u);
+          }
+          tc::mma_commit_warp(&s_mma_done[j & 1]);
         }
-        tc::mma_commit_warp(&s_mma_done[j & 1]);
         __syncwarp();
-      }
-      if (j >= 1) {                                  // epilogue of tile t = j - 1
-        const int t = j - 1, buf = t & 1;
-        const int tile = blockIdx.x + t * gridDim.x;
-        const int k0 = tile * E, Ev = min(E, K - k0);
+      } else if (j >= 1) {                             // RK update of tile t = j - 1
         float* su = sU + (t % D::NSU) * D::U_FLOATS;
         float* sr = sR + (t % D::NSR) * D::U_FLOATS;
         wait_or_flag(&s_mma_done[buf], (t >> 1) & 1, A.status);
@@ -244,9 +272,10 @@ __global__ void __launch_bounds__(TtDims<N>::THREADS, 1) tt_stage_kernel(const S
           for (int e = 0; e < E; ++e)
             dte[e] = RK && A.dt_elem && e < Ev ? __ldg(A.dt_elem + k0 + e) : A.dt;
           // column n = (c, e) is the tile row n * Np + node; u and res share one
-          // shared array, so every batch is loaded before any of its stores
+          // shared array, so every batch is loaded before any of its stores;
+          // columns are paired (n, n + 1) for packed FP32x2 arithmetic
           constexpr int CH = 12;
-          static_assert(ROWS % CH == 0, "epilogue batches");
+          static_assert(ROWS % CH == 0 && E % 2 == 0, "epilogue batches");
 #pragma unroll
           for (int n0 = 0; n0 < ROWS; n0 += CH) {
             float rv[CH], uv[CH];
@@ -258,51 +287,63 @@ __global__ void __launch_bounds__(TtDims<N>::THREADS, 1) tt_stage_kernel(const S
               }
             }
 #pragma unroll
-            for (int q = 0; q < CH; ++q) {
-              const int n = n0 + q, e = n % E;
-              if (e >= Ev) continue;
-              const float r = __uint_as_float(acc[n]) * (A.tc_inv_bscale / scl[n]);
+            for (int q = 0; q < CH; q += 2) {
+              const int n = n0 + q, e = n % E;           // e even: e + 1 < E
+              const float2 r = __fmul2_rn(
+                  make_float2(__uint_as_float(acc[n]), __uint_as_float(acc[n + 1])),
+                  make_float2(scl[n], scl[n + 1]));
               if (RK) {
-                const float rn = fmaf(A.a, rv[q], dte[e] * r);
-                sr[n * Np + node] = rn;
-                su[n * Np + node] = fmaf(A.b, rn, uv[q]);
+                const float2 rn = __ffma2_rn(f2(A.a), make_float2(rv[q], rv[q + 1]),
+                                             __fmul2_rn(make_float2(dte[e], dte[e + 1]), r));
+                const float2 un = __ffma2_rn(f2(A.b), rn, make_float2(uv[q], uv[q + 1]));
+                if (e < Ev) {
+                  sr[n * Np + node] = rn.x;
+                  su[n * Np + node] = un.x;
+                }
+                if (e + 1 < Ev) {
+                  sr[(n + 1) * Np + node] = rn.y;
+                  su[(n + 1) * Np + node] = un.y;
+                }
               } else {
-                sr[n * Np + node] = r;
+                if (e < Ev) sr[n * Np + node] = r.x;
+                if (e + 1 < Ev) sr[(n + 1) * Np + node] = r.y;
               }
             }
           }
         }
-        tc::fence_proxy_async_smem();
-        named_sync(1, 128);
-        if (warp == 0 && tc::elect_one()) {
-          const uint32_t fb = uint32_t(Ev) * Np * 4;
-          for (int c = 0; c < 6; ++c) {
-            const size_t g = (size_t(c) * K + k0) * Np;
-            if (RK) {
-              tc::bulk_s2g(A.u_out + g, su + c * E * Np, fb);
-              tc::bulk_s2g(A.res + g, sr + c * E * Np, fb);
-            } else {
-              tc::bulk_s2g(A.rhs + g, sr + c * E * Np, fb);
-            }
-          }
-          tc::bulk_commit();
-          // slots of tile t-1 (stored one round ago) take tiles t+NSU-1 and t+1
-          asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
-          tc::fence_proxy_async_smem();
-          if (t + D::NSU - 1 < ntiles) {
-            const int s = (t + D::NSU - 1) % D::NSU;
-            tt_load_u<N>(A, tile + (D::NSU - 1) * gridDim.x, sU + s * D::U_FLOATS,
-                         sG + s * D::G_FLOATS, &s_u_full[s]);
-          }
-          if (RK && t + 1 < ntiles) {
-            const int s = (t + 1) % D::NSR;
-            tt_load_res<N>(A, tile + gridDim.x, sR + s * D::U_FLOATS, &s_r_full[s]);
+        tc::fence_proxy_async_smem();                  // tile stores -> bulk-copy reads
+      }
+      named_sync(1, 128);
+      if (warp == 3 && j >= 1 && tc::elect_one()) {
+        float* su = sU + (t % D::NSU) * D::U_FLOATS;
+        float* sr = sR + (t % D::NSR) * D::U_FLOATS;
+        const uint32_t fb = uint32_t(Ev) * Np * 4;
+        for (int c = 0; c < 6; ++c) {
+          const size_t g = (size_t(c) * K + k0) * Np;
+          if (RK) {
+            tc::bulk_s2g(A.u_out + g, su + c * E * Np, fb);
+            tc::bulk_s2g(A.res + g, sr + c * E * Np, fb);
+          } else {
+            tc::bulk_s2g(A.rhs + g, sr + c * E * Np, fb);
           }
         }
-        __syncwarp();
+        tc::bulk_commit();
+        // slots of tile t-1 (stored one round ago) take tiles t+NSU-1 and t+1
+        asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
+        tc::fence_proxy_async_smem();
+        if (t + D::NSU - 1 < ntiles) {
+          const int s = (t + D::NSU - 1) % D::NSU;
+          tt_load_u<N>(A, tile + (D::NSU - 1) * gridDim.x, sU + s * D::U_FLOATS,
+                       sG + s * D::G_FLOATS, &s_u_full[s]);
+        }
+        if (RK && t + 1 < ntiles) {
+          const int s = (t + 1) % D::NSR;
+          tt_load_res<N>(A, tile + gridDim.x, sR + s * D::U_FLOATS, &s_r_full[s]);
+        }
       }
+      __syncwarp();
     }
-    if (warp == 0 && tc::elect_one()) tc::bulk_wait_all();
+    if (warp == 3 && tc::elect_one()) tc::bulk_wait_all();
     __syncwarp();
   } else {
     // ============================ producer warps ===============================
@@ -447,7 +488,8 @@ __global__ void __launch_bounds__(TtDims<N>::THREADS, 1) tt_stage_kernel(const S
 #pragma unroll
       for (int q = 0; q < D::QR; ++q) rmax = fmaxf(rmax, sBound[q * ROWS + xn]);
       const float s = row_scale(rmax);
-      if (xq == 0) sScale[(t & 3) * ROWS + xn] = s;
+      // column factor of the accumulator: 1 / (Op scale x row scale), a power of two
+      if (xq == 0) sScale[(t & 3) * ROWS + xn] = A.tc_inv_bscale / s;
       // the single X buffer is free once the MMAs of tile t-1 have completed
       if (t >= 1) wait_or_flag(&s_mma_done[(t - 1) & 1], ((t - 1) >> 1) & 1, A.status);
 #pragma unroll
