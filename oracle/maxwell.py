@@ -23,6 +23,22 @@ dg-subtasks, into a volume part and a lifted surface part:
 The time stepper is the five-stage, two-register low-storage RK4 of Carpenter
 and Kennedy (1994), cited in Section 6:
       res <- a_i res + dt rhs(u),   u <- u + b_i res,   i = 0..4.
+
+Materials and boundaries (optional arguments eps, mu, bc):
+  * per-element permittivity eps_k and permeability mu_k (the conservation form
+    of Section 6 carries diag(eps, mu) on u_t): rhs_E is divided by eps_k and
+    rhs_H by mu_k; the flux is the upwind flux of Section 6 with impedance
+    Z = sqrt(mu / eps) and admittance Y = 1 / Z, written with jumps
+    [u] = u+ - u-:
+        n.(F - F*)_E = 1/(Z- + Z+) n x ( Z+ [H] - alpha n x [E])
+        n.(F - F*)_H = 1/(Y- + Y+) n x (-Y+ [E] - alpha n x [H])
+    (the 1/2 and the cross-face average {Z} of Section 6 combine into
+    1/(Z- + Z+); for Z- = Z+ = 1 this is the vacuum flux above);
+  * boundary faces: bc = 0 a perfect conductor (E+ = -E-, H+ = H-), bc = 1 a
+    characteristic absorbing boundary (Section 6's sample calculation): the
+    exterior state is zero, so no wave enters; on either, Z+ = Z-.
+  * the energy weights E by eps and H by mu: 1/2 sum_k J_k (eps_k E^T M E +
+    mu_k H^T M H).
 """
 from __future__ import annotations
 
@@ -70,35 +86,60 @@ def volume_term(mesh, u):
     return np.concatenate([curlH, -curlE])
 
 
-def surface_flux(mesh, u, alpha: float = 1.0):
-    """Step a3: Fscale * n.(F - F*) at every face node, shape (6, K, 4*Nfp)."""
+def _materials(mesh, eps, mu):
+    eps = np.ones(mesh.K) if eps is None else np.asarray(eps, dtype=np.float64)
+    mu = np.ones(mesh.K) if mu is None else np.asarray(mu, dtype=np.float64)
+    return eps, mu
+
+
+def surface_flux(mesh, u, alpha: float = 1.0, eps=None, mu=None, bc=None):
+    """Step a3: Fscale * n.(F - F*) at every face node, shape (6, K, 4*Nfp).
+
+    eps, mu: per-element material (default 1); bc: (K, 4) boundary kind of
+    each face, 0 perfect conductor (default), 1 absorbing (read on boundary
+    faces only)."""
     K, Nfp = mesh.K, mesh.Nfp
+    eps, mu = _materials(mesh, eps, mu)
     flat = u.reshape(6, -1)
     uM = flat[:, mesh.vmapM].reshape(6, K, 4, Nfp)
     uP = flat[:, mesh.vmapP].reshape(6, K, 4, Nfp).copy()
-    bnd = mesh.boundary[None, :, :, None]
-    uP[:3] = np.where(bnd, -uM[:3], uP[:3])      # PEC: E+ = -E-
-    uP[3:] = np.where(bnd, uM[3:], uP[3:])       #      H+ =  H-
-    dE = uM[:3] - uP[:3]
-    dH = uM[3:] - uP[3:]
+    bnd = mesh.boundary
+    absorb = bnd & (np.zeros((K, 4), bool) if bc is None else np.asarray(bc) == 1)
+    pec = bnd & ~absorb
+    uP[:3] = np.where(pec[None, :, :, None], -uM[:3], uP[:3])      # PEC: E+ = -E-
+    uP[3:] = np.where(pec[None, :, :, None], uM[3:], uP[3:])       #      H+ =  H-
+    uP = np.where(absorb[None, :, :, None], 0.0, uP)               # absorbing: u+ = 0
+    # impedances of both sides (the neighbour's, or the element's own on boundaries)
+    Z = np.sqrt(mu / eps)
+    ZM = np.repeat(Z[:, None], 4, axis=1)
+    ZP = np.where(bnd, ZM, Z[mesh.EToE])
+    YM, YP = 1.0 / ZM, 1.0 / ZP
+    jE = uP[:3] - uM[:3]                      # [E] = E+ - E-
+    jH = uP[3:] - uM[3:]
     n = (mesh.nx[:, :, None], mesh.ny[:, :, None], mesh.nz[:, :, None])
-    ndE = n[0] * dE[0] + n[1] * dE[1] + n[2] * dE[2]
-    ndH = n[0] * dH[0] + n[1] * dH[1] + n[2] * dH[2]
-    nxdH = _cross(n, dH)
-    nxdE = _cross(n, dE)
-    fE = [-nxdH[i] + alpha * (n[i] * ndE - dE[i]) for i in range(3)]
-    fH = [nxdE[i] + alpha * (n[i] * ndH - dH[i]) for i in range(3)]
-    flux = np.stack(fE + fH) * (0.5 * mesh.Fscale[None, :, :, None])
+    nxjE = _cross(n, jE)
+    nxjH = _cross(n, jH)
+    nxnxjE = _cross(n, nxjE)
+    nxnxjH = _cross(n, nxjH)
+    cE = (1.0 / (ZM + ZP))[:, :, None]
+    cH = (1.0 / (YM + YP))[:, :, None]
+    zp, yp = ZP[:, :, None], YP[:, :, None]
+    fE = [cE * (zp * nxjH[i] - alpha * nxnxjE[i]) for i in range(3)]
+    fH = [cH * (-yp * nxjE[i] - alpha * nxnxjH[i]) for i in range(3)]
+    flux = np.stack(fE + fH) * mesh.Fscale[None, :, :, None]
     return flux.reshape(6, K, 4 * Nfp)
 
 
-def rhs(mesh, u, alpha: float = 1.0):
+def rhs(mesh, u, alpha: float = 1.0, eps=None, mu=None, bc=None):
     """Semi-discrete right-hand side du/dt, shape (6, K, Np), FP64."""
     u = np.asarray(u, dtype=np.float64)
+    eps, mu = _materials(mesh, eps, mu)
     vol = volume_term(mesh, u)
-    flux = surface_flux(mesh, u, alpha)
+    flux = surface_flux(mesh, u, alpha, eps, mu, bc)
     surf = np.einsum("im,fkm->fki", mesh.ref.LIFT, flux)
-    return vol + surf
+    w = np.concatenate([np.repeat(1.0 / eps[None, :], 3, axis=0),
+                        np.repeat(1.0 / mu[None, :], 3, axis=0)])
+    return (vol + surf) * w[:, :, None]
 
 
 def stage_update(u, res, r, a, b, dt):
@@ -107,24 +148,30 @@ def stage_update(u, res, r, a, b, dt):
     return u + b * res, res
 
 
-def lserk4_run(mesh, u, dt: float, nsteps: int, res=None, alpha: float = 1.0):
+def lserk4_run(mesh, u, dt: float, nsteps: int, res=None, alpha: float = 1.0,
+               eps=None, mu=None, bc=None):
     """Advance u by nsteps LSERK4 steps; returns (u, res)."""
     a, b, _ = lserk4_coefficients()
     u = np.array(u, dtype=np.float64)
     res = np.zeros_like(u) if res is None else np.array(res, dtype=np.float64)
     for _ in range(nsteps):
         for i in range(5):
-            u, res = stage_update(u, res, rhs(mesh, u, alpha), a[i], b[i], dt)
+            u, res = stage_update(u, res, rhs(mesh, u, alpha, eps, mu, bc), a[i], b[i], dt)
     return u, res
 
 
-def energy(mesh, u):
-    """Discrete energy 1/2 sum_k J_k sum_fields u_k^T M u_k."""
+def energy(mesh, u, eps=None, mu=None):
+    """Discrete energy 1/2 sum_k J_k (eps_k E_k^T M E_k + mu_k H_k^T M H_k)."""
     u = np.asarray(u, dtype=np.float64)
+    eps, mu = _materials(mesh, eps, mu)
     Mu = np.einsum("ij,fkj->fki", mesh.ref.M, u)
-    return 0.5 * float(np.sum(mesh.J[None, :, None] * u * Mu))
+    w = np.concatenate([np.repeat(eps[None, :], 3, axis=0), np.repeat(mu[None, :], 3, axis=0)])
+    return 0.5 * float(np.sum((mesh.J[None, :] * w)[:, :, None] * u * Mu))
 
 
-def cfl_dt(mesh, C: float = 1.0):
-    """Time step dt = C * min_{k,f} (1/Fscale) * 2/(N+1)^2."""
-    return C * float(np.min(1.0 / mesh.Fscale)) * 2.0 / (mesh.N + 1) ** 2
+def cfl_dt(mesh, C: float = 1.0, eps=None, mu=None):
+    """Time step dt = C * min_{k,f} (sqrt(eps_k mu_k) / Fscale) * 2/(N+1)^2 (the
+    wave speed of element k is 1 / sqrt(eps_k mu_k))."""
+    eps, mu = _materials(mesh, eps, mu)
+    slow = np.sqrt(eps * mu)[:, None]
+    return C * float(np.min(slow / mesh.Fscale)) * 2.0 / (mesh.N + 1) ** 2
