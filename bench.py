@@ -98,7 +98,7 @@ def load_peaks():
 
 def kernel_source_digest():
     h = hashlib.sha256()
-    for n in ("stage_kernel.cuh", "tc_stage.cuh", "tcgen05.cuh", "device.h"):
+    for n in ("stage_kernel.cuh", "tc_stage.cuh", "tc_stage_t.cuh", "tcgen05.cuh", "device.h"):
         with open(os.path.join(ROOT, "paper_0901_1024_gb300", "csrc", n), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]

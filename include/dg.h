@@ -143,6 +143,30 @@ int dg_get_geometry(const dg_mesh* mesh, double* metric, double* J, double* norm
  * Host only. */
 int dg_set_flux(dg_mesh* mesh, double alpha);
 
+/* Materials (Section 6, where diag(eps, mu) multiplies u_t): per-element
+ * permittivity eps[k] and permeability mu[k], host arrays of K finite values
+ * > 0 (copied); NULL sets 1 for every element (vacuum, the default).  The
+ * stage then divides rhs_E by eps and rhs_H by mu and uses the upwind flux of
+ * Section 6 with impedance Z = sqrt(mu/eps) and admittance Y = 1/Z:
+ *   E: 1/(Z- + Z+) n x ( Z+ [H] - alpha n x [E]),
+ *   H: 1/(Y- + Y+) n x (-Y+ [E] - alpha n x [H]),   [u] = u+ - u-;
+ * dg_energy weights E by eps and H by mu, and dt_cfl scales with
+ * min sqrt(eps mu).  A mesh with materials (or absorbing faces) runs the FP32
+ * CUDA-core stage.  Host only.  Errors: DG_ERR_ARG (NULL mesh, a value not
+ * finite or <= 0), DG_ERR_OOM. */
+int dg_set_materials(dg_mesh* mesh, const double* eps, const double* mu);
+
+/* Boundary condition of every boundary face: kind[4 k + f] for face f of
+ * element k (faces numbered as in dg_get_connectivity), either DG_BC_PEC
+ * (perfect conductor: E+ = -E-, H+ = H-; the default) or DG_BC_ABSORBING
+ * (characteristic absorbing boundary: exterior state zero, Z+ = Z-, so no
+ * wave enters).  Entries of interior faces are ignored.  NULL: every boundary
+ * face a perfect conductor.  Host only.  Errors: DG_ERR_ARG (NULL mesh, a kind
+ * other than 0 or 1), DG_ERR_OOM. */
+#define DG_BC_PEC       0
+#define DG_BC_ABSORBING 1
+int dg_set_boundary(dg_mesh* mesh, const int8_t* kind);
+
 /*
  * Implementation of the RK-stage operator (the paper notes that each operator
  * part may need its own strategy on the GPU, Section 4):

@@ -106,10 +106,36 @@ class Mesh:
     def set_flux(self, alpha: float):
         check(self._lib.dg_set_flux(self._h, float(alpha)), "dg_set_flux")
 
+    def set_materials(self, eps=None, mu=None):
+        """Per-element permittivity and permeability (K values > 0 each; None: 1).
+        The stage then uses the impedance-weighted upwind flux, dt_cfl and the
+        energy follow the materials, and the FP32 CUDA-core stage runs."""
+        e = None if eps is None else np.ascontiguousarray(eps, np.float64)
+        m = None if mu is None else np.ascontiguousarray(mu, np.float64)
+        for a in (e, m):
+            if a is not None and a.shape != (self.K,):
+                raise ValueError("eps and mu need one value per element")
+        check(self._lib.dg_set_materials(self._h, None if e is None else _dptr(e, np.float64),
+                                         None if m is None else _dptr(m, np.float64)),
+              "dg_set_materials")
+        self._read_info(self.N)
+
+    BC_PEC, BC_ABSORBING = 0, 1
+
+    def set_boundary(self, kind=None):
+        """Boundary kind of every face, (K, 4) array of BC_PEC / BC_ABSORBING
+        (read on boundary faces only; faces numbered as the normals of
+        dg_get_geometry); None: every boundary face a perfect conductor."""
+        k = None if kind is None else np.ascontiguousarray(kind, np.int8)
+        if k is not None and k.shape != (self.K, 4):
+            raise ValueError("kind needs shape (K, 4)")
+        check(self._lib.dg_set_boundary(self._h, None if k is None else k.ctypes.data),
+              "dg_set_boundary")
+
     STAGE_AUTO, STAGE_FP32, STAGE_TC = 0, 1, 2
 
     def set_stage_impl(self, impl: int):
-        """0 = auto (tensor cores for N = 2..4), 1 = FP32 CUDA cores, 2 = tensor cores."""
+        """0 = auto (tensor cores for N = 2..6), 1 = FP32 CUDA cores, 2 = tensor cores."""
         check(self._lib.dg_set_stage_impl(self._h, int(impl)), "dg_set_stage_impl")
 
     def nodes(self) -> np.ndarray:

@@ -29,6 +29,8 @@ SIGNATURES = {
     "dg_get_operators": (C.c_int, [_vp, _dp, _dp, _dp, _dp, _dp]),
     "dg_get_geometry": (C.c_int, [_vp, _dp, _dp, _dp, _dp]),
     "dg_set_flux": (C.c_int, [_vp, C.c_double]),
+    "dg_set_materials": (C.c_int, [_vp, _dp, _dp]),
+    "dg_set_boundary": (C.c_int, [_vp, _vp]),
     "dg_set_stage_impl": (C.c_int, [_vp, C.c_int]),
     "dg_rhs": (C.c_int, [_vp, _vp, _vp, _vp]),
     "dg_step": (C.c_int, [_vp, _vp, _vp, C.c_double, C.c_int, _vp]),

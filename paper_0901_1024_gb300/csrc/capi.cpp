@@ -31,6 +31,33 @@ namespace dg {
 void set_error(const std::string& msg) { g_error = msg; }
 }  // namespace dg
 
+namespace dg {
+void update_dt_cfl(dg_mesh* m) {
+  if (m->N == 0) return;
+  double mn = INFINITY;
+  for (int64_t k = 0; k < m->K; ++k) {
+    const double slow = m->eps.empty() ? 1.0 : std::sqrt(m->eps[k] * m->mu[k]);
+    for (int f = 0; f < 4; ++f) mn = std::fmin(mn, slow / m->Fscale[4 * k + f]);
+  }
+  m->dt_cfl = mn * 2.0 / ((m->N + 1.0) * (m->N + 1.0));
+}
+
+bool has_materials_or_absorbing(const dg_mesh* m) {
+  if (!m->eps.empty()) return true;
+  for (int8_t b : m->bc)
+    if (b == DG_BC_ABSORBING) return true;
+  return false;
+}
+}  // namespace dg
+
+// Drops the device copy of the mesh; the next device call rebuilds it.
+static void invalidate_device(dg_mesh* m) {
+  if (m->dev) {
+    dgdev::destroy_device_state(m->dev);
+    m->dev = nullptr;
+  }
+}
+
 extern "C" {
 
 const char* dg_last_error(void) { return g_error.c_str(); }
@@ -80,9 +107,51 @@ int dg_set_order(dg_mesh* m, int N) {
     return fail(DG_ERR_OOM, "host allocation failed");
   }
   m->N = N;
-  double mn = INFINITY;
-  for (double f : m->Fscale) mn = std::fmin(mn, 1.0 / f);
-  m->dt_cfl = mn * 2.0 / ((N + 1.0) * (N + 1.0));
+  dg::update_dt_cfl(m);
+  return DG_OK;
+}
+
+int dg_set_materials(dg_mesh* m, const double* eps, const double* mu) {
+  if (int rc = check_mesh(m, false)) return rc;
+  const int64_t K = m->K;
+  for (const double* a : {eps, mu})
+    if (a)
+      for (int64_t k = 0; k < K; ++k)
+        if (!std::isfinite(a[k]) || a[k] <= 0.0)
+          return fail(DG_ERR_ARG, "eps and mu must be finite and > 0 (element " +
+                                      std::to_string(k) + ")");
+  try {
+    if (!eps && !mu) {
+      m->eps.clear();
+      m->mu.clear();
+    } else {
+      m->eps.assign(K, 1.0);
+      m->mu.assign(K, 1.0);
+      if (eps) std::copy(eps, eps + K, m->eps.begin());
+      if (mu) std::copy(mu, mu + K, m->mu.begin());
+    }
+  } catch (const std::bad_alloc&) {
+    return fail(DG_ERR_OOM, "host allocation failed");
+  }
+  dg::update_dt_cfl(m);
+  invalidate_device(m);
+  return DG_OK;
+}
+
+int dg_set_boundary(dg_mesh* m, const int8_t* kind) {
+  if (int rc = check_mesh(m, false)) return rc;
+  const int64_t K = m->K;
+  if (kind)
+    for (int64_t i = 0; i < 4 * K; ++i)
+      if (kind[i] != DG_BC_PEC && kind[i] != DG_BC_ABSORBING)
+        return fail(DG_ERR_ARG, "boundary kind must be DG_BC_PEC or DG_BC_ABSORBING");
+  try {
+    if (kind) m->bc.assign(kind, kind + 4 * K);
+    else m->bc.clear();
+  } catch (const std::bad_alloc&) {
+    return fail(DG_ERR_OOM, "host allocation failed");
+  }
+  invalidate_device(m);
   return DG_OK;
 }
 
@@ -129,6 +198,28 @@ int dg_mesh_pack(const dg_mesh* const* meshes, int count, dg_mesh** out) {
       for (int32_t e : s->nbr_elem) m->nbr_elem.push_back(static_cast<int32_t>(e + k0));
       m->nbr_code.insert(m->nbr_code.end(), s->nbr_code.begin(), s->nbr_code.end());
       m->dt_cfl = std::fmin(m->dt_cfl, s->dt_cfl);
+      // materials and boundary kinds: the parts' own, defaults where a part has none
+      const bool any_mat = [&] {
+        for (int q = 0; q < count; ++q) if (!meshes[q]->eps.empty()) return true;
+        return false;
+      }();
+      const bool any_bc = [&] {
+        for (int q = 0; q < count; ++q) if (!meshes[q]->bc.empty()) return true;
+        return false;
+      }();
+      if (any_mat) {
+        if (s->eps.empty()) {
+          m->eps.insert(m->eps.end(), Ks, 1.0);
+          m->mu.insert(m->mu.end(), Ks, 1.0);
+        } else {
+          m->eps.insert(m->eps.end(), s->eps.begin(), s->eps.end());
+          m->mu.insert(m->mu.end(), s->mu.begin(), s->mu.end());
+        }
+      }
+      if (any_bc) {
+        if (s->bc.empty()) m->bc.insert(m->bc.end(), 4 * Ks, int8_t(DG_BC_PEC));
+        else m->bc.insert(m->bc.end(), s->bc.begin(), s->bc.end());
+      }
       k0 += Ks;
       v0 += s->nv;
     }

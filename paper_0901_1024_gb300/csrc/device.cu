@@ -108,14 +108,17 @@ __global__ void __launch_bounds__(kEnergyRows) energy_rows_kernel(const EnergyAr
   const int64_t Kr = A.k1 - A.k0, rows = 6 * Kr;
   const int64_t first = int64_t(blockIdx.x) * kEnergyRows, stride = int64_t(gridDim.x) * kEnergyRows;
   // thread t's row of a pass: its global offset (published for the copies);
-  // returns its element's Jacobian (loaded a pass ahead with two buffers; J > 0),
-  // or -1 for no row
+  // returns its weight J_k (times eps_k for E rows, mu_k for H rows with
+  // materials), loaded a pass ahead with two buffers (> 0), or -1 for no row
   auto row_of = [&](int64_t r0, int b) -> float {
     const int64_t g = r0 + threadIdx.x;
     if (g >= rows) return -1.f;
     const int64_t c = g / Kr, k = A.k0 + (g - c * Kr);
     sRow[b][threadIdx.x] = (c * A.K + k) * NP;
-    return __ldg(reinterpret_cast<const float*>(A.geo) + k * kGeoWords + 9);
+    const float J = __ldg(reinterpret_cast<const float*>(A.geo) + k * kGeoWords + 9);
+    if (!A.mat) return J;
+    const float4 w = __ldg(A.mat + k * kMatVecs);
+    return J * (c < 3 ? w.z : w.w);
   };
   auto issue = [&](int64_t r0, int b) {
     if (r0 < rows) {
@@ -215,12 +218,14 @@ __global__ void __launch_bounds__(kEnergyThreads) energy_kernel(const EnergyArgs
   double acc = 0.0;
   for (int k = A.k0 + blockIdx.x * nw + warp; k < A.k1; k += gridDim.x * nw) {
     float ek = 0.f;
+    const float4 mw = A.mat ? __ldg(A.mat + size_t(k) * kMatVecs) : make_float4(1.f, 1.f, 1.f, 1.f);
     for (int c = 0; c < 6; ++c) {
       const float* uk = A.u + (size_t(c) * A.K + k) * A.Np;
+      const float w = c < 3 ? mw.z : mw.w;          // eps for E, mu for H (1 in vacuum)
       for (int i = lane; i < A.Np; i += 32) {
         float s = 0.f;
         for (int j = 0; j < A.Np; ++j) s = fmaf(__ldg(A.M + j * A.Np + i), __ldg(uk + j), s);
-        ek = fmaf(__ldg(uk + i), s, ek);
+        ek = fmaf(w * __ldg(uk + i), s, ek);
       }
     }
 #pragma unroll
@@ -306,6 +311,7 @@ struct DeviceState {
   double* result = nullptr;
   int egrid = 0;
   void* tcB = nullptr;          // tensor-core B pieces (orders <= kTcMaxOrder)
+  float4* mat = nullptr;        // material records (meshes with materials), in the arena
   float* tcgeo = nullptr;       // word-major geometry for the tensor-core stage
   int tc_geo_stride = 0;
   float tc_inv_bscale = 1.f;
@@ -567,8 +573,9 @@ int ensure_device(dg_mesh* m, std::string& err) {
   // arena layout (bytes, each part 256-byte aligned)
   auto up = [](size_t x) { return (x + 255) & ~size_t(255); };
   const size_t geo_b = static_cast<size_t>(K) * dgdev::kGeoWords * 4;
+  const size_t mat_b = m->eps.empty() ? 0 : static_cast<size_t>(K) * dgdev::kMatVecs * 16;
   const size_t tcg_b = tc ? static_cast<size_t>(ntiles) * d->tc_geo_stride * 4 : 0;
-  const size_t o_tcg = up(geo_b), o_part = o_tcg + up(tcg_b);
+  const size_t o_mat = up(geo_b), o_tcg = o_mat + up(mat_b), o_part = o_tcg + up(tcg_b);
   const size_t o_res = o_part + up(sizeof(double) * d->egrid), o_stat = o_res + 256;
   const size_t total = o_stat + 256;
   std::vector<unsigned char> host(o_part, 0);
@@ -582,7 +589,8 @@ int ensure_device(dg_mesh* m, std::string& err) {
     uint32_t codes = 0;
     for (int f = 0; f < 4; ++f) {
       const int c = m->nbr_code[4 * k + f];
-      codes |= static_cast<uint32_t>(c + 1) << (8 * f);
+      const bool absorbing = c < 0 && !m->bc.empty() && m->bc[4 * k + f] == DG_BC_ABSORBING;
+      codes |= (absorbing ? dgdev::kAbsorbingCode : static_cast<uint32_t>(c + 1)) << (8 * f);
       for (int dd = 0; dd < 3; ++dd)
         g[12 + 4 * f + dd] = static_cast<float>(m->normals[(dd * K + k) * 4 + f]);
       g[15 + 4 * f] = static_cast<float>(m->Fscale[4 * k + f]);
@@ -590,6 +598,23 @@ int ensure_device(dg_mesh* m, std::string& err) {
       std::memcpy(&g[28 + f], &nb, 4);
     }
     std::memcpy(&g[10], &codes, 4);
+  }
+  if (mat_b) {
+    // material records: 1/eps, 1/mu, eps, mu, then the flux coefficients of each
+    // face from the impedances of both sides (the element's own on boundaries)
+    float4* mr = reinterpret_cast<float4*>(host.data() + o_mat);
+    for (int64_t k = 0; k < K; ++k) {
+      const double e = m->eps[k], u = m->mu[k], zm = std::sqrt(u / e);
+      mr[k * dgdev::kMatVecs] = make_float4(static_cast<float>(1.0 / e), static_cast<float>(1.0 / u),
+                                            static_cast<float>(e), static_cast<float>(u));
+      for (int f = 0; f < 4; ++f) {
+        const int64_t k2 = m->nbr_code[4 * k + f] < 0 ? k : m->nbr_elem[4 * k + f];
+        const double zp = std::sqrt(m->mu[k2] / m->eps[k2]), ym = 1.0 / zm, yp = 1.0 / zp;
+        mr[k * dgdev::kMatVecs + 1 + f] =
+            make_float4(static_cast<float>(zp / (zm + zp)), static_cast<float>(1.0 / (zm + zp)),
+                        static_cast<float>(yp / (ym + yp)), static_cast<float>(1.0 / (ym + yp)));
+      }
+    }
   }
   if (tc) {
     // tiled geometry, one contiguous block per tile: word-major [kTcGeoWords][E]
@@ -617,6 +642,7 @@ int ensure_device(dg_mesh* m, std::string& err) {
   DG_CUDA(cudaMemcpy(base, host.data(), host.size(), cudaMemcpyHostToDevice), "cudaMemcpy H2D");
   DG_CUDA(cudaMemset(base + o_stat, 0, 256), "cudaMemset");
   d->geo = reinterpret_cast<float4*>(base);
+  d->mat = mat_b ? reinterpret_cast<float4*>(base + o_mat) : nullptr;
   d->tcgeo = tc ? reinterpret_cast<float*>(base + o_tcg) : nullptr;
   d->partials = reinterpret_cast<double*>(base + o_part);
   d->result = reinterpret_cast<double*>(base + o_res);
@@ -630,6 +656,8 @@ int ensure_device(dg_mesh* m, std::string& err) {
 // field chunk 16-byte aligned: (K * Np) % 4 == 0 and 16-byte aligned buffers.
 static bool use_tc(const dg_mesh* m, std::initializer_list<const void*> bufs) {
   if (m->stage_impl == DG_STAGE_FP32 || m->N > dgdev::kTcMaxOrder) return false;
+  // materials and absorbing faces are handled by the FP32 kernel only
+  if (dg::has_materials_or_absorbing(m)) return false;
   // at N = 1 (Np = 4) the FP32 kernel is faster unless tensor cores are asked for
   if (m->stage_impl == DG_STAGE_AUTO && m->N == 1) return false;
   if ((m->K * m->ops.Np) % 4 != 0) return false;
@@ -647,6 +675,7 @@ static dgdev::StageArgs stage_args(dg_mesh* m, bool tc) {
   a.tc_inv_bscale = d->tc_inv_bscale;
   a.status = d->status;
   a.geo = d->geo;
+  a.mat = d->mat;
   a.D4 = d->D4;
   a.LIFT4 = d->LIFT4;
   a.fmask = d->fmask;
@@ -765,7 +794,7 @@ static int energy_impl(dg_mesh* m, const float* u, double* out, cudaStream_t s,
                        std::string& err, int64_t k0 = 0, int64_t k1 = -1) {
   DeviceState* d = m->dev;
   dgdev::EnergyArgs a{u, d->M, d->geo, static_cast<int>(d->K), d->Np, d->partials, d->result,
-                      static_cast<int>(k0), static_cast<int>(k1 < 0 ? d->K : k1)};
+                      static_cast<int>(k0), static_cast<int>(k1 < 0 ? d->K : k1), d->mat};
   DG_CUDA(traced(m, s, 2, [&] { return dgdev::launch_energy_partials(a, d->egrid, s); }),
           "energy kernel launch");
   DG_CUDA(traced(m, s, 3, [&] { return dgdev::launch_energy_final(a, d->egrid, s); }),
@@ -781,8 +810,8 @@ static int energy_impl(dg_mesh* m, const float* u, double* out, cudaStream_t s,
   return DG_OK;
 }
 
-int device_resident(const dg_mesh* m, const float** M, const void** geo, int64_t* K, int* Np,
-                    std::string& err) {
+int device_resident(const dg_mesh* m, const float** M, const void** geo, const void** mat,
+                    int64_t* K, int* Np, std::string& err) {
   int cur = -1;
   DG_CUDA(cudaGetDevice(&cur), "cudaGetDevice");
   const DeviceState* d = m->dev;
@@ -793,6 +822,7 @@ int device_resident(const dg_mesh* m, const float** M, const void** geo, int64_t
   }
   *M = d->M;
   *geo = d->geo;
+  *mat = d->mat;
   *K = d->K;
   *Np = d->Np;
   return DG_OK;

@@ -14,6 +14,17 @@ namespace dgdev {
 //   [12+4f .. 15+4f]  nx ny nz Fscale of face f
 //   [28+f]   neighbour element of face f (int32; itself on a wall)
 constexpr int kGeoWords = 32;
+// Neighbour code byte of a characteristic absorbing boundary face (0: perfect
+// conductor, 1..24: interior face).
+constexpr unsigned kAbsorbingCode = 0xFFu;
+// Optional material record, 5 float4 per tetrahedron (meshes with materials):
+//   [0]      1/eps, 1/mu, eps, mu
+//   [1 + f]  A_E, B_E, A_H, B_H of face f: the flux of Section 6 is
+//            A_E (-n x dH) + alpha B_E (n (n.dE) - dE) for E and
+//            A_H ( n x dE) + alpha B_H (n (n.dH) - dH) for H (d = u- - u+), with
+//            A_E = Z+/(Z- + Z+), B_E = 1/(Z- + Z+), A_H = Y+/(Y- + Y+),
+//            B_H = 1/(Y- + Y+); 1/2 each in vacuum.
+constexpr int kMatVecs = 5;
 
 // Stage-kernel tiling per order N: tile of E tetrahedra, G row groups (threads
 // = E * G).  Chosen so a thread holds at most 7 rows and the shared tiles of
@@ -40,6 +51,7 @@ struct StageArgs {
   int num_tiles;
   float a, b, dt, alpha;
   const float* dt_elem;    // RK mode: per-element time step [K], or null for dt
+  const float4* mat;       // [K][kMatVecs] material record, or null (vacuum)
   // tensor-core path only
   const float* tcgeo;       // per tile: [kTcGeoWords][tc_tile_elems(N)] word-major geometry
   int tc_geo_stride;        // floats per tile block
@@ -89,6 +101,7 @@ struct EnergyArgs {
   double* partials;    // [grid]
   double* result;      // [1]
   int k0, k1;          // elements k0 <= k < k1 (0, K: the whole mesh)
+  const float4* mat;   // material record (E rows weighted by eps, H rows by mu), or null
 };
 int energy_grid(int num_sms);
 cudaError_t launch_energy_partials(const EnergyArgs& a, int grid, cudaStream_t s);

@@ -62,6 +62,9 @@ struct dg_mesh {
   dg::RefOps ops;
   double dt_cfl = 0.0;
   double alpha = 1.0;
+  // materials and boundary kinds (empty: vacuum, every boundary face PEC)
+  std::vector<double> eps, mu;    // [K]
+  std::vector<int8_t> bc;         // [K][4], DG_BC_* (read on boundary faces)
   dgdev::DeviceState* dev = nullptr;
   int64_t last_launches = 0;
   bool trace = false;
@@ -69,6 +72,10 @@ struct dg_mesh {
 };
 
 namespace dg {
+// dt_cfl of the current order: min over k, f of sqrt(eps_k mu_k) / Fscale_kf, times 2 / (N + 1)^2
+void update_dt_cfl(dg_mesh* m);
+// true when the mesh has materials or absorbing boundary faces
+bool has_materials_or_absorbing(const dg_mesh* m);
 // mesh.cpp
 int mesh_build(dg_mesh* m, const double* verts, int64_t nv, const int32_t* tets, int64_t K,
                std::string& err);
@@ -89,10 +96,11 @@ int device_energy_range(dg_mesh* m, const float* u, int64_t k0, int64_t k1, doub
 int device_step_host(dg_mesh* m, float* u, float* res, double dt, int nsteps, double* energy,
                      void* stream, std::string& err);
 int device_trace_reset(dg_mesh* m, int reserve, std::string& err);
-// Device copies of M and the geometry records if the mesh is resident on the
-// current device at its current order (no allocation), else DG_ERR_STATE.
-int device_resident(const dg_mesh* m, const float** M, const void** geo, int64_t* K, int* Np,
-                    std::string& err);
+// Device copies of M, the geometry records and the material records (null in
+// vacuum) if the mesh is resident on the current device at its current order
+// (no allocation), else DG_ERR_STATE.
+int device_resident(const dg_mesh* m, const float** M, const void** geo, const void** mat,
+                    int64_t* K, int* Np, std::string& err);
 int device_trace_read(dg_mesh* m, double* ms, int32_t* kind, int64_t cap, int64_t* count,
                       std::string& err);
 }  // namespace dg

@@ -35,19 +35,22 @@ static __device__ __align__(256) double g_energy_partials[kMaxBlocks];
 // its 64 tetrahedra in a fixed order and writes partials[b].
 __global__ void __launch_bounds__(kThreads)
 energy_block_sums(const float* __restrict__ u, const float* __restrict__ M,
-                  const float* __restrict__ geo, int K, int Np, double* partials) {
+                  const float* __restrict__ geo, const float4* __restrict__ mat, int K, int Np,
+                  double* partials) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   double acc = 0.0;
   for (int q = 0; q < kElemsPerBlock / (kThreads / 32); ++q) {
     const int k = blockIdx.x * kElemsPerBlock + warp * (kElemsPerBlock / (kThreads / 32)) + q;
     if (k >= K) break;
     float ek = 0.f;
+    const float4 mw = mat ? __ldg(mat + size_t(k) * dgdev::kMatVecs) : make_float4(1.f, 1.f, 1.f, 1.f);
     for (int c = 0; c < 6; ++c) {
       const float* uk = u + (size_t(c) * K + k) * Np;
+      const float w = c < 3 ? mw.z : mw.w;        // eps for E, mu for H (1 in vacuum)
       for (int i = lane; i < Np; i += 32) {
         float s = 0.f;
         for (int j = 0; j < Np; ++j) s = fmaf(__ldg(M + j * Np + i), __ldg(uk + j), s);
-        ek = fmaf(__ldg(uk + i), s, ek);
+        ek = fmaf(w * __ldg(uk + i), s, ek);
       }
     }
 #pragma unroll
@@ -101,9 +104,10 @@ extern "C" int dg_energy_noalloc(dg_mesh* m, const float* u, double* energy, voi
   std::string err;
   const float* M = nullptr;
   const void* geo = nullptr;
+  const void* mat = nullptr;
   int64_t K = 0;
   int Np = 0;
-  if (int rc = dg::device_resident(m, &M, &geo, &K, &Np, err)) { dg::set_error(err); return rc; }
+  if (int rc = dg::device_resident(m, &M, &geo, &mat, &K, &Np, err)) { dg::set_error(err); return rc; }
   int dev = -1;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess || dev < 0 || dev >= 64) {
@@ -126,6 +130,7 @@ extern "C" int dg_energy_noalloc(dg_mesh* m, const float* u, double* energy, voi
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const int blocks = static_cast<int>((K + kElemsPerBlock - 1) / kElemsPerBlock);
   energy_block_sums<<<blocks, kThreads, 0, s>>>(u, M, static_cast<const float*>(geo),
+                                                static_cast<const float4*>(mat),
                                                 static_cast<int>(K), Np,
                                                 static_cast<double*>(partials));
   e = cudaGetLastError();

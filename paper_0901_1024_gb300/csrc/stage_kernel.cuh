@@ -6,8 +6,10 @@
 //      the tile in shared memory (coalesced loads);
 //   2. flux extraction (Alg. 3 of the paper): for every face node, u- from the
 //      tile, u+ from the tile when the neighbour is in it and from global
-//      memory otherwise (PEC ghost on walls), the upwind flux of Section 6
-//      scaled by Fscale/2, into a shared flux tile [6][E][4 Nfp];
+//      memory otherwise (PEC ghost on walls, zero on absorbing faces), the
+//      upwind flux of Section 6 scaled by Fscale/2 (with materials: by Fscale
+//      and the impedance coefficients of the face), into a shared flux tile
+//      [6][E][4 Nfp];
 //   3. local differentiation (Alg. 4): U_r, U_s, U_t = Dr U, Ds U, Dt U for
 //      three fields at a time, chain rule with the element's metric terms
 //      (Eq. dg-reference-matrices) and the curl (Eq. maxwells-claws),
@@ -109,6 +111,9 @@ __global__ void __launch_bounds__(StageDims<N>::T) stage_kernel(const StageArgs 
         if (code == 0u) {                       // perfectly conducting wall
 #pragma unroll
           for (int c = 0; c < 3; ++c) { uP[c] = -uM[c]; uP[c + 3] = uM[c + 3]; }
+        } else if (code == kAbsorbingCode) {    // characteristic absorbing: no incoming wave
+#pragma unroll
+          for (int c = 0; c < 6; ++c) uP[c] = 0.f;
         } else {
           const int k2 = __float_as_int(ge[28 + f]);
           const int i2 = __ldg(A.perm + (f * 24 + int(code) - 1) * Nfp + j);
@@ -128,16 +133,32 @@ __global__ void __launch_bounds__(StageDims<N>::T) stage_kernel(const StageArgs 
         const float ndE = nx * dEx + ny * dEy + nz * dEz;
         const float ndH = nx * dHx + ny * dHy + nz * dHz;
         const float al = A.alpha;
-        // E: -n x dH + alpha (n (n.dE) - dE);  H: n x dE + alpha (n (n.dH) - dH)
-        const float fl[6] = {
-            -(ny * dHz - nz * dHy) + al * (nx * ndE - dEx),
-            -(nz * dHx - nx * dHz) + al * (ny * ndE - dEy),
-            -(nx * dHy - ny * dHx) + al * (nz * ndE - dEz),
-            (ny * dEz - nz * dEy) + al * (nx * ndH - dHx),
-            (nz * dEx - nx * dEz) + al * (ny * ndH - dHy),
-            (nx * dEy - ny * dEx) + al * (nz * ndH - dHz)};
+        if (!A.mat) {
+          // E: -n x dH + alpha (n (n.dE) - dE);  H: n x dE + alpha (n (n.dH) - dH)
+          const float fl[6] = {
+              -(ny * dHz - nz * dHy) + al * (nx * ndE - dEx),
+              -(nz * dHx - nx * dHz) + al * (ny * ndE - dEy),
+              -(nx * dHy - ny * dHx) + al * (nz * ndE - dEz),
+              (ny * dEz - nz * dEy) + al * (nx * ndH - dHx),
+              (nz * dEx - nx * dEz) + al * (ny * ndH - dHy),
+              (nx * dEy - ny * dEx) + al * (nz * ndH - dHz)};
 #pragma unroll
-        for (int c = 0; c < 6; ++c) sf[(c * E + e) * FS + m] = sc * fl[c];
+          for (int c = 0; c < 6; ++c) sf[(c * E + e) * FS + m] = sc * fl[c];
+        } else {
+          // Section 6 with impedances: A_E (-n x dH) + alpha B_E (n (n.dE) - dE),
+          // A_H (n x dE) + alpha B_H (n (n.dH) - dH), the coefficients of face f
+          const float4 cf = __ldg(A.mat + size_t(k0 + e) * kMatVecs + 1 + f);
+          const float fs = 2.f * sc, bE = al * cf.y, bH = al * cf.w;
+          const float fl[6] = {
+              cf.x * -(ny * dHz - nz * dHy) + bE * (nx * ndE - dEx),
+              cf.x * -(nz * dHx - nx * dHz) + bE * (ny * ndE - dEy),
+              cf.x * -(nx * dHy - ny * dHx) + bE * (nz * ndE - dEz),
+              cf.z * (ny * dEz - nz * dEy) + bH * (nx * ndH - dHx),
+              cf.z * (nz * dEx - nx * dEz) + bH * (ny * ndH - dHy),
+              cf.z * (nx * dEy - ny * dEx) + bH * (nz * ndH - dHz)};
+#pragma unroll
+          for (int c = 0; c < 6; ++c) sf[(c * E + e) * FS + m] = fs * fl[c];
+        }
       }
     }
     __syncthreads();
@@ -244,7 +265,11 @@ __global__ void __launch_bounds__(StageDims<N>::T) stage_kernel(const StageArgs 
       const size_t base = (size_t(c) * K + k0) * Np;
       for (int idx = tid; idx < Ev * Np; idx += D::T) {
         const int ee = idx / Np, i = idx - ee * Np;
-        const float r = sf[(c * E + ee) * US + i];
+        float r = sf[(c * E + ee) * US + i];
+        if (A.mat) {                            // rhs_E / eps, rhs_H / mu
+          const float4 w = __ldg(A.mat + size_t(k0 + ee) * kMatVecs);
+          r *= c < 3 ? w.x : w.y;
+        }
         if (RK) {
           const float dtk = A.dt_elem ? __ldg(A.dt_elem + k0 + ee) : A.dt;
           const float rn = fmaf(A.a, A.res[base + idx], dtk * r);

@@ -59,8 +59,8 @@ template <int N> struct TtDims {
   static constexpr int CF = KG / 8;                   // first flux chunk
   static constexpr int ACOLS = tt_acols(N);           // tensor-memory columns per Op piece
   static constexpr int ACC0 = 2 * ACOLS;              // first accumulator column
-  static constexpr int THREADS = 512;                 // 4 epilogue + 12 producer warps
-  static constexpr int PRODUCERS = 384;
+  static constexpr int PRODUCERS = 384;               // a multiple of ROWS
+  static constexpr int THREADS = 128 + PRODUCERS;     // 4 epilogue warps + producer warps
   static constexpr int QR = PRODUCERS / ROWS;         // producers per X row
   static constexpr int CPT = (KCH + QR - 1) / QR;     // X chunks per producer
   static constexpr int ITEMS = (E * NF + PRODUCERS - 1) / PRODUCERS;   // flux items per producer
@@ -81,7 +81,7 @@ template <int N> struct TtDims {
   static constexpr int OFF_TAB = OFF_SC + 4 * ROWS * 4;      // face-node table (NF bytes)
   static constexpr int SMEM = OFF_TAB + ((NF + 15) & ~15);
   static_assert(NN % 16 == 0 && NN <= 256, "MMA N");
-  static_assert(PRODUCERS % ROWS == 0 && CPT * QR == KCH, "X chunk split");
+  static_assert(PRODUCERS % ROWS == 0 && PRODUCERS % 32 == 0 && CPT * QR >= KCH, "X chunk split");
   static_assert(ACC0 + 2 * NN <= 512, "tensor-memory budget");
   static_assert(ACOLS % 16 == 0, "operator columns are written 16 at a time");
   static_assert(Np <= 128 && NF < 128 && Np < 128 && E <= 32, "item encoding");
@@ -456,7 +456,10 @@ __global__ void __launch_bounds__(TtDims<N>::THREADS, 1) tt_stage_kernel(const S
       for (int q = 0; q < D::CPT; ++q) {
         const int ch = xq + D::QR * q;
         float v[8];
-        if (ch < D::CF) {                              // g^mu, nodes j0 .. j0 + 7
+        if (ch >= D::KCH) {                            // past the row (uneven split)
+#pragma unroll
+          for (int j = 0; j < 8; ++j) v[j] = 0.f;
+        } else if (ch < D::CF) {                       // g^mu, nodes j0 .. j0 + 7
           const int mu = ch / D::CG, j0 = (ch - mu * D::CG) * 8;
           const float ca = sgn * sg[(3 * mu + (o + 1) % 3) * E + xe];
           const float cb = -sgn * sg[(3 * mu + (o + 2) % 3) * E + xe];
@@ -495,6 +498,7 @@ __global__ void __launch_bounds__(TtDims<N>::THREADS, 1) tt_stage_kernel(const S
 #pragma unroll
       for (int q = 0; q < D::CPT; ++q) {
         const int ch = xq + D::QR * q;
+        if (ch >= D::KCH) break;
         uint32_t hi[4], lo[4];
 #pragma unroll
         for (int p = 0; p < 4; ++p) {

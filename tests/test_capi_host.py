@@ -148,3 +148,46 @@ def test_partition_order_errors(dg):
     assert lib.dg_partition_order(None, 20, ptr) == -1
     assert lib.dg_partition_order(mesh._h, 4, ptr) == 0
     assert sorted(perm) == list(range(mesh.K))
+
+
+def test_materials_and_boundary_host_side(dg):
+    """dg_set_materials / dg_set_boundary: validation, dt_cfl with materials
+    against the oracle, reset by NULL, and packing keeps each part's materials
+    (its dt_cfl is the smallest part's)."""
+    from paper_0901_1024_gb300 import DGError
+    verts, tets = kuhn_box_mesh(2, 0.15, 8)
+    m = dg.Mesh(verts, tets, 3)
+    om = oracle.build_mesh(verts, tets, 3)
+    vac = m.dt_cfl
+    rng = np.random.default_rng(5)
+    eps, mu = rng.uniform(0.5, 4.0, m.K), rng.uniform(0.5, 3.0, m.K)
+    m.set_materials(eps, mu)
+    want = oracle.maxwell.cfl_dt(om, 1.0, eps, mu)
+    assert abs(m.dt_cfl - want) < 1e-14 * want
+    for bad in (0.0, -1.0, float("nan"), float("inf")):
+        e2 = eps.copy()
+        e2[3] = bad
+        with pytest.raises(DGError) as ei:
+            m.set_materials(e2, mu)
+        assert ei.value.code == -1
+    assert abs(m.dt_cfl - want) < 1e-14 * want       # a rejected call changes nothing
+    m.set_materials(None, None)
+    assert m.dt_cfl == vac
+    m.set_materials(eps)                              # mu = 1
+    assert abs(m.dt_cfl - oracle.maxwell.cfl_dt(om, 1.0, eps, np.ones(m.K))) < 1e-14 * m.dt_cfl
+    kind = np.zeros((m.K, 4), np.int8)
+    kind[0, 0] = 2
+    with pytest.raises(DGError) as ei:
+        m.set_boundary(kind)
+    assert ei.value.code == -1
+    with pytest.raises(ValueError):
+        m.set_boundary(np.zeros((m.K, 3), np.int8))
+    kind[0, 0] = 1
+    m.set_boundary(kind)
+    m.set_boundary(None)
+    lib = dg.load()
+    assert lib.dg_set_materials(None, None, None) == -1
+    assert lib.dg_set_boundary(None, None) == -1
+    b = dg.Mesh(verts, tets, 3)
+    p = dg.Mesh.pack([m, b])
+    assert p.dt_cfl == min(m.dt_cfl, b.dt_cfl)

@@ -1,0 +1,138 @@
+"""GPU parity with materials (per-element eps, mu) and absorbing boundaries:
+the CUDA path through the C ABI against the FP64 oracle.  Tolerances as for
+the vacuum operator: 1e-5 (one RHS), 1e-4 (steps), 1e-6 (energy)."""
+import numpy as np
+import pytest
+
+import oracle
+from workloads import kuhn_box_mesh, random_fields
+
+pytestmark = pytest.mark.gpu
+
+RHS_TOL = 1e-5
+STEP_TOL = 1e-4
+
+
+@pytest.fixture(scope="module")
+def env():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_0901_1024_gb300 as dg
+    return torch, dg
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a, np.float64) - b) / np.linalg.norm(b))
+
+
+def _materials(K, seed):
+    rng = np.random.default_rng(seed)
+    eps = rng.uniform(0.5, 4.0, K)
+    mu = rng.uniform(0.5, 3.0, K)
+    bc = rng.integers(0, 2, (K, 4)).astype(np.int8)
+    return eps, mu, bc
+
+
+def _setup(dg, verts, tets, N, seed, with_eps=True, with_bc=True):
+    mesh, om = dg.Mesh(verts, tets, N), oracle.build_mesh(verts, tets, N)
+    eps, mu, bc = _materials(om.K, seed)
+    if not with_eps:
+        eps = mu = None
+    if not with_bc:
+        bc = None
+    mesh.set_materials(eps, mu)
+    mesh.set_boundary(bc)
+    return mesh, om, eps, mu, bc
+
+
+def _kinds(mesh):
+    _, kinds = mesh.trace_read()
+    return set(int(k) for k in kinds)
+
+
+@pytest.mark.parametrize("N", range(1, 10))
+@pytest.mark.parametrize("what", ["materials_and_absorbing", "absorbing_only"])
+def test_rhs_parity_materials(env, N, what):
+    """Random eps, mu per element and a random mix of perfect-conductor and
+    absorbing boundary faces; the tensor cores are asked for, the FP32 kernel
+    runs (K = 162 or 48: ragged last tile)."""
+    torch, dg = env
+    n = 3 if N <= 4 else 2
+    verts, tets = kuhn_box_mesh(n, 0.15, 60 + N)
+    mesh, om, eps, mu, bc = _setup(dg, verts, tets, N, N, with_eps=what != "absorbing_only")
+    u32 = random_fields(om.K, om.Np, 70 + N).astype(np.float32)
+    mesh.set_stage_impl(mesh.STAGE_TC)
+    mesh.trace_enable(4)
+    u = torch.from_numpy(u32).cuda()
+    out = torch.full_like(u, float("nan"))
+    mesh.rhs(u, out)
+    torch.cuda.synchronize()
+    assert _kinds(mesh) == {1}
+    want = oracle.rhs(om, u32.astype(np.float64), 1.0, eps, mu, bc)
+    got = out.cpu().numpy()
+    assert np.isfinite(got).all()
+    assert rel(got, want) < RHS_TOL
+
+
+@pytest.mark.parametrize("alpha", [1.0, 0.0])
+def test_step_parity_materials(env, alpha):
+    """20 LSERK4 steps with materials and absorbing faces, upwind and central."""
+    torch, dg = env
+    verts, tets = kuhn_box_mesh(2, 0.1, 3)
+    mesh, om, eps, mu, bc = _setup(dg, verts, tets, 3, 11)
+    mesh.set_flux(alpha)
+    u0 = random_fields(om.K, om.Np, 12).astype(np.float32)
+    dt = mesh.dt_cfl
+    assert dt == pytest.approx(oracle.maxwell.cfl_dt(om, 1.0, eps, mu), rel=1e-14)
+    u = torch.from_numpy(u0).cuda()
+    res = torch.zeros_like(u)
+    mesh.step(u, res, dt, 20)
+    torch.cuda.synchronize()
+    ue, _ = oracle.lserk4_run(om, u0.astype(np.float64), dt, 20, alpha=alpha, eps=eps, mu=mu, bc=bc)
+    assert rel(u.cpu().numpy(), ue) < STEP_TOL
+
+
+@pytest.mark.parametrize("N", [2, 6, 7])
+def test_energy_parity_materials(env, N):
+    """Energy weighted by eps (E) and mu (H): the row-staged kernel (N <= 6),
+    the warp-per-element kernel (N = 7) and the allocation-free entry point."""
+    torch, dg = env
+    verts, tets = kuhn_box_mesh(3, 0.15, 2)
+    mesh, om, eps, mu, _ = _setup(dg, verts, tets, N, 21, with_bc=False)
+    u32 = random_fields(om.K, om.Np, 22).astype(np.float32)
+    u = torch.from_numpy(u32).cuda()
+    want = oracle.energy(om, u32.astype(np.float64), eps, mu)
+    assert abs(mesh.energy(u) - want) < 1e-6 * want
+    out = torch.zeros(1, dtype=torch.float64, device="cuda")
+    mesh.energy_noalloc(u, out)
+    torch.cuda.synchronize()
+    assert abs(float(out.item()) - want) < 1e-6 * want
+
+
+def test_packed_mesh_with_materials_matches_its_parts(env):
+    """dg_mesh_pack of a mesh with materials and absorbing faces and a mesh
+    given eps = mu = 1 explicitly (the pack fills 1 for parts without
+    materials): a packed stage is bit for bit each part's own stage."""
+    torch, dg = env
+    va, ta = kuhn_box_mesh(2, 0.1, 1)
+    vb, tb = kuhn_box_mesh(2, 0.15, 2)
+    a, _, _, _, _ = _setup(dg, va, ta, 3, 31)
+    b = dg.Mesh(vb, tb, 3)
+    b.set_materials(np.ones(b.K), np.ones(b.K))
+    p = dg.Mesh.pack([a, b])
+    u0 = random_fields(p.K, p.Np, 32).astype(np.float32)
+    dt = min(a.dt_cfl, b.dt_cfl)
+    outs = []
+    for m, sl in ((a, slice(0, a.K)), (b, slice(a.K, p.K))):
+        u = torch.from_numpy(np.ascontiguousarray(u0[:, sl])).cuda()
+        w, r = torch.empty_like(u), torch.zeros_like(u)
+        m.rk_stage(u, w, r, 1, dt)
+        outs.append(w.cpu().numpy())
+    u = torch.from_numpy(u0).cuda()
+    w, r = torch.empty_like(u), torch.zeros_like(u)
+    p.rk_stage(u, w, r, 1, dt)
+    torch.cuda.synchronize()
+    assert np.array_equal(w.cpu().numpy(), np.concatenate(outs, axis=1))
