@@ -151,8 +151,9 @@ int dg_set_flux(dg_mesh* mesh, double alpha);
  *   E: 1/(Z- + Z+) n x ( Z+ [H] - alpha n x [E]),
  *   H: 1/(Y- + Y+) n x (-Y+ [E] - alpha n x [H]),   [u] = u+ - u-;
  * dg_energy weights E by eps and H by mu, and dt_cfl scales with
- * min sqrt(eps mu).  A mesh with materials (or absorbing faces) runs the FP32
- * CUDA-core stage.  Host only.  Errors: DG_ERR_ARG (NULL mesh, a value not
+ * min sqrt(eps mu).  Every stage implementation supports materials and
+ * absorbing faces (the tensor-core kernels through a separate instantiation,
+ * so vacuum meshes run unchanged code).  Host only.  Errors: DG_ERR_ARG (NULL mesh, a value not
  * finite or <= 0), DG_ERR_OOM. */
 int dg_set_materials(dg_mesh* mesh, const double* eps, const double* mu);
 

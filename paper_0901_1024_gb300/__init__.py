@@ -108,8 +108,8 @@ class Mesh:
 
     def set_materials(self, eps=None, mu=None):
         """Per-element permittivity and permeability (K values > 0 each; None: 1).
-        The stage then uses the impedance-weighted upwind flux, dt_cfl and the
-        energy follow the materials, and the FP32 CUDA-core stage runs."""
+        The stage then uses the impedance-weighted upwind flux; dt_cfl and the
+        energy follow the materials."""
         e = None if eps is None else np.ascontiguousarray(eps, np.float64)
         m = None if mu is None else np.ascontiguousarray(mu, np.float64)
         for a in (e, m):

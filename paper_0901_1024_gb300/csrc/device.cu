@@ -312,6 +312,7 @@ struct DeviceState {
   int egrid = 0;
   void* tcB = nullptr;          // tensor-core B pieces (orders <= kTcMaxOrder)
   float4* mat = nullptr;        // material records (meshes with materials), in the arena
+  bool absorbing = false;       // some boundary face is absorbing
   float* tcgeo = nullptr;       // word-major geometry for the tensor-core stage
   int tc_geo_stride = 0;
   float tc_inv_bscale = 1.f;
@@ -590,6 +591,7 @@ int ensure_device(dg_mesh* m, std::string& err) {
     for (int f = 0; f < 4; ++f) {
       const int c = m->nbr_code[4 * k + f];
       const bool absorbing = c < 0 && !m->bc.empty() && m->bc[4 * k + f] == DG_BC_ABSORBING;
+      d->absorbing = d->absorbing || absorbing;
       codes |= (absorbing ? dgdev::kAbsorbingCode : static_cast<uint32_t>(c + 1)) << (8 * f);
       for (int dd = 0; dd < 3; ++dd)
         g[12 + 4 * f + dd] = static_cast<float>(m->normals[(dd * K + k) * 4 + f]);
@@ -611,8 +613,8 @@ int ensure_device(dg_mesh* m, std::string& err) {
         const int64_t k2 = m->nbr_code[4 * k + f] < 0 ? k : m->nbr_elem[4 * k + f];
         const double zp = std::sqrt(m->mu[k2] / m->eps[k2]), ym = 1.0 / zm, yp = 1.0 / zp;
         mr[k * dgdev::kMatVecs + 1 + f] =
-            make_float4(static_cast<float>(zp / (zm + zp)), static_cast<float>(1.0 / (zm + zp)),
-                        static_cast<float>(yp / (ym + yp)), static_cast<float>(1.0 / (ym + yp)));
+            make_float4(static_cast<float>(zp), static_cast<float>(1.0 / (zm + zp)),
+                        static_cast<float>(yp), static_cast<float>(1.0 / (ym + yp)));
       }
     }
   }
@@ -656,8 +658,6 @@ int ensure_device(dg_mesh* m, std::string& err) {
 // field chunk 16-byte aligned: (K * Np) % 4 == 0 and 16-byte aligned buffers.
 static bool use_tc(const dg_mesh* m, std::initializer_list<const void*> bufs) {
   if (m->stage_impl == DG_STAGE_FP32 || m->N > dgdev::kTcMaxOrder) return false;
-  // materials and absorbing faces are handled by the FP32 kernel only
-  if (dg::has_materials_or_absorbing(m)) return false;
   // at N = 1 (Np = 4) the FP32 kernel is faster unless tensor cores are asked for
   if (m->stage_impl == DG_STAGE_AUTO && m->N == 1) return false;
   if ((m->K * m->ops.Np) % 4 != 0) return false;
@@ -676,6 +676,7 @@ static dgdev::StageArgs stage_args(dg_mesh* m, bool tc) {
   a.status = d->status;
   a.geo = d->geo;
   a.mat = d->mat;
+  a.absorbing = d->absorbing ? 1 : 0;
   a.D4 = d->D4;
   a.LIFT4 = d->LIFT4;
   a.fmask = d->fmask;

@@ -19,11 +19,12 @@ constexpr int kGeoWords = 32;
 constexpr unsigned kAbsorbingCode = 0xFFu;
 // Optional material record, 5 float4 per tetrahedron (meshes with materials):
 //   [0]      1/eps, 1/mu, eps, mu
-//   [1 + f]  A_E, B_E, A_H, B_H of face f: the flux of Section 6 is
-//            A_E (-n x dH) + alpha B_E (n (n.dE) - dE) for E and
-//            A_H ( n x dE) + alpha B_H (n (n.dH) - dH) for H (d = u- - u+), with
-//            A_E = Z+/(Z- + Z+), B_E = 1/(Z- + Z+), A_H = Y+/(Y- + Y+),
-//            B_H = 1/(Y- + Y+); 1/2 each in vacuum.
+//   [1 + f]  Z+, B_E, Y+, B_H of face f: the flux of Section 6 is
+//            B_E (Z+ (-n x dH) + alpha (n (n.dE) - dE)) for E and
+//            B_H (Y+ ( n x dE) + alpha (n (n.dH) - dH)) for H (d = u- - u+),
+//            B_E = 1/(Z- + Z+), B_H = 1/(Y- + Y+), Z+ / Y+ the neighbour's
+//            impedance / admittance (the element's own on boundary faces);
+//            vacuum: 1, 1/2, 1, 1/2.
 constexpr int kMatVecs = 5;
 
 // Stage-kernel tiling per order N: tile of E tetrahedra, G row groups (threads
@@ -59,6 +60,7 @@ struct StageArgs {
                             // K-major shared-memory layout, orders 5, 6 as tensor-memory rows
   float tc_inv_bscale;      // 1 / (power-of-two scale applied to [Dr Ds Dt LIFT])
   int* status;              // set to 1 if an MMA completion wait timed out
+  int absorbing;            // 1 if any boundary face is absorbing (code kAbsorbingCode)
 };
 
 // Tensor-core stage: elements per tile.  Orders <= 4: 6 * 20 = 120 of the 128

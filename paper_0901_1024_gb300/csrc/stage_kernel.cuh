@@ -145,19 +145,19 @@ __global__ void __launch_bounds__(StageDims<N>::T) stage_kernel(const StageArgs 
 #pragma unroll
           for (int c = 0; c < 6; ++c) sf[(c * E + e) * FS + m] = sc * fl[c];
         } else {
-          // Section 6 with impedances: A_E (-n x dH) + alpha B_E (n (n.dE) - dE),
-          // A_H (n x dE) + alpha B_H (n (n.dH) - dH), the coefficients of face f
+          // Section 6 with impedances: B_E (Z+ (-n x dH) + alpha (n (n.dE) - dE)),
+          // B_H (Y+ (n x dE) + alpha (n (n.dH) - dH)), the coefficients of face f
           const float4 cf = __ldg(A.mat + size_t(k0 + e) * kMatVecs + 1 + f);
-          const float fs = 2.f * sc, bE = al * cf.y, bH = al * cf.w;
+          const float fs = 2.f * sc, sE = fs * cf.y, sH = fs * cf.w;
           const float fl[6] = {
-              cf.x * -(ny * dHz - nz * dHy) + bE * (nx * ndE - dEx),
-              cf.x * -(nz * dHx - nx * dHz) + bE * (ny * ndE - dEy),
-              cf.x * -(nx * dHy - ny * dHx) + bE * (nz * ndE - dEz),
-              cf.z * (ny * dEz - nz * dEy) + bH * (nx * ndH - dHx),
-              cf.z * (nz * dEx - nx * dEz) + bH * (ny * ndH - dHy),
-              cf.z * (nx * dEy - ny * dEx) + bH * (nz * ndH - dHz)};
+              cf.x * -(ny * dHz - nz * dHy) + al * (nx * ndE - dEx),
+              cf.x * -(nz * dHx - nx * dHz) + al * (ny * ndE - dEy),
+              cf.x * -(nx * dHy - ny * dHx) + al * (nz * ndE - dEz),
+              cf.z * (ny * dEz - nz * dEy) + al * (nx * ndH - dHx),
+              cf.z * (nz * dEx - nx * dEz) + al * (ny * ndH - dHy),
+              cf.z * (nx * dEy - ny * dEx) + al * (nz * ndH - dHz)};
 #pragma unroll
-          for (int c = 0; c < 6; ++c) sf[(c * E + e) * FS + m] = fs * fl[c];
+          for (int c = 0; c < 6; ++c) sf[(c * E + e) * FS + m] = (c < 3 ? sE : sH) * fl[c];
         }
       }
     }

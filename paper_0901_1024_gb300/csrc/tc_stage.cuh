@@ -297,7 +297,9 @@ __device__ __forceinline__ void build_flux_half(const FRow& g, int role) {
   split_store_fn<NPH, P0>([&](int p) { return __fmul2_rn(w[p - P0], f2(s)); }, g.a_hi, g.a_lo);
 }
 
-template <int N, bool RK>
+// EXT: meshes with materials (A.mat) or absorbing faces; the vacuum instantiation
+// has none of that arithmetic.
+template <int N, bool RK, bool EXT>
 __global__ void __launch_bounds__(TcDims<N>::THREADS, 1) tc_stage_kernel(const StageArgs A) {
   using D = TcDims<N>;
   constexpr int E = D::E, Np = D::Np, Nfp = D::Nfp, NF = D::NF, FSTR = D::FSTR;
@@ -397,7 +399,11 @@ __global__ void __launch_bounds__(TcDims<N>::THREADS, 1) tc_stage_kernel(const S
         tc::tmem_ld_wait();
         tc::fence_before_sync();
         if (row < D::ROWS && re < Ev) {
-          const float inv = A.tc_inv_bscale / sScale[(t & 3) * 128 + row];
+          float inv = A.tc_inv_bscale / sScale[(t & 3) * 128 + row];
+          if (EXT && A.mat) {                  // rhs_E / eps, rhs_H / mu
+            const float4 w = __ldg(A.mat + size_t(k0 + re) * kMatVecs);
+            inv *= rc < 3 ? w.x : w.y;
+          }
           const float dte = RK && A.dt_elem ? __ldg(A.dt_elem + k0 + re) : A.dt;
           float* pr = sr + (rc * E + re) * Np;
           float* pu = su + (rc * E + re) * Np;
@@ -523,14 +529,19 @@ __global__ void __launch_bounds__(TcDims<N>::THREADS, 1) tc_stage_kernel(const S
         const int k2 = __float_as_int(sg[(26 + f) * E + ec]);
         const int i2 = nodes[ec * NF + m];
         const int e2 = k2 - k0;
-        const uint32_t kind = !ok ? 0u : code == 0u ? 1u : unsigned(e2) < unsigned(Ev) ? 2u : 3u;
+        // absorbing faces (EXT): a wall whose exterior state is zero
+        const bool absorbing = EXT && code == kAbsorbingCode;
+        const uint32_t kind = !ok ? 0u
+                              : (code == 0u || absorbing) ? 1u
+                              : unsigned(e2) < unsigned(Ev) ? 2u : 3u;
         if (kind == 3u) {
           const float* src = A.u_in + size_t(k2) * Np + i2;
 #pragma unroll
           for (int c = 0; c < 6; ++c)
             tc::cp_async4(F + (c * E + e) * FSTR + m, src + size_t(c) * K * Np);
         }
-        info[q] = kind | uint32_t(kind == 2u ? e2 * Np + i2 : ec * Np + idM) << 2;
+        info[q] = kind | uint32_t(kind == 2u ? e2 * Np + i2 : ec * Np + idM) << 2 |
+                  (absorbing ? 0x80000000u : 0u);
       }
       tc::cp_async_commit();
       tc::cp_async_wait_all();
@@ -540,6 +551,7 @@ __global__ void __launch_bounds__(TcDims<N>::THREADS, 1) tc_stage_kernel(const S
       {
         constexpr int NQ = (D::ITEMS + 1) & ~1;
         float uM[NQ][6], up[NQ][6], nv[NQ][4];
+        float4 cf[EXT ? NQ : 1];          // EXT: Z+, B_E, Y+, B_H of the item's face
         uint32_t kinds[NQ];
 #pragma unroll
         for (int q = 0; q < NQ; ++q) {
@@ -549,21 +561,27 @@ __global__ void __launch_bounds__(TcDims<N>::THREADS, 1) tc_stage_kernel(const S
             for (int c = 0; c < 6; ++c) uM[q][c] = up[q][c] = 0.f;
 #pragma unroll
             for (int w = 0; w < 4; ++w) nv[q][w] = 0.f;
+            if constexpr (EXT) cf[q] = make_float4(1.f, 0.5f, 1.f, 0.5f);
             continue;
           }
           const uint32_t it = item[q], kind = info[q] & 3u;
           kinds[q] = kind;
           const int e = kind ? int(it & 31) : 0, m = (it >> 5) & 127, f = (it >> 12) & 3;
           const int idM = (it >> 14) & 63;
-          const float* pp = kind == 3u ? F + e * FSTR + m : su + (info[q] >> 2);
+          const float* pp = kind == 3u ? F + e * FSTR + m
+                                       : su + (EXT ? (info[q] >> 2) & 0x1FFFFFFFu : info[q] >> 2);
           const int ps = kind == 3u ? E * FSTR : E * Np;
+          const bool zero_ext = EXT && (info[q] >> 31);          // absorbing: u+ = 0
 #pragma unroll
           for (int c = 0; c < 6; ++c) {
             uM[q][c] = su[c * E * Np + e * Np + idM];
-            up[q][c] = pp[c * ps];
+            up[q][c] = zero_ext ? 0.f : pp[c * ps];
           }
 #pragma unroll
           for (int w = 0; w < 4; ++w) nv[q][w] = sg[(10 + 4 * f + w) * E + e];
+          if constexpr (EXT)
+            cf[q] = A.mat && kind ? __ldg(A.mat + size_t(k0 + e) * kMatVecs + 1 + f)
+                                  : make_float4(1.f, 0.5f, 1.f, 0.5f);
         }
         const float2 m1 = f2(-1.f), nal = f2(-A.alpha), al = f2(A.alpha);
 #pragma unroll
@@ -580,19 +598,36 @@ __global__ void __launch_bounds__(TcDims<N>::THREADS, 1) tc_stage_kernel(const S
           const float2 nx = make_float2(nv[q][0], nv[r][0]), ny = make_float2(nv[q][1], nv[r][1]);
           const float2 nz = make_float2(nv[q][2], nv[r][2]);
           const float2 sc = __fmul2_rn(f2(0.5f), make_float2(nv[q][3], nv[r][3]));
+          // EXT: B_E (Z+ (-n x dH) + ...), B_H (Y+ (n x dE) + ...) with Fscale
+          float2 zp = f2(1.f), yp = f2(1.f), scE = sc, scH = sc;
+          if constexpr (EXT) {
+            zp = make_float2(cf[q].x, cf[r].x);
+            yp = make_float2(cf[q].z, cf[r].z);
+            scE = __fmul2_rn(make_float2(cf[q].y, cf[r].y), make_float2(nv[q][3], nv[r][3]));
+            scH = __fmul2_rn(make_float2(cf[q].w, cf[r].w), make_float2(nv[q][3], nv[r][3]));
+          }
           const float2 mx = __fmul2_rn(m1, nx), my = __fmul2_rn(m1, ny), mz = __fmul2_rn(m1, nz);
           const float2 aE = __fmul2_rn(al, __ffma2_rn(nz, dEz, __ffma2_rn(ny, dEy, __fmul2_rn(nx, dEx))));
           const float2 aH = __fmul2_rn(al, __ffma2_rn(nz, dHz, __ffma2_rn(ny, dHy, __fmul2_rn(nx, dHx))));
           // fluxE = -n x dH + alpha (n (n.dE) - dE), fluxH = n x dE + alpha (n (n.dH) - dH)
           float2 fl[6];
-          fl[0] = __ffma2_rn(nal, dEx, __ffma2_rn(nx, aE, __ffma2_rn(my, dHz, __fmul2_rn(nz, dHy))));
-          fl[1] = __ffma2_rn(nal, dEy, __ffma2_rn(ny, aE, __ffma2_rn(mz, dHx, __fmul2_rn(nx, dHz))));
-          fl[2] = __ffma2_rn(nal, dEz, __ffma2_rn(nz, aE, __ffma2_rn(mx, dHy, __fmul2_rn(ny, dHx))));
-          fl[3] = __ffma2_rn(nal, dHx, __ffma2_rn(nx, aH, __ffma2_rn(mz, dEy, __fmul2_rn(ny, dEz))));
-          fl[4] = __ffma2_rn(nal, dHy, __ffma2_rn(ny, aH, __ffma2_rn(mx, dEz, __fmul2_rn(nz, dEx))));
-          fl[5] = __ffma2_rn(nal, dHz, __ffma2_rn(nz, aH, __ffma2_rn(my, dEx, __fmul2_rn(nx, dEy))));
+          if constexpr (!EXT) {
+            fl[0] = __ffma2_rn(nal, dEx, __ffma2_rn(nx, aE, __ffma2_rn(my, dHz, __fmul2_rn(nz, dHy))));
+            fl[1] = __ffma2_rn(nal, dEy, __ffma2_rn(ny, aE, __ffma2_rn(mz, dHx, __fmul2_rn(nx, dHz))));
+            fl[2] = __ffma2_rn(nal, dEz, __ffma2_rn(nz, aE, __ffma2_rn(mx, dHy, __fmul2_rn(ny, dHx))));
+            fl[3] = __ffma2_rn(nal, dHx, __ffma2_rn(nx, aH, __ffma2_rn(mz, dEy, __fmul2_rn(ny, dEz))));
+            fl[4] = __ffma2_rn(nal, dHy, __ffma2_rn(ny, aH, __ffma2_rn(mx, dEz, __fmul2_rn(nz, dEx))));
+            fl[5] = __ffma2_rn(nal, dHz, __ffma2_rn(nz, aH, __ffma2_rn(my, dEx, __fmul2_rn(nx, dEy))));
+          } else {
+            fl[0] = __ffma2_rn(nal, dEx, __ffma2_rn(nx, aE, __fmul2_rn(zp, __ffma2_rn(my, dHz, __fmul2_rn(nz, dHy)))));
+            fl[1] = __ffma2_rn(nal, dEy, __ffma2_rn(ny, aE, __fmul2_rn(zp, __ffma2_rn(mz, dHx, __fmul2_rn(nx, dHz)))));
+            fl[2] = __ffma2_rn(nal, dEz, __ffma2_rn(nz, aE, __fmul2_rn(zp, __ffma2_rn(mx, dHy, __fmul2_rn(ny, dHx)))));
+            fl[3] = __ffma2_rn(nal, dHx, __ffma2_rn(nx, aH, __fmul2_rn(yp, __ffma2_rn(mz, dEy, __fmul2_rn(ny, dEz)))));
+            fl[4] = __ffma2_rn(nal, dHy, __ffma2_rn(ny, aH, __fmul2_rn(yp, __ffma2_rn(mx, dEz, __fmul2_rn(nz, dEx)))));
+            fl[5] = __ffma2_rn(nal, dHz, __ffma2_rn(nz, aH, __fmul2_rn(yp, __ffma2_rn(my, dEx, __fmul2_rn(nx, dEy)))));
+          }
 #pragma unroll
-          for (int c = 0; c < 6; ++c) fl[c] = __fmul2_rn(sc, fl[c]);
+          for (int c = 0; c < 6; ++c) fl[c] = __fmul2_rn(c < 3 ? scE : scH, fl[c]);
           if (kinds[q]) {
             float* fr = F + int(item[q] & 31) * FSTR + int((item[q] >> 5) & 127);
 #pragma unroll
@@ -649,7 +684,9 @@ cudaError_t launch_tc_stage_n(bool rk, const StageArgs& a, int num_sms, cudaStre
   cudaError_t err = cudaGetDevice(&dev);
   if (err != cudaSuccess) return err;
   dev &= 15;
-  auto kern = rk ? tc_stage_kernel<N, true> : tc_stage_kernel<N, false>;
+  const bool ext = a.mat || a.absorbing;
+  auto kern = rk ? (ext ? tc_stage_kernel<N, true, true> : tc_stage_kernel<N, true, false>)
+                 : (ext ? tc_stage_kernel<N, false, true> : tc_stage_kernel<N, false, false>);
   // at least 120 KB of shared memory: never two CTAs (each takes all 512
   // tensor-memory columns) on one SM
   constexpr int smem = D::SMEM > 120 * 1024 ? D::SMEM : 120 * 1024;

@@ -131,7 +131,9 @@ __device__ __forceinline__ void lds8(const float* p, float* v) {
   v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
 }
 
-template <int N, bool RK>
+// EXT: meshes with materials (A.mat) or absorbing faces; the vacuum instantiation
+// has none of that arithmetic.
+template <int N, bool RK, bool EXT>
 __global__ void __launch_bounds__(TtDims<N>::THREADS, 1) tt_stage_kernel(const StageArgs A) {
   using D = TtDims<N>;
   constexpr int E = D::E, Np = D::Np, Nfp = D::Nfp, NF = D::NF, FSTR = D::FSTR, ROWS = D::ROWS;
@@ -390,14 +392,19 @@ __global__ void __launch_bounds__(TtDims<N>::THREADS, 1) tt_stage_kernel(const S
         const int k2 = __float_as_int(sg[(26 + f) * E + ec]);
         const int i2 = nodes[ec * NF + m];
         const int e2 = k2 - k0;
-        const uint32_t kind = !ok ? 0u : code == 0u ? 1u : unsigned(e2) < unsigned(Ev) ? 2u : 3u;
+        // absorbing faces (EXT): a wall whose exterior state is zero
+        const bool absorbing = EXT && code == kAbsorbingCode;
+        const uint32_t kind = !ok ? 0u
+                              : (code == 0u || absorbing) ? 1u
+                              : unsigned(e2) < unsigned(Ev) ? 2u : 3u;
         if (kind == 3u) {
           const float* src = A.u_in + size_t(k2) * Np + i2;
 #pragma unroll
           for (int c = 0; c < 6; ++c)
             tc::cp_async4(F + (c * E + e) * FSTR + m, src + size_t(c) * K * Np);
         }
-        info[q] = kind | uint32_t(kind == 2u ? e2 * Np + i2 : ec * Np + idM) << 2;
+        info[q] = kind | uint32_t(kind == 2u ? e2 * Np + i2 : ec * Np + idM) << 2 |
+                  (absorbing ? 0x80000000u : 0u);
       }
       tc::cp_async_commit();
       tc::cp_async_wait_all();
@@ -405,20 +412,26 @@ __global__ void __launch_bounds__(TtDims<N>::THREADS, 1) tt_stage_kernel(const S
       // all operands loaded before any store into the flux buffer
       {
         float uM[D::ITEMS][6], up[D::ITEMS][6], nv[D::ITEMS][4];
+        float4 cf[EXT ? D::ITEMS : 1];        // EXT: Z+, B_E, Y+, B_H of the item's face
 #pragma unroll
         for (int q = 0; q < D::ITEMS; ++q) {
           const uint32_t it = item[q], kind = info[q] & 3u;
           const int e = kind ? int(it & 31) : 0, m = (it >> 5) & 127, f = (it >> 12) & 3;
           const int idM = (it >> 14) & 127;
-          const float* pp = kind == 3u ? F + e * FSTR + m : su + (info[q] >> 2);
+          const float* pp = kind == 3u ? F + e * FSTR + m
+                                       : su + (EXT ? (info[q] >> 2) & 0x1FFFFFFFu : info[q] >> 2);
           const int ps = kind == 3u ? E * FSTR : E * Np;
+          const bool zero_ext = EXT && (info[q] >> 31);          // absorbing: u+ = 0
 #pragma unroll
           for (int c = 0; c < 6; ++c) {
             uM[q][c] = su[c * E * Np + e * Np + idM];
-            up[q][c] = pp[c * ps];
+            up[q][c] = zero_ext ? 0.f : pp[c * ps];
           }
 #pragma unroll
           for (int w = 0; w < 4; ++w) nv[q][w] = sg[(10 + 4 * f + w) * E + e];
+          if constexpr (EXT)
+            cf[q] = A.mat && kind ? __ldg(A.mat + size_t(k0 + e) * kMatVecs + 1 + f)
+                                  : make_float4(1.f, 0.5f, 1.f, 0.5f);
         }
 #pragma unroll
         for (int q = 0; q < D::ITEMS; ++q) {
@@ -434,17 +447,25 @@ __global__ void __launch_bounds__(TtDims<N>::THREADS, 1) tt_stage_kernel(const S
           const float al = A.alpha;
           const float aE = al * fmaf(nz, dEz, fmaf(ny, dEy, nx * dEx));
           const float aH = al * fmaf(nz, dHz, fmaf(ny, dHy, nx * dHx));
-          // fluxE = -n x dH + alpha (n (n.dE) - dE), fluxH = n x dE + alpha (n (n.dH) - dH)
+          // fluxE = -n x dH + alpha (n (n.dE) - dE), fluxH = n x dE + alpha (n (n.dH) - dH);
+          // EXT: B_E (Z+ (-n x dH) + ...), B_H (Y+ (n x dE) + ...) with Fscale
+          float zp = 1.f, yp = 1.f, scE = sc, scH = sc;
+          if constexpr (EXT) {
+            zp = cf[q].x;
+            yp = cf[q].z;
+            scE = cf[q].y * nv[q][3];
+            scH = cf[q].w * nv[q][3];
+          }
           float fl[6];
-          fl[0] = fmaf(-al, dEx, fmaf(nx, aE, fmaf(-ny, dHz, nz * dHy)));
-          fl[1] = fmaf(-al, dEy, fmaf(ny, aE, fmaf(-nz, dHx, nx * dHz)));
-          fl[2] = fmaf(-al, dEz, fmaf(nz, aE, fmaf(-nx, dHy, ny * dHx)));
-          fl[3] = fmaf(-al, dHx, fmaf(nx, aH, fmaf(-nz, dEy, ny * dEz)));
-          fl[4] = fmaf(-al, dHy, fmaf(ny, aH, fmaf(-nx, dEz, nz * dEx)));
-          fl[5] = fmaf(-al, dHz, fmaf(nz, aH, fmaf(-ny, dEx, nx * dEy)));
+          fl[0] = fmaf(-al, dEx, fmaf(nx, aE, zp * fmaf(-ny, dHz, nz * dHy)));
+          fl[1] = fmaf(-al, dEy, fmaf(ny, aE, zp * fmaf(-nz, dHx, nx * dHz)));
+          fl[2] = fmaf(-al, dEz, fmaf(nz, aE, zp * fmaf(-nx, dHy, ny * dHx)));
+          fl[3] = fmaf(-al, dHx, fmaf(nx, aH, yp * fmaf(-nz, dEy, ny * dEz)));
+          fl[4] = fmaf(-al, dHy, fmaf(ny, aH, yp * fmaf(-nx, dEz, nz * dEx)));
+          fl[5] = fmaf(-al, dHz, fmaf(nz, aH, yp * fmaf(-ny, dEx, nx * dEy)));
           float* fr = F + int(item[q] & 31) * FSTR + int((item[q] >> 5) & 127);
 #pragma unroll
-          for (int c = 0; c < 6; ++c) fr[c * E * FSTR] = sc * fl[c];
+          for (int c = 0; c < 6; ++c) fr[c * E * FSTR] = (c < 3 ? scE : scH) * fl[c];
         }
       }
       named_sync(2, D::PRODUCERS);                     // the flux buffer is complete
@@ -491,8 +512,16 @@ __global__ void __launch_bounds__(TtDims<N>::THREADS, 1) tt_stage_kernel(const S
 #pragma unroll
       for (int q = 0; q < D::QR; ++q) rmax = fmaxf(rmax, sBound[q * ROWS + xn]);
       const float s = row_scale(rmax);
-      // column factor of the accumulator: 1 / (Op scale x row scale), a power of two
-      if (xq == 0) sScale[(t & 3) * ROWS + xn] = A.tc_inv_bscale / s;
+      // column factor of the accumulator: 1 / (Op scale x row scale), a power of
+      // two (EXT with materials: times 1/eps or 1/mu of the row's element)
+      if (xq == 0) {
+        float fac = A.tc_inv_bscale / s;
+        if (EXT && A.mat && live) {
+          const float4 w = __ldg(A.mat + size_t(k0 + xe) * kMatVecs);
+          fac *= xc < 3 ? w.x : w.y;
+        }
+        sScale[(t & 3) * ROWS + xn] = fac;
+      }
       // the single X buffer is free once the MMAs of tile t-1 have completed
       if (t >= 1) wait_or_flag(&s_mma_done[(t - 1) & 1], ((t - 1) >> 1) & 1, A.status);
 #pragma unroll
@@ -528,7 +557,9 @@ cudaError_t launch_tt_stage_n(bool rk, const StageArgs& a, int num_sms, cudaStre
   cudaError_t err = cudaGetDevice(&dev);
   if (err != cudaSuccess) return err;
   dev &= 15;
-  auto kern = rk ? tt_stage_kernel<N, true> : tt_stage_kernel<N, false>;
+  const bool ext = a.mat || a.absorbing;
+  auto kern = rk ? (ext ? tt_stage_kernel<N, true, true> : tt_stage_kernel<N, true, false>)
+                 : (ext ? tt_stage_kernel<N, false, true> : tt_stage_kernel<N, false, false>);
   // at least 120 KB of shared memory: never two CTAs (each takes all 512
   // tensor-memory columns) on one SM
   constexpr int smem = D::SMEM > 120 * 1024 ? D::SMEM : 120 * 1024;

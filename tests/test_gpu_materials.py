@@ -53,24 +53,33 @@ def _kinds(mesh):
     return set(int(k) for k in kinds)
 
 
+FP32, TC = 1, 2
+
+
 @pytest.mark.parametrize("N", range(1, 10))
+@pytest.mark.parametrize("impl", [FP32, TC])
 @pytest.mark.parametrize("what", ["materials_and_absorbing", "absorbing_only"])
-def test_rhs_parity_materials(env, N, what):
+def test_rhs_parity_materials(env, N, impl, what):
     """Random eps, mu per element and a random mix of perfect-conductor and
-    absorbing boundary faces; the tensor cores are asked for, the FP32 kernel
-    runs (K = 162 or 48: ragged last tile)."""
+    absorbing boundary faces on both stage implementations (the tensor-core
+    request runs the tensor cores up to N = 6 and the FP32 kernel above);
+    K = 162 (156 for the order <= 4 tensor cores, whose bulk copies need
+    K Np % 4 == 0): ragged last tiles of 20 and of 8 elements."""
     torch, dg = env
-    n = 3 if N <= 4 else 2
-    verts, tets = kuhn_box_mesh(n, 0.15, 60 + N)
+    verts, tets = kuhn_box_mesh(3, 0.15, 60 + N)
+    if impl == TC and N <= 4:
+        tets = tets[:156]
     mesh, om, eps, mu, bc = _setup(dg, verts, tets, N, N, with_eps=what != "absorbing_only")
     u32 = random_fields(om.K, om.Np, 70 + N).astype(np.float32)
-    mesh.set_stage_impl(mesh.STAGE_TC)
+    u32[:, ::5] *= 1e-4                                 # rows of different scales
+    mesh.set_stage_impl(impl)
     mesh.trace_enable(4)
     u = torch.from_numpy(u32).cuda()
     out = torch.full_like(u, float("nan"))
     mesh.rhs(u, out)
     torch.cuda.synchronize()
-    assert _kinds(mesh) == {1}
+    tc_ran = impl == TC and N <= 6 and (om.K * om.Np) % 4 == 0
+    assert _kinds(mesh) == ({5} if tc_ran else {1})
     want = oracle.rhs(om, u32.astype(np.float64), 1.0, eps, mu, bc)
     got = out.cpu().numpy()
     assert np.isfinite(got).all()
@@ -78,21 +87,46 @@ def test_rhs_parity_materials(env, N, what):
 
 
 @pytest.mark.parametrize("alpha", [1.0, 0.0])
-def test_step_parity_materials(env, alpha):
+@pytest.mark.parametrize("impl,N", [(FP32, 3), (TC, 3), (TC, 6)])
+def test_step_parity_materials(env, alpha, impl, N):
     """20 LSERK4 steps with materials and absorbing faces, upwind and central."""
     torch, dg = env
     verts, tets = kuhn_box_mesh(2, 0.1, 3)
-    mesh, om, eps, mu, bc = _setup(dg, verts, tets, 3, 11)
+    mesh, om, eps, mu, bc = _setup(dg, verts, tets, N, 11)
     mesh.set_flux(alpha)
+    mesh.set_stage_impl(impl)
     u0 = random_fields(om.K, om.Np, 12).astype(np.float32)
     dt = mesh.dt_cfl
     assert dt == pytest.approx(oracle.maxwell.cfl_dt(om, 1.0, eps, mu), rel=1e-14)
     u = torch.from_numpy(u0).cuda()
     res = torch.zeros_like(u)
+    mesh.trace_enable(200)
     mesh.step(u, res, dt, 20)
     torch.cuda.synchronize()
+    assert _kinds(mesh) == ({4} if impl == TC else {0})
     ue, _ = oracle.lserk4_run(om, u0.astype(np.float64), dt, 20, alpha=alpha, eps=eps, mu=mu, bc=bc)
     assert rel(u.cpu().numpy(), ue) < STEP_TOL
+
+
+def test_tensor_cores_agree_with_fp32_on_a_large_material_mesh(env):
+    """N = 4, K = 10 368 (several tiles per CTA): the tensor-core and FP32
+    stages agree on a mesh with materials and absorbing faces."""
+    torch, dg = env
+    verts, tets = kuhn_box_mesh(12, 0.15, 9)
+    mesh = dg.Mesh(verts, tets, 4)
+    eps, mu, bc = _materials(mesh.K, 41)
+    mesh.set_materials(eps, mu)
+    mesh.set_boundary(bc)
+    u0 = random_fields(mesh.K, mesh.Np, 42).astype(np.float32)
+    out = []
+    for impl in (TC, FP32):
+        mesh.set_stage_impl(impl)
+        u = torch.from_numpy(u0).cuda()
+        res = torch.zeros_like(u)
+        mesh.step(u, res, mesh.dt_cfl, 2)
+        out.append(u.cpu().numpy())
+    assert np.isfinite(out[0]).all()
+    assert rel(out[0], out[1].astype(np.float64)) < RHS_TOL
 
 
 @pytest.mark.parametrize("N", [2, 6, 7])
