@@ -391,6 +391,22 @@ __global__ void __launch_bounds__(TcDims<N>::THREADS, 1) tc_stage_kernel(const S
         const int k0 = tile * E, Ev = min(E, K - k0);
         float* su = sU + (t % D::NSU) * D::U_FLOATS;
         float* sr = sR + (t % D::NSR) * D::U_FLOATS;
+        if (warp == 0 && tc::elect_one()) {
+          // the slots of tile t-1 (its stores were issued one round ago) take
+          // tiles t+NSU-1 and t+1 now, before this tile's update
+          asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+          tc::fence_proxy_async_smem();
+          if (t + D::NSU - 1 < ntiles) {
+            const int s = (t + D::NSU - 1) % D::NSU;
+            tc_load_u<N>(A, tile + (D::NSU - 1) * gridDim.x, sU + s * D::U_FLOATS,
+                         sG + s * D::G_FLOATS, &s_u_full[s]);
+          }
+          if (RK && t + 1 < ntiles) {
+            const int s = (t + 1) % D::NSR;
+            tc_load_res<N>(A, tile + gridDim.x, sR + s * D::U_FLOATS, &s_r_full[s]);
+          }
+        }
+        __syncwarp();
         wait_or_flag(&s_mma_done[buf], (t >> 1) & 1, A.status);
         if (RK) wait_or_flag(&s_r_full[t % D::NSR], (t / D::NSR) & 1, A.status);
         tc::fence_after_sync();
@@ -459,18 +475,6 @@ __global__ void __launch_bounds__(TcDims<N>::THREADS, 1) tc_stage_kernel(const S
             }
           }
           tc::bulk_commit();
-          // slots of tile t-1 (stored one round ago) take tiles t+NSU-1 and t+1
-          asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
-          tc::fence_proxy_async_smem();
-          if (t + D::NSU - 1 < ntiles) {
-            const int s = (t + D::NSU - 1) % D::NSU;
-            tc_load_u<N>(A, tile + (D::NSU - 1) * gridDim.x, sU + s * D::U_FLOATS,
-                         sG + s * D::G_FLOATS, &s_u_full[s]);
-          }
-          if (RK && t + 1 < ntiles) {
-            const int s = (t + 1) % D::NSR;
-            tc_load_res<N>(A, tile + gridDim.x, sR + s * D::U_FLOATS, &s_r_full[s]);
-          }
         }
         __syncwarp();
       }
@@ -679,7 +683,7 @@ __global__ void __launch_bounds__(TcDims<N>::THREADS, 1) tc_stage_kernel(const S
 template <int N>
 cudaError_t launch_tc_stage_n(bool rk, const StageArgs& a, int num_sms, cudaStream_t s) {
   using D = TcDims<N>;
-  static bool attr[2][16] = {};
+  static bool attr[2][2][16] = {};      // [rk][ext][device]: attribute set
   int dev = 0;
   cudaError_t err = cudaGetDevice(&dev);
   if (err != cudaSuccess) return err;
@@ -690,10 +694,11 @@ cudaError_t launch_tc_stage_n(bool rk, const StageArgs& a, int num_sms, cudaStre
   // at least 120 KB of shared memory: never two CTAs (each takes all 512
   // tensor-memory columns) on one SM
   constexpr int smem = D::SMEM > 120 * 1024 ? D::SMEM : 120 * 1024;
-  if (!attr[rk ? 1 : 0][dev]) {
+  bool& done = attr[rk ? 1 : 0][ext ? 1 : 0][dev];
+  if (!done) {
     err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (err != cudaSuccess) return err;
-    attr[rk ? 1 : 0][dev] = true;
+    done = true;
   }
   const int grid = a.num_tiles < num_sms ? a.num_tiles : num_sms;
   if (grid <= 0) return cudaSuccess;

@@ -256,6 +256,21 @@ __global__ void __launch_bounds__(TtDims<N>::THREADS, 1) tt_stage_kernel(const S
           }
           tc::mma_commit_warp(&s_mma_done[j & 1]);
         }
+        if (j >= 1 && tc::elect_one()) {
+          // the slots of tile t-1 (stored in the previous iteration) take tiles
+          // t+NSU-1 and t+1 now, while warps 0..2 update tile t
+          asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+          tc::fence_proxy_async_smem();
+          if (t + D::NSU - 1 < ntiles) {
+            const int s = (t + D::NSU - 1) % D::NSU;
+            tt_load_u<N>(A, tile + (D::NSU - 1) * gridDim.x, sU + s * D::U_FLOATS,
+                         sG + s * D::G_FLOATS, &s_u_full[s]);
+          }
+          if (RK && t + 1 < ntiles) {
+            const int s = (t + 1) % D::NSR;
+            tt_load_res<N>(A, tile + gridDim.x, sR + s * D::U_FLOATS, &s_r_full[s]);
+          }
+        }
         __syncwarp();
       } else if (j >= 1) {                             // RK update of tile t = j - 1
         float* su = sU + (t % D::NSU) * D::U_FLOATS;
@@ -330,18 +345,6 @@ __global__ void __launch_bounds__(TtDims<N>::THREADS, 1) tt_stage_kernel(const S
           }
         }
         tc::bulk_commit();
-        // slots of tile t-1 (stored one round ago) take tiles t+NSU-1 and t+1
-        asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
-        tc::fence_proxy_async_smem();
-        if (t + D::NSU - 1 < ntiles) {
-          const int s = (t + D::NSU - 1) % D::NSU;
-          tt_load_u<N>(A, tile + (D::NSU - 1) * gridDim.x, sU + s * D::U_FLOATS,
-                       sG + s * D::G_FLOATS, &s_u_full[s]);
-        }
-        if (RK && t + 1 < ntiles) {
-          const int s = (t + 1) % D::NSR;
-          tt_load_res<N>(A, tile + gridDim.x, sR + s * D::U_FLOATS, &s_r_full[s]);
-        }
       }
       __syncwarp();
     }
@@ -552,7 +555,7 @@ __global__ void __launch_bounds__(TtDims<N>::THREADS, 1) tt_stage_kernel(const S
 template <int N>
 cudaError_t launch_tt_stage_n(bool rk, const StageArgs& a, int num_sms, cudaStream_t s) {
   using D = TtDims<N>;
-  static bool attr[2][16] = {};
+  static bool attr[2][2][16] = {};      // [rk][ext][device]: attribute set
   int dev = 0;
   cudaError_t err = cudaGetDevice(&dev);
   if (err != cudaSuccess) return err;
@@ -563,10 +566,11 @@ cudaError_t launch_tt_stage_n(bool rk, const StageArgs& a, int num_sms, cudaStre
   // at least 120 KB of shared memory: never two CTAs (each takes all 512
   // tensor-memory columns) on one SM
   constexpr int smem = D::SMEM > 120 * 1024 ? D::SMEM : 120 * 1024;
-  if (!attr[rk ? 1 : 0][dev]) {
+  bool& done = attr[rk ? 1 : 0][ext ? 1 : 0][dev];
+  if (!done) {
     err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (err != cudaSuccess) return err;
-    attr[rk ? 1 : 0][dev] = true;
+    done = true;
   }
   const int grid = a.num_tiles < num_sms ? a.num_tiles : num_sms;
   if (grid <= 0) return cudaSuccess;

@@ -170,3 +170,24 @@ def test_packed_mesh_with_materials_matches_its_parts(env):
     p.rk_stage(u, w, r, 1, dt)
     torch.cuda.synchronize()
     assert np.array_equal(w.cpu().numpy(), np.concatenate(outs, axis=1))
+
+
+@pytest.mark.parametrize("N", [4, 6])
+def test_vacuum_then_material_mesh_in_one_process(env, N):
+    """The vacuum and the material instantiation of a tensor-core stage
+    launched one after the other (each sets up its own launch attributes),
+    then the vacuum one again."""
+    torch, dg = env
+    verts, tets = kuhn_box_mesh(2, 0.1, 8)
+    vac, om = dg.Mesh(verts, tets, N), oracle.build_mesh(verts, tets, N)
+    mat, _, eps, mu, bc = _setup(dg, verts, tets, N, 51)
+    u32 = random_fields(om.K, om.Np, 52).astype(np.float32)
+    u = torch.from_numpy(u32).cuda()
+    for mesh, kw in ((vac, {}), (mat, dict(eps=eps, mu=mu, bc=bc)), (vac, {})):
+        mesh.set_stage_impl(TC)
+        mesh.trace_enable(2)
+        out = torch.full_like(u, float("nan"))
+        mesh.rhs(u, out)
+        torch.cuda.synchronize()
+        assert _kinds(mesh) == {5}
+        assert rel(out.cpu().numpy(), oracle.rhs(om, u32.astype(np.float64), 1.0, **kw)) < RHS_TOL
