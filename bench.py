@@ -379,17 +379,22 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-def serve_requests(count, rate, seed):
+SERVE_SHAPE = {"n": (4, 20), "N": (1, 7), "T": (0.5, 4.0)}
+
+
+def serve_requests(count, rate, seed, shape=SERVE_SHAPE):
     """Seeded request stream: Poisson arrivals at `rate` per second; box meshes
-    of n^3 x 6 tets (n uniform in 4..10, jitter 0.1h), orders N uniform in 1..6,
-    end times T uniform in [0.1, 0.5], Gaussian pulse of width 0.3 at a seeded
-    centre."""
+    of n^3 x 6 tets (n uniform in shape["n"], jitter 0.1h), orders N uniform in
+    shape["N"], end times T uniform in shape["T"] (both ends included for
+    integers), Gaussian pulse of width 0.3 at a seeded centre."""
     from paper_0901_1024_gb300.serve import Request
     rng = np.random.Generator(np.random.PCG64(seed))
     t, reqs = 0.0, []
     for rid in range(count):
         t += rng.exponential(1.0 / rate)
-        n, N, T = int(rng.integers(4, 11)), int(rng.integers(1, 7)), float(rng.uniform(0.1, 0.5))
+        n = int(rng.integers(shape["n"][0], shape["n"][1] + 1))
+        N = int(rng.integers(shape["N"][0], shape["N"][1] + 1))
+        T = float(rng.uniform(*shape["T"]))
         c = tuple(rng.uniform(-0.5, 0.5, 3))
         verts, tets = kuhn_box_mesh(n, 0.1, 1000 + rid)
         reqs.append(Request(rid, verts, tets, N, T,
@@ -397,46 +402,77 @@ def serve_requests(count, rate, seed):
     return reqs
 
 
-def run_serve(args):
-    """Served solves/s and latency percentiles of a request stream: the
-    continuous-batching server (packed launches, CUDA graphs, autotuned stage
-    kernels) against the plain per-solve form (one solve at a time, its own
-    launches) on the same stream."""
-    import torch
-    from paper_0901_1024_gb300.serve import Server
-    reqs = serve_requests(args.requests, args.rate, 5)
-    Server(autotune=True).run(serve_requests(4, 1e9, 99), max_iterations=10**6)   # warm-up
+SERVE_CONFIGS = {
+    # Poisson stream of solves with n in [4, 20], N in {1..7}, T in [0.5, 4]
+    "served": dict(count=32, seed=5, shape=SERVE_SHAPE),
+    # 64 independent solves present at once, n in [4, 16], N in {2..6}
+    "batched": dict(count=64, seed=6, shape={"n": (4, 16), "N": (2, 6), "T": (0.5, 0.5)}),
+}
 
-    def summary(results, wall):
+
+def run_serve(args):
+    """Solves/s and latency percentiles of a request set, three ways on the same
+    GPU: the continuous-batching server (packed launches, CUDA graphs, autotuned
+    stage kernels); the per-solve form with the same kernels (one solve at a
+    time, its own launches); and the plain per-solve form (one solve at a time
+    on the FP32 CUDA-core stage).  `--serve-config served` is a Poisson stream
+    at `--rate`; `batched` releases all solves at once."""
+    import torch
+    from paper_0901_1024_gb300 import Mesh
+    from paper_0901_1024_gb300.serve import Server
+    cfg = SERVE_CONFIGS[args.serve_config]
+    count = args.requests if args.serve_config == "served" else cfg["count"]
+    rate = args.rate if args.serve_config == "served" else 1e12
+    reqs = serve_requests(count, rate, cfg["seed"], cfg["shape"])
+    # warm-up, as a serving process would at start-up: the same meshes released
+    # together with a tiny end time set up every kernel and let the autotuner
+    # pick the stage implementation of every (order, decade of K) in the set
+    Server(autotune=True).run(serve_requests(count, 1e12, cfg["seed"],
+                                             {**cfg["shape"], "T": (0.01, 0.01)}),
+                              max_iterations=10**6)
+
+    def summary(results, wall, srv):
         lat = np.array([r.latency for r in results])
+        dofs = int(sum(6 * r.K * ((r.N + 1) * (r.N + 2) * (r.N + 3) // 6) * 5 * r.steps
+                       for r in results))
         return {"solves_per_s": len(results) / wall, "p50_latency_s": float(np.percentile(lat, 50)),
                 "p99_latency_s": float(np.percentile(lat, 99)), "wall_s": wall,
-                "dof_updates": int(sum(6 * r.K * ((r.N + 1) * (r.N + 2) * (r.N + 3) // 6) * 5 * r.steps
-                                       for r in results))}
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    srv = Server(batch=True, graphs=not args.serve_no_graphs, autotune=True,
-                 rebuild_every=args.rebuild_every)
-    served = srv.run(reqs, max_iterations=10**7)
-    ours = summary(served, time.perf_counter() - t0)
-    ours["host_phases"] = srv.stats
-    t0 = time.perf_counter()
-    one = Server(hbm_budget=1.0, batch=False, graphs=False, autotune=False)
-    plain = one.run(reqs, max_iterations=10**7)
-    base = summary(plain, time.perf_counter() - t0)
-    base["host_phases"] = one.stats
-    worst = max(float(np.linalg.norm(a.fields - b.fields) / max(np.linalg.norm(b.fields), 1e-30))
-                for a, b in zip(served, plain))
+                "dof_updates": dofs, "dof_updates_per_s": dofs / wall, "host_phases": srv.stats}
+
+    def timed(srv):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        res = srv.run(reqs, max_iterations=10**7)
+        torch.cuda.synchronize()
+        return res, summary(res, time.perf_counter() - t0, srv)
+
+    served, ours = timed(Server(batch=True, graphs=not args.serve_no_graphs, autotune=True,
+                                rebuild_every=args.rebuild_every))
+    same, base = timed(Server(hbm_budget=1.0, batch=False, graphs=False, autotune=False))
+    plain_res, plain = timed(Server(hbm_budget=1.0, batch=False, graphs=False, autotune=False,
+                                    impl=Mesh.STAGE_FP32))
+
+    def worst(a_list, b_list):
+        return max(float(np.linalg.norm(a.fields - b.fields) / max(np.linalg.norm(b.fields), 1e-30))
+                   for a, b in zip(a_list, b_list))
+    shape = cfg["shape"]
+    workload = (f"{count} requests, " + (f"Poisson {rate}/s" if args.serve_config == "served"
+                                          else "all released at t = 0") +
+                f", box meshes n^3 x 6 with n in {shape['n'][0]}..{shape['n'][1]}, N in "
+                f"{shape['N'][0]}..{shape['N'][1]}, T in [{shape['T'][0]}, {shape['T'][1]}], "
+                "Gaussian pulse, jitter 0.1h, seeded")
     line = {"metric": "served solves/s", "value": ours["solves_per_s"], "unit": "solves/s",
-            "higher_is_better": True, "n_gpus": 1, "dtype": "f32 (FP16x3 tensor cores for N<=6)",
-            "data": "synthetic", "mode": "serve",
-            "config": {"workload": f"{args.requests} requests, Poisson {args.rate}/s, n in 4..10, "
-                                   "N in 1..6, T in [0.1, 0.5], Gaussian pulse",
+            "higher_is_better": True, "n_gpus": 1,
+            "dtype": "f32 fields (FP16x3 tensor-core contractions for N = 2..6)",
+            "data": "synthetic", "mode": "serve", "serve_config": args.serve_config,
+            "config": {"workload": workload,
                        "server": "continuous batching: one packed launch per RK stage and order, "
-                                 "CUDA graphs, autotuned stage kernel per (N, K)"},
-            "served": ours, "one_at_a_time": base,
-            "speedup_solves_per_s": ours["solves_per_s"] / base["solves_per_s"],
-            "max_rel_l2_vs_one_at_a_time": worst}
+                                 "CUDA graphs, autotuned stage kernel per (N, K), HBM budget 150 GB"},
+            "served": ours, "one_at_a_time_same_kernels": base, "plain_one_at_a_time_fp32": plain,
+            "speedup_vs_same_kernels": ours["solves_per_s"] / base["solves_per_s"],
+            "speedup_vs_plain": ours["solves_per_s"] / plain["solves_per_s"],
+            "max_rel_l2_vs_same_kernels": worst(served, same),
+            "max_rel_l2_vs_plain_fp32": worst(served, plain_res)}
     print(json.dumps(line), flush=True)
 
 
@@ -496,11 +532,13 @@ def main():
                     help="stage: the RK-stage benchmark (default); serve: the request-stream "
                          "benchmark; sweep: stage throughput for N = 1..9")
     ap.add_argument("--sweep-steps", type=int, default=20)
-    ap.add_argument("--requests", type=int, default=48)
+    ap.add_argument("--requests", type=int, default=32)
     ap.add_argument("--rebuild-every", type=int, default=32,
                     help="serve mode: steps a pack runs before waiting solves join it")
     ap.add_argument("--serve-no-graphs", action="store_true")
     ap.add_argument("--rate", type=float, default=200.0)
+    ap.add_argument("--serve-config", default="served", choices=sorted(SERVE_CONFIGS),
+                    help="request set of --mode serve: a Poisson stream, or solves released together")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=15.0)

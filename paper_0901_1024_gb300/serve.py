@@ -162,6 +162,9 @@ class _Pack:
 class Server:
     """Continuous-batching request loop (see the module docstring).
 
+    The autotuner's choices (stage implementation per order, decade of K and
+    device) are kept for the life of the process, shared by every Server.
+
     hbm_budget : bytes of device memory the live solves may hold.
     batch      : pack the solves of one order into one stage launch; False
                  steps every live solve with its own launches (same arithmetic).
@@ -181,11 +184,12 @@ class Server:
         self.autotune, self.impl, self.keep = autotune, impl, keep_fields
         self.stream = torch.cuda.Stream()
         self._padding = {}
-        self._tuned = {}
         # host seconds per phase of the last run: admitting (mesh setup),
         # packing (pack build, device setup, graph capture, tuning), stepping,
         # retiring (energy, copy-out); and how many packs were built
         self.stats = {}
+
+    _tuned = {}                        # (device, N, decade of K) -> stage implementation
 
     # ---- stage implementation per (N, K) ---------------------------------
     def _pad_mesh(self, N):
@@ -200,7 +204,8 @@ class Server:
         if N > 6:
             return Mesh.STAGE_FP32
         K = sum(s.K for s in solves)
-        key = (N, min(3, int(math.log10(max(K, 1))) - 2))     # <1e3, <1e4, <1e5, more
+        key = (self.torch.cuda.current_device(), N,
+               min(3, int(math.log10(max(K, 1))) - 2))     # <1e3, <1e4, <1e5, more
         if key not in self._tuned:
             torch = self.torch
             times = {}
