@@ -259,7 +259,10 @@ int dg_energy_range(dg_mesh* mesh, const float* u, int64_t k0, int64_t k1, doubl
  * End-to-end convenience: copy host fields to the device, advance nsteps
  * LSERK4 steps, copy the fields back and (if energy != NULL) compute the
  * energy of the result.
- *   u, res : host, [6][K][Np] FP32, in/out (page-locked memory is fastest).
+ *   u   : host, [6][K][Np] FP32, in/out (page-locked memory is fastest);
+ *   res : host RK register, [6][K][Np] FP32, in/out, or NULL: then only u
+ *         crosses the bus and the device register starts from zero (a step's
+ *         result does not depend on it: the first LSERK4 stage has a = 0).
  * Uses library-owned device buffers; synchronises `stream`.
  */
 int dg_step_host(dg_mesh* mesh, float* u, float* res, double dt, int nsteps,

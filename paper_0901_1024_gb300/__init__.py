@@ -216,8 +216,11 @@ class Mesh:
         return out
 
     def step_host(self, u_host, res_host, dt: float, nsteps: int, with_energy=True, stream=None):
-        """u_host, res_host: host float32 buffers (NumPy arrays or pinned CPU tensors)."""
+        """u_host, res_host: host float32 buffers (NumPy arrays or pinned CPU
+        tensors); res_host may be None (only u crosses the bus)."""
         def hptr(a):
+            if a is None:
+                return None
             if isinstance(a, np.ndarray):
                 assert a.dtype == np.float32 and a.flags.c_contiguous
                 return C.c_void_p(a.ctypes.data)

@@ -852,11 +852,14 @@ int device_step_host(dg_mesh* m, float* u, float* res, double dt, int nsteps, do
   if (!d->h_u) DG_CUDA(cudaMalloc(&d->h_u, bytes), "cudaMalloc");
   if (!d->h_res) DG_CUDA(cudaMalloc(&d->h_res, bytes), "cudaMalloc");
   DG_CUDA(cudaMemcpyAsync(d->h_u, u, bytes, cudaMemcpyHostToDevice, s), "cudaMemcpyAsync H2D");
-  DG_CUDA(cudaMemcpyAsync(d->h_res, res, bytes, cudaMemcpyHostToDevice, s), "cudaMemcpyAsync H2D");
+  // without a host RK register the device one starts from zero (the first
+  // LSERK4 stage has a = 0, so a step's result does not depend on it)
+  if (res) DG_CUDA(cudaMemcpyAsync(d->h_res, res, bytes, cudaMemcpyHostToDevice, s), "cudaMemcpyAsync H2D");
+  else DG_CUDA(cudaMemsetAsync(d->h_res, 0, bytes, s), "cudaMemsetAsync");
   if ((rc = step_impl(m, d->h_u, d->h_res, dt, nsteps, s, err))) return rc;
   int64_t launches = m->last_launches;
   DG_CUDA(cudaMemcpyAsync(u, d->h_u, bytes, cudaMemcpyDeviceToHost, s), "cudaMemcpyAsync D2H");
-  DG_CUDA(cudaMemcpyAsync(res, d->h_res, bytes, cudaMemcpyDeviceToHost, s), "cudaMemcpyAsync D2H");
+  if (res) DG_CUDA(cudaMemcpyAsync(res, d->h_res, bytes, cudaMemcpyDeviceToHost, s), "cudaMemcpyAsync D2H");
   if (energy) {
     if ((rc = energy_impl(m, d->h_u, energy, s, err))) return rc;
     launches += 2;

@@ -380,6 +380,13 @@ def test_step_host_matches_device_step(env):
     torch.cuda.synchronize()
     assert np.array_equal(uh, ud.cpu().numpy()) and np.array_equal(rh, rd.cpu().numpy())
     assert abs(eh - mesh.energy(ud)) <= 1e-12 * eh
+    # without a host RK register only u crosses the bus; the steps are the same,
+    # and a garbage register left in the library's buffer does not leak in
+    uh2 = u0.copy()
+    mesh.step_host(uh2, np.full_like(u0, 1e30), mesh.dt_cfl, 1, with_energy=False)
+    uh2 = u0.copy()
+    eh2 = mesh.step_host(uh2, None, mesh.dt_cfl, 3)
+    assert np.array_equal(uh2, uh) and eh2 == eh
 
 
 def test_step_is_deterministic_and_resumable(env):
