@@ -195,6 +195,35 @@ def job_value(world, dof_per_stage, stages, seconds):
     return world * dof_per_stage * stages / seconds
 
 
+def path_accuracy(mesh, w, x, u0, dt, steps=200):
+    """Outside the timed region: `steps` LSERK4 steps from the initial fields on
+    the default stage path and on the plain FP32 CUDA-core path; their relative
+    L2 distance, and for the cavity mode each one's error against the exact
+    solution at the final time."""
+    import torch
+    out = {"steps": steps}
+    finals = {}
+    for name, impl in (("default", mesh.STAGE_AUTO), ("plain_fp32", mesh.STAGE_FP32)):
+        mesh.set_stage_impl(impl)
+        mesh.trace_enable(5)
+        u = torch.from_numpy(u0).cuda()
+        r = torch.zeros_like(u)
+        mesh.step(u, r, dt, steps)
+        torch.cuda.synchronize()
+        _, kinds = mesh.trace_read()
+        mesh.trace_enable(0)
+        finals[name] = u.cpu().numpy().astype(np.float64)
+        out[name + "_kernel"] = "tensor cores" if 4 in set(int(k) for k in kinds) else "FP32 CUDA cores"
+    mesh.set_stage_impl(mesh.STAGE_AUTO)
+    ref = finals["plain_fp32"]
+    out["rel_l2_default_vs_plain_fp32"] = float(np.linalg.norm(finals["default"] - ref) / np.linalg.norm(ref))
+    if w["init"] == "cavity":
+        exact = cavity_mode(x[0], x[1], x[2], steps * dt)
+        for name, v in finals.items():
+            out["rel_l2_vs_exact_" + name] = float(np.linalg.norm(v - exact) / np.linalg.norm(exact))
+    return out
+
+
 def run_ours(args):
     import torch
     import paper_0901_1024_gb300 as dg
@@ -275,6 +304,10 @@ def run_ours(args):
                "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes + 8,
                "steps": n_e2e, "call": "dg_step_host (pinned host u; H2D, 5 stages, D2H of u, energy)"}
 
+    accuracy = None
+    if rank == 0 and not args.no_accuracy:
+        accuracy = path_accuracy(mesh, w, x, u0, dt)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = time_oracle(w, verts, tets, budget_s=args.cpu_budget)
@@ -309,6 +342,7 @@ def run_ours(args):
             "clocks": clocks,
             "e2e": e2e,
             "gpu_launches": int(launches),
+            "accuracy": accuracy,
             "cpu_baseline": cpu,
         }
         print(json.dumps(line), flush=True)
@@ -542,6 +576,8 @@ def main():
                     help="request set of --mode serve: a Poisson stream, or solves released together")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-accuracy", action="store_true",
+                    help="skip the 200-step comparison of the default and the plain FP32 path")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)          # at least 3 untimed warm-up steps
