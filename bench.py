@@ -238,6 +238,8 @@ def run_ours(args):
     w, verts, tets = workload_inputs(args.workload)
     tets = element_order(dg, args.order, verts, tets, w["N"])
     mesh = dg.Mesh(verts, tets, w["N"])
+    mesh.set_stage_impl({"auto": mesh.STAGE_AUTO, "fp32": mesh.STAGE_FP32,
+                         "tc": mesh.STAGE_TC}[args.stage_kernel])
     K, Np, Nfp = mesh.K, mesh.Np, mesh.Nfp
     x = mesh.nodes()
     u0 = initial_fields(w, x).astype(np.float32)
@@ -323,7 +325,7 @@ def run_ours(args):
                        "l2": "inputs larger than L2 (u+res+work copy = %.0f MB > 129 MB)"
                              % (3 * u0.nbytes / 1e6),
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
-                       "element_order": args.order},
+                       "element_order": args.order, "stage_kernel": args.stage_kernel},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                          "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
                          "kernel": ((f"tc_stage_kernel<N={w['N']},RK> (tcgen05, FP16x3 split)" if w["N"] <= 4
@@ -576,6 +578,8 @@ def main():
                     help="request set of --mode serve: a Poisson stream, or solves released together")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--stage-kernel", default="auto", choices=["auto", "fp32", "tc"],
+                    help="stage implementation of the timed run (auto: the library's default per order)")
     ap.add_argument("--no-accuracy", action="store_true",
                     help="skip the 200-step comparison of the default and the plain FP32 path")
     ap.add_argument("--cpu-budget", type=float, default=15.0)

@@ -54,7 +54,9 @@ template <int N> struct StageDims {
   static_assert((UT % 4) == 0 && (FT % 4) == 0, "tiles must stay 16-byte aligned");
 };
 
-template <int N, bool RK>
+// EXT: meshes with materials (A.mat) or absorbing faces; the vacuum
+// instantiation compiles without any of that code.
+template <int N, bool RK, bool EXT>
 __global__ void __launch_bounds__(StageDims<N>::T) stage_kernel(const StageArgs A) {
   using D = StageDims<N>;
   constexpr int E = D::E, G = D::G, Np = D::Np, Nfp = D::Nfp, NF = D::NF, R = D::R;
@@ -111,7 +113,7 @@ __global__ void __launch_bounds__(StageDims<N>::T) stage_kernel(const StageArgs 
         if (code == 0u) {                       // perfectly conducting wall
 #pragma unroll
           for (int c = 0; c < 3; ++c) { uP[c] = -uM[c]; uP[c + 3] = uM[c + 3]; }
-        } else if (code == kAbsorbingCode) {    // characteristic absorbing: no incoming wave
+        } else if (EXT && code == kAbsorbingCode) {   // characteristic absorbing: no incoming wave
 #pragma unroll
           for (int c = 0; c < 6; ++c) uP[c] = 0.f;
         } else {
@@ -133,7 +135,7 @@ __global__ void __launch_bounds__(StageDims<N>::T) stage_kernel(const StageArgs 
         const float ndE = nx * dEx + ny * dEy + nz * dEz;
         const float ndH = nx * dHx + ny * dHy + nz * dHz;
         const float al = A.alpha;
-        if (!A.mat) {
+        if (!EXT || !A.mat) {
           // E: -n x dH + alpha (n (n.dE) - dE);  H: n x dE + alpha (n (n.dH) - dH)
           const float fl[6] = {
               -(ny * dHz - nz * dHy) + al * (nx * ndE - dEx),
@@ -266,7 +268,7 @@ __global__ void __launch_bounds__(StageDims<N>::T) stage_kernel(const StageArgs 
       for (int idx = tid; idx < Ev * Np; idx += D::T) {
         const int ee = idx / Np, i = idx - ee * Np;
         float r = sf[(c * E + ee) * US + i];
-        if (A.mat) {                            // rhs_E / eps, rhs_H / mu
+        if (EXT && A.mat) {                     // rhs_E / eps, rhs_H / mu
           const float4 w = __ldg(A.mat + size_t(k0 + ee) * kMatVecs);
           r *= c < 3 ? w.x : w.y;
         }
@@ -287,13 +289,15 @@ __global__ void __launch_bounds__(StageDims<N>::T) stage_kernel(const StageArgs 
 template <int N>
 cudaError_t launch_stage_n(bool rk, const StageArgs& a, int num_sms, cudaStream_t s) {
   using D = StageDims<N>;
-  static int occ[2][16] = {};
+  static int occ[2][2][16] = {};        // [rk][ext][device]: CTAs per SM
   int dev = 0;
   cudaError_t err = cudaGetDevice(&dev);
   if (err != cudaSuccess) return err;
   dev &= 15;
-  auto kern = rk ? stage_kernel<N, true> : stage_kernel<N, false>;
-  int& o = occ[rk ? 1 : 0][dev];
+  const bool ext = a.mat || a.absorbing;
+  auto kern = rk ? (ext ? stage_kernel<N, true, true> : stage_kernel<N, true, false>)
+                 : (ext ? stage_kernel<N, false, true> : stage_kernel<N, false, false>);
+  int& o = occ[rk ? 1 : 0][ext ? 1 : 0][dev];
   if (o == 0) {
     err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                int(D::smem_bytes));
