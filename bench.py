@@ -96,24 +96,38 @@ def load_peaks():
     return dict(FALLBACK_PEAKS), "fallback"
 
 
-def kernel_source_digest():
+# Source files of each stage kernel family: a profile summary records the
+# digest of the family it measured.
+KERNEL_SOURCES = {
+    "tc": ("tc_stage.cuh", "tcgen05.cuh", "device.h"),                    # tensor cores, N <= 4
+    "tt": ("tc_stage_t.cuh", "tc_stage.cuh", "tcgen05.cuh", "device.h"),  # tensor cores, N = 5, 6
+    "fp32": ("stage_kernel.cuh", "device.h"),                             # CUDA cores
+}
+
+
+def kernel_family(N, tc_path):
+    return ("tc" if N <= 4 else "tt") if tc_path else "fp32"
+
+
+def kernel_source_digest(family):
     h = hashlib.sha256()
-    for n in ("stage_kernel.cuh", "tc_stage.cuh", "tc_stage_t.cuh", "tcgen05.cuh", "device.h"):
+    for n in KERNEL_SOURCES[family]:
         with open(os.path.join(ROOT, "paper_0901_1024_gb300", "csrc", n), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(workload):
-    """DRAM bytes per stage launch from the committed ncu summary, if it was
-    taken on the current kernel source (digest line), else None."""
+def profiled_traffic(workload, family):
+    """DRAM bytes per stage launch from the committed ncu summary of this
+    workload, if it was taken on the current source of the kernel family that
+    ran (digest line), else None."""
     p = os.path.join(ROOT, "profiles", f"stage_kernel_{workload}.md")
     if not os.path.exists(p):
         return None
     text = open(p).read()
     dg = re.search(r"kernel_source_digest:\s*([0-9a-f]+)", text)
     tb = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", text)
-    if not dg or not tb or dg.group(1) != kernel_source_digest():
+    if not dg or not tb or dg.group(1) != kernel_source_digest(family):
         return None
     return float(tb.group(1))
 
@@ -282,7 +296,7 @@ def run_ours(args):
     peaks, peaks_src = load_peaks()
     algo_bytes = stage_bytes_per_elem(Np) * K
     achieved = algo_bytes / avg_stage_s / 1e9
-    traffic = profiled_traffic(args.workload)
+    traffic = profiled_traffic(args.workload, kernel_family(w["N"], tc_path))
     flops = flops_per_elem_stage(w["N"], Np, Nfp) * K
     fp32_peak = 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12   # TFLOP/s, FP32 FMA
 
