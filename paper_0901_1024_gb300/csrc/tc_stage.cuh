@@ -22,11 +22,14 @@
 //     extraction, Alg. 3 of the paper; up to 3 face nodes per thread): neighbour
 //     values outside the tile arrive by 4-byte cp.async copies into the flux
 //     buffer, every face node's upwind flux (PEC ghost state on walls) is
-//     written to a shared [row][m] buffer; after a named barrier they build the
-//     A rows of tile t in tensor memory (tcgen05.st), per lane quarter roles 0
-//     and 1 the two halves of the node range of the g^mu blocks and roles 2
-//     and 3 the two halves of the flux block, with one power-of-two scale per
-//     row (published by a second barrier) and the FP16 hi/lo split;
+//     written to a shared [row][m] buffer; then they build the A rows of tile t
+//     in tensor memory (tcgen05.st), per lane quarter roles 0 and 1 the two
+//     halves of the node range of the g^mu blocks (they do not read the flux
+//     buffer: they signal it with bar.arrive and go on) and roles 2 and 3 the
+//     two halves of the flux block (bar.sync: after every flux is stored; they
+//     also take the last, partial round of flux items), with one power-of-two
+//     scale per row (published by a barrier of all producers) and the FP16
+//     hi/lo split;
 //   * MMA/epilogue warps (4): warp 0 issues the 3 x K/16 MMAs of tile t into a
 //     double-buffered FP32 accumulator (elect.sync, commit to an mbarrier) and
 //     all bulk copies; all four then read tile t-1's accumulator rows
@@ -66,6 +69,10 @@ template <int N> struct TcDims {
   static constexpr int THREADS = 640;                 // 4 epilogue + 16 producer warps
   static constexpr int PRODUCERS = 512;
   static constexpr int ITEMS = (E * NF + PRODUCERS - 1) / PRODUCERS;   // flux items per producer
+  // the last, partial round of flux items goes to roles 2 and 3 (the flux-block
+  // builders, whose build is shorter); when it fits them, roles 0 and 1 skip it
+  static constexpr int LAST = E * NF - (ITEMS - 1) * PRODUCERS;
+  static constexpr bool SPLIT = ITEMS >= 2 && (ITEMS - 1) % 2 == 0 && LAST <= PRODUCERS / 2;
   static constexpr int NSU = 5, NSR = 2;              // ring slots: fields+geometry, RK register
   // shared memory (bytes)
   static constexpr int U_FLOATS = 6 * E * Np;         // one tile of one state array
@@ -78,8 +85,8 @@ template <int N> struct TcDims {
   static constexpr int OFF_G = OFF_U + NSU * U_FLOATS * 4;
   static constexpr int OFF_R = OFF_G + NSU * G_FLOATS * 4;   // NSR slots
   static constexpr int OFF_F = OFF_R + NSR * U_FLOATS * 4;   // one flux buffer
-  static constexpr int OFF_BND = OFF_F + F_FLOATS * 4;         // [4 roles][128] row bounds
-  static constexpr int OFF_SC = OFF_BND + 4 * 128 * 4;       // [4][128] row scales
+  static constexpr int OFF_BND = OFF_F + F_FLOATS * 4;         // [2 tiles][4 roles][128] row bounds
+  static constexpr int OFF_SC = OFF_BND + 2 * 4 * 128 * 4;   // [4][128] row scales
   static constexpr int OFF_TAB = OFF_SC + 4 * 128 * 4;
   static constexpr int SMEM = OFF_TAB + TAB_BYTES;
   static_assert((U_FLOATS * 4) % 16 == 0 && (E * Np * 4) % 16 == 0, "bulk-copy alignment");
@@ -158,6 +165,10 @@ __device__ __forceinline__ float row_scale(float rmax) {
 __device__ __forceinline__ void named_sync(int id, int nthreads) {
   asm volatile("bar.sync %0, %1;" :: "r"(id), "r"(nthreads) : "memory");
 }
+// Signal a named barrier without waiting (producer side of bar.arrive / bar.sync).
+__device__ __forceinline__ void named_arrive(int id, int nthreads) {
+  asm volatile("bar.arrive %0, %1;" :: "r"(id), "r"(nthreads) : "memory");
+}
 
 constexpr uint32_t kWaitLimit = 1u << 26;
 
@@ -233,12 +244,14 @@ __device__ __forceinline__ void build_g_half(const GRow& g, int role) {
       cmax = fmaxf(cmax, fabsf(g.sg[(3 * mu + (g.o + 1) % 3) * E + g.re]) +
                              fabsf(g.sg[(3 * mu + (g.o + 2) % 3) * E + g.re]));
   }
-  named_sync(2, D::PRODUCERS);            // everyone read the previous tile's bounds
-  // |g^mu| <= (|r_mu,a| + |r_mu,b|) max(max|U_a|, max|U_b|) over this node range
-  g.sBound[role * 128 + g.row] = cmax * umax;
+  // |g^mu| <= (|r_mu,a| + |r_mu,b|) max(max|U_a|, max|U_b|) over this node range;
+  // bounds of tiles t and t+1 live in different halves (a thread reads tile t's
+  // before it arrives at tile t+1's barrier, which precedes tile t+2's writes)
+  float* bnd = g.sBound + (g.t & 1) * 512;
+  bnd[role * 128 + g.row] = cmax * umax;
   named_sync(2, D::PRODUCERS);            // row bounds published
-  const float s = row_scale(fmaxf(fmaxf(g.sBound[g.row], g.sBound[128 + g.row]),
-                                  fmaxf(g.sBound[256 + g.row], g.sBound[384 + g.row])));
+  const float s = row_scale(fmaxf(fmaxf(bnd[g.row], bnd[128 + g.row]),
+                                  fmaxf(bnd[256 + g.row], bnd[384 + g.row])));
   // A[buf] is free once the MMAs of tile t-2 have completed
   if (g.t >= 2) wait_or_flag(g.mma_done, ((g.t - 2) >> 1) & 1, g.status);
   tc::fence_after_sync();
@@ -278,7 +291,6 @@ template <int N, int P0, int NPH>
 __device__ __forceinline__ void build_flux_half(const FRow& g, int role) {
   using D = TcDims<N>;
   constexpr int NF = D::NF;
-  named_sync(2, D::PRODUCERS);                     // the flux buffer is complete
   const float2* frow = reinterpret_cast<const float2*>(g.frow);
   float2 w[NPH];
   float fmax = 0.f;
@@ -287,10 +299,11 @@ __device__ __forceinline__ void build_flux_half(const FRow& g, int role) {
     w[i] = (g.live && 2 * (P0 + i) < NF) ? frow[P0 + i] : make_float2(0.f, 0.f);
     fmax = fmaxf(fmax, fmaxf(fabsf(w[i].x), fabsf(w[i].y)));
   }
-  g.sBound[role * 128 + g.row] = fmax;
+  float* bnd = g.sBound + (g.t & 1) * 512;
+  bnd[role * 128 + g.row] = fmax;
   named_sync(2, D::PRODUCERS);                     // row bounds published
-  const float s = row_scale(fmaxf(fmaxf(g.sBound[g.row], g.sBound[128 + g.row]),
-                                  fmaxf(g.sBound[256 + g.row], g.sBound[384 + g.row])));
+  const float s = row_scale(fmaxf(fmaxf(bnd[g.row], bnd[128 + g.row]),
+                                  fmaxf(bnd[256 + g.row], bnd[384 + g.row])));
   // A[buf] is free once the MMAs of tile t-2 have completed
   if (g.t >= 2) wait_or_flag(g.mma_done, ((g.t - 2) >> 1) & 1, g.status);
   tc::fence_after_sync();
@@ -497,12 +510,16 @@ __global__ void __launch_bounds__(TcDims<N>::THREADS, 1) tc_stage_kernel(const S
     const int fb = rc < 3 ? 3 + (o + 1) % 3 : (o + 1) % 3;
     const float sgn = rc < 3 ? 1.f : -1.f;
     // Item idx = pt + q * PRODUCERS is face node m of element e (idx = e * NF + m), so
-    // a warp's items are consecutive face nodes of one or two elements.  Their
-    // tile-independent decode: e | m << 5 | f << 12 | idM << 14, bit 31 past the end.
+    // a warp's items are consecutive face nodes of one or two elements; in the
+    // last round the producer numbering is rotated by half, so that its items go
+    // to roles 2 and 3 first.  Tile-independent decode: e | m << 5 | f << 12 |
+    // idM << 14, bit 31 past the end.
     uint32_t item[D::ITEMS];
 #pragma unroll
     for (int q = 0; q < D::ITEMS; ++q) {
-      const int idx = pt + q * D::PRODUCERS;
+      const int idx = q < D::ITEMS - 1 ? pt + q * D::PRODUCERS
+                                       : (D::ITEMS - 1) * D::PRODUCERS +
+                                             (pt + D::PRODUCERS / 2) % D::PRODUCERS;
       const int e = idx / NF, m = idx - e * NF;
       item[q] = idx < E * NF ? uint32_t(e) | uint32_t(m) << 5 | uint32_t(m / Nfp) << 12 |
                                    uint32_t(sFmask[m]) << 14
@@ -523,8 +540,13 @@ __global__ void __launch_bounds__(TcDims<N>::THREADS, 1) tc_stage_kernel(const S
       // F was last read in the build of tile t-1, before its barrier.
       const unsigned char* nodes = reinterpret_cast<const unsigned char*>(sg + kTcGeoWords * E);
       uint32_t info[D::ITEMS];          // kind | ofs << 2
+      const bool last_round = !D::SPLIT || role >= 2;   // this warp takes last-round items
 #pragma unroll
       for (int q = 0; q < D::ITEMS; ++q) {
+        if (q == D::ITEMS - 1 && !last_round) {
+          info[q] = 0u;
+          continue;
+        }
         const uint32_t it = item[q];
         const int e = it & 31, m = (it >> 5) & 127, f = (it >> 12) & 3, idM = (it >> 14) & 63;
         const bool ok = !(it >> 31) && e < Ev;
@@ -559,7 +581,7 @@ __global__ void __launch_bounds__(TcDims<N>::THREADS, 1) tc_stage_kernel(const S
         uint32_t kinds[NQ];
 #pragma unroll
         for (int q = 0; q < NQ; ++q) {
-          if (q >= D::ITEMS) {
+          if (q >= D::ITEMS || (q == D::ITEMS - 1 && !last_round)) {
             kinds[q] = 0u;
 #pragma unroll
             for (int c = 0; c < 6; ++c) uM[q][c] = up[q][c] = 0.f;
@@ -590,6 +612,7 @@ __global__ void __launch_bounds__(TcDims<N>::THREADS, 1) tc_stage_kernel(const S
         const float2 m1 = f2(-1.f), nal = f2(-A.alpha), al = f2(A.alpha);
 #pragma unroll
         for (int q = 0; q < NQ; q += 2) {
+          if (q >= D::ITEMS - 1 && !last_round) continue;   // a pair of last-round items only
           const int r = q + 1;
           auto P = [&](const float (*v)[6], int c) { return make_float2(v[q][c], v[r][c]); };
           const float2 nwe = make_float2(kinds[q] == 1u ? 1.f : -1.f, kinds[r] == 1u ? 1.f : -1.f);
@@ -645,6 +668,11 @@ __global__ void __launch_bounds__(TcDims<N>::THREADS, 1) tc_stage_kernel(const S
           }
         }
       }
+      // The flux buffer is complete once every producer has stored its items:
+      // roles 2 and 3 (which read it) wait for that; roles 0 and 1 only signal
+      // and go on with the g blocks.
+      if (role < 2) named_arrive(3, D::PRODUCERS);
+      else named_sync(3, D::PRODUCERS);
       // ---- A rows of tile t
       const bool live = row < D::ROWS && re < Ev;
       const uint32_t a_hi = tbase + lane_off + buf * D::BUF_COLS;
