@@ -19,17 +19,18 @@
 // One persistent CTA per SM (all 512 tensor-memory columns), two warp groups
 // working on different tiles at once, linked by mbarriers:
 //   * producer warps (16): together they compute the fluxes of tile t (flux
-//     extraction, Alg. 3 of the paper; up to 3 face nodes per thread): neighbour
+//     extraction, Alg. 3 of the paper; up to 2 face nodes per thread; at N = 4
+//     the face nodes of the tile's last 3 elements are done one tile earlier by
+//     epilogue warps 1..3 into a small parity-buffered flux buffer): neighbour
 //     values outside the tile arrive by 4-byte cp.async copies into the flux
 //     buffer, every face node's upwind flux (PEC ghost state on walls) is
 //     written to a shared [row][m] buffer; then they build the A rows of tile t
 //     in tensor memory (tcgen05.st), per lane quarter roles 0 and 1 the two
 //     halves of the node range of the g^mu blocks (they do not read the flux
 //     buffer: they signal it with bar.arrive and go on) and roles 2 and 3 the
-//     two halves of the flux block (bar.sync: after every flux is stored; they
-//     also take the last, partial round of flux items), with one power-of-two
-//     scale per row (published by a barrier of all producers) and the FP16
-//     hi/lo split;
+//     two halves of the flux block (bar.sync: after every flux is stored), with
+//     one power-of-two scale per row (published by a barrier of all producers)
+//     and the FP16 hi/lo split;
 //   * MMA/epilogue warps (4): warp 0 issues the 3 x K/16 MMAs of tile t into a
 //     double-buffered FP32 accumulator (elect.sync, commit to an mbarrier) and
 //     all bulk copies; all four then read tile t-1's accumulator rows
@@ -68,11 +69,15 @@ template <int N> struct TcDims {
                                                       // a warp's 32 rows are conflict-free
   static constexpr int THREADS = 640;                 // 4 epilogue + 16 producer warps
   static constexpr int PRODUCERS = 512;
-  static constexpr int ITEMS = (E * NF + PRODUCERS - 1) / PRODUCERS;   // flux items per producer
-  // the last, partial round of flux items goes to roles 2 and 3 (the flux-block
-  // builders, whose build is shorter); when it fits them, roles 0 and 1 skip it
-  static constexpr int LAST = E * NF - (ITEMS - 1) * PRODUCERS;
-  static constexpr bool SPLIT = ITEMS >= 2 && (ITEMS - 1) % 2 == 0 && LAST <= PRODUCERS / 2;
+  // Flux items (face nodes): the producers take elements 0 .. E0-1 in at most
+  // two rounds; the face nodes of elements E0 .. E-1 are computed one tile
+  // ahead by epilogue warps 1..3 (warp 0 issues the MMAs), which otherwise
+  // wait for A.
+  static constexpr int E0 = 2 * PRODUCERS / NF < E ? 2 * PRODUCERS / NF : E;
+  static constexpr int ITEMS = (E0 * NF + PRODUCERS - 1) / PRODUCERS;  // flux items per producer
+  static constexpr int EPI = (E - E0) * NF;              // face nodes of the epilogue threads
+  static constexpr int EITEMS = EPI ? (EPI + 95) / 96 : 1;   // per thread of warps 1..3
+  static constexpr int FCOUNT = PRODUCERS + (EPI ? 128 : 0);  // threads at the flux barrier
   static constexpr int NSU = 5, NSR = 2;              // ring slots: fields+geometry, RK register
   // shared memory (bytes)
   static constexpr int U_FLOATS = 6 * E * Np;         // one tile of one state array
@@ -85,7 +90,9 @@ template <int N> struct TcDims {
   static constexpr int OFF_G = OFF_U + NSU * U_FLOATS * 4;
   static constexpr int OFF_R = OFF_G + NSU * G_FLOATS * 4;   // NSR slots
   static constexpr int OFF_F = OFF_R + NSR * U_FLOATS * 4;   // one flux buffer
-  static constexpr int OFF_BND = OFF_F + F_FLOATS * 4;         // [2 tiles][4 roles][128] row bounds
+  static constexpr int F2_FLOATS = 6 * (E - E0) * FSTR;      // epilogue-computed flux rows
+  static constexpr int OFF_F2 = OFF_F + F_FLOATS * 4;         // [2 tiles][6][E - E0][FSTR]
+  static constexpr int OFF_BND = OFF_F2 + 2 * F2_FLOATS * 4;  // [2 tiles][4 roles][128] row bounds
   static constexpr int OFF_SC = OFF_BND + 2 * 4 * 128 * 4;   // [4][128] row scales
   static constexpr int OFF_TAB = OFF_SC + 4 * 128 * 4;
   static constexpr int SMEM = OFF_TAB + TAB_BYTES;
@@ -310,12 +317,167 @@ __device__ __forceinline__ void build_flux_half(const FRow& g, int role) {
   split_store_fn<NPH, P0>([&](int p) { return __fmul2_rn(w[p - P0], f2(s)); }, g.a_hi, g.a_lo);
 }
 
+// Decode of flux item idx = e * NF + m (face node m of element e), for idx <
+// `elems` * NF: e | m << 5 | f << 12 | idM << 14 (f the face, idM the element's
+// node there); bit 31 set past the end.
+template <int N>
+__device__ __forceinline__ uint32_t tc_item(int idx, int elems, const unsigned char* sFmask) {
+  using D = TcDims<N>;
+  const int e = idx / D::NF, m = idx - e * D::NF;
+  return idx < elems * D::NF ? uint32_t(e) | uint32_t(m) << 5 | uint32_t(m / D::Nfp) << 12 |
+                                   uint32_t(sFmask[m]) << 14
+                             : 0x80000000u;
+}
+
+// Flux extraction (Alg. 3) of the face nodes `item` (decoded e | m << 5 | f << 12 |
+// idM << 14, bit 31: none) of the tile starting at element k0 with Ev valid
+// elements, fields su and geometry sg in shared memory: classify, gather the
+// neighbour values outside the tile, form the upwind fluxes (PEC ghost state on
+// walls, zero exterior state on absorbing faces) and store them at
+// dst + (c * CS + e - E0) * FSTR + m for field c of element e (E0 <= e < E0 + CS).
+template <int N, bool EXT, int NI>
+__device__ __forceinline__ void tc_flux_items(const uint32_t (&item)[NI], const StageArgs& A,
+                                              int k0, int Ev, const float* su, const float* sg,
+                                              float* dst, int CS, int E0) {
+  using D = TcDims<N>;
+  constexpr int E = D::E, Np = D::Np, NF = D::NF, FSTR = D::FSTR;
+  const int K = A.K;
+  const unsigned char* nodes = reinterpret_cast<const unsigned char*>(sg + kTcGeoWords * E);
+  // Classify every item (0 none, 1 wall, 2 neighbour in the tile, 3 neighbour
+  // outside it) and start the gathers of kind 3: the six neighbour values go by
+  // 4-byte asynchronous copies into the destination words this item's flux will
+  // overwrite (no registers, no extra space).
+  uint32_t info[NI];                // kind | ofs << 2
+#pragma unroll
+  for (int q = 0; q < NI; ++q) {
+    const uint32_t it = item[q];
+    const int e = it & 31, m = (it >> 5) & 127, f = (it >> 12) & 3, idM = (it >> 14) & 63;
+    const bool ok = !(it >> 31) && e < Ev;
+    const int ec = ok ? e : 0;
+    const unsigned code = (__float_as_uint(sg[9 * E + ec]) >> (8 * f)) & 0xffu;
+    const int k2 = __float_as_int(sg[(26 + f) * E + ec]);
+    const int i2 = nodes[ec * NF + m];
+    const int e2 = k2 - k0;
+    // absorbing faces (EXT): a wall whose exterior state is zero
+    const bool absorbing = EXT && code == kAbsorbingCode;
+    const uint32_t kind = !ok ? 0u
+                          : (code == 0u || absorbing) ? 1u
+                          : unsigned(e2) < unsigned(Ev) ? 2u : 3u;
+    if (kind == 3u) {
+      const float* src = A.u_in + size_t(k2) * Np + i2;
+#pragma unroll
+      for (int c = 0; c < 6; ++c)
+        tc::cp_async4(dst + (c * CS + e - E0) * FSTR + m, src + size_t(c) * K * Np);
+    }
+    info[q] = kind | uint32_t(kind == 2u ? e2 * Np + i2 : ec * Np + idM) << 2 |
+              (absorbing ? 0x80000000u : 0u);
+  }
+  tc::cp_async_commit();
+  tc::cp_async_wait_all();
+  // upwind flux of every face node (PEC ghost state E+ = -E-, H+ = H- on walls):
+  // every item's operands are loaded before any store into the flux buffer,
+  // then items are processed two at a time in packed FP32x2 arithmetic
+  {
+    constexpr int NQ = (NI + 1) & ~1;
+    float uM[NQ][6], up[NQ][6], nv[NQ][4];
+    float4 cf[EXT ? NQ : 1];          // EXT: Z+, B_E, Y+, B_H of the item's face
+    uint32_t kinds[NQ];
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+      if (q >= NI) {
+        kinds[q] = 0u;
+#pragma unroll
+        for (int c = 0; c < 6; ++c) uM[q][c] = up[q][c] = 0.f;
+#pragma unroll
+        for (int w = 0; w < 4; ++w) nv[q][w] = 0.f;
+        if constexpr (EXT) cf[q] = make_float4(1.f, 0.5f, 1.f, 0.5f);
+        continue;
+      }
+      const uint32_t it = item[q], kind = info[q] & 3u;
+      kinds[q] = kind;
+      const int e = kind ? int(it & 31) : 0, m = (it >> 5) & 127, f = (it >> 12) & 3;
+      const int idM = (it >> 14) & 63;
+      const float* pp = kind == 3u ? dst + (e - E0) * FSTR + m
+                                   : su + (EXT ? (info[q] >> 2) & 0x1FFFFFFFu : info[q] >> 2);
+      const int ps = kind == 3u ? CS * FSTR : E * Np;
+      const bool zero_ext = EXT && (info[q] >> 31);          // absorbing: u+ = 0
+#pragma unroll
+      for (int c = 0; c < 6; ++c) {
+        uM[q][c] = su[c * E * Np + e * Np + idM];
+        up[q][c] = zero_ext ? 0.f : pp[c * ps];
+      }
+#pragma unroll
+      for (int w = 0; w < 4; ++w) nv[q][w] = sg[(10 + 4 * f + w) * E + e];
+      if constexpr (EXT)
+        cf[q] = A.mat && kind ? __ldg(A.mat + size_t(k0 + e) * kMatVecs + 1 + f)
+                              : make_float4(1.f, 0.5f, 1.f, 0.5f);
+    }
+    const float2 m1 = f2(-1.f), nal = f2(-A.alpha), al = f2(A.alpha);
+#pragma unroll
+    for (int q = 0; q < NQ; q += 2) {
+      const int r = q + 1;
+      auto P = [&](const float (*v)[6], int c) { return make_float2(v[q][c], v[r][c]); };
+      const float2 nwe = make_float2(kinds[q] == 1u ? 1.f : -1.f, kinds[r] == 1u ? 1.f : -1.f);
+      const float2 dEx = __ffma2_rn(nwe, P(up, 0), P(uM, 0));
+      const float2 dEy = __ffma2_rn(nwe, P(up, 1), P(uM, 1));
+      const float2 dEz = __ffma2_rn(nwe, P(up, 2), P(uM, 2));
+      const float2 dHx = __ffma2_rn(m1, P(up, 3), P(uM, 3));
+      const float2 dHy = __ffma2_rn(m1, P(up, 4), P(uM, 4));
+      const float2 dHz = __ffma2_rn(m1, P(up, 5), P(uM, 5));
+      const float2 nx = make_float2(nv[q][0], nv[r][0]), ny = make_float2(nv[q][1], nv[r][1]);
+      const float2 nz = make_float2(nv[q][2], nv[r][2]);
+      const float2 sc = __fmul2_rn(f2(0.5f), make_float2(nv[q][3], nv[r][3]));
+      // EXT: B_E (Z+ (-n x dH) + ...), B_H (Y+ (n x dE) + ...) with Fscale
+      float2 zp = f2(1.f), yp = f2(1.f), scE = sc, scH = sc;
+      if constexpr (EXT) {
+        zp = make_float2(cf[q].x, cf[r].x);
+        yp = make_float2(cf[q].z, cf[r].z);
+        scE = __fmul2_rn(make_float2(cf[q].y, cf[r].y), make_float2(nv[q][3], nv[r][3]));
+        scH = __fmul2_rn(make_float2(cf[q].w, cf[r].w), make_float2(nv[q][3], nv[r][3]));
+      }
+      const float2 mx = __fmul2_rn(m1, nx), my = __fmul2_rn(m1, ny), mz = __fmul2_rn(m1, nz);
+      const float2 aE = __fmul2_rn(al, __ffma2_rn(nz, dEz, __ffma2_rn(ny, dEy, __fmul2_rn(nx, dEx))));
+      const float2 aH = __fmul2_rn(al, __ffma2_rn(nz, dHz, __ffma2_rn(ny, dHy, __fmul2_rn(nx, dHx))));
+      // fluxE = -n x dH + alpha (n (n.dE) - dE), fluxH = n x dE + alpha (n (n.dH) - dH)
+      float2 fl[6];
+      if constexpr (!EXT) {
+        fl[0] = __ffma2_rn(nal, dEx, __ffma2_rn(nx, aE, __ffma2_rn(my, dHz, __fmul2_rn(nz, dHy))));
+        fl[1] = __ffma2_rn(nal, dEy, __ffma2_rn(ny, aE, __ffma2_rn(mz, dHx, __fmul2_rn(nx, dHz))));
+        fl[2] = __ffma2_rn(nal, dEz, __ffma2_rn(nz, aE, __ffma2_rn(mx, dHy, __fmul2_rn(ny, dHx))));
+        fl[3] = __ffma2_rn(nal, dHx, __ffma2_rn(nx, aH, __ffma2_rn(mz, dEy, __fmul2_rn(ny, dEz))));
+        fl[4] = __ffma2_rn(nal, dHy, __ffma2_rn(ny, aH, __ffma2_rn(mx, dEz, __fmul2_rn(nz, dEx))));
+        fl[5] = __ffma2_rn(nal, dHz, __ffma2_rn(nz, aH, __ffma2_rn(my, dEx, __fmul2_rn(nx, dEy))));
+      } else {
+        fl[0] = __ffma2_rn(nal, dEx, __ffma2_rn(nx, aE, __fmul2_rn(zp, __ffma2_rn(my, dHz, __fmul2_rn(nz, dHy)))));
+        fl[1] = __ffma2_rn(nal, dEy, __ffma2_rn(ny, aE, __fmul2_rn(zp, __ffma2_rn(mz, dHx, __fmul2_rn(nx, dHz)))));
+        fl[2] = __ffma2_rn(nal, dEz, __ffma2_rn(nz, aE, __fmul2_rn(zp, __ffma2_rn(mx, dHy, __fmul2_rn(ny, dHx)))));
+        fl[3] = __ffma2_rn(nal, dHx, __ffma2_rn(nx, aH, __fmul2_rn(yp, __ffma2_rn(mz, dEy, __fmul2_rn(ny, dEz)))));
+        fl[4] = __ffma2_rn(nal, dHy, __ffma2_rn(ny, aH, __fmul2_rn(yp, __ffma2_rn(mx, dEz, __fmul2_rn(nz, dEx)))));
+        fl[5] = __ffma2_rn(nal, dHz, __ffma2_rn(nz, aH, __fmul2_rn(yp, __ffma2_rn(my, dEx, __fmul2_rn(nx, dEy)))));
+      }
+#pragma unroll
+      for (int c = 0; c < 6; ++c) fl[c] = __fmul2_rn(c < 3 ? scE : scH, fl[c]);
+      if (kinds[q]) {
+        float* fr = dst + (int(item[q] & 31) - E0) * FSTR + int((item[q] >> 5) & 127);
+#pragma unroll
+        for (int c = 0; c < 6; ++c) fr[c * CS * FSTR] = fl[c].x;
+      }
+      if (r < NI && kinds[r]) {
+        float* fr = dst + (int(item[r < NI ? r : 0] & 31) - E0) * FSTR +
+                    int((item[r < NI ? r : 0] >> 5) & 127);
+#pragma unroll
+        for (int c = 0; c < 6; ++c) fr[c * CS * FSTR] = fl[c].y;
+      }
+    }
+  }
+}
+
 // EXT: meshes with materials (A.mat) or absorbing faces; the vacuum instantiation
 // has none of that arithmetic.
 template <int N, bool RK, bool EXT>
 __global__ void __launch_bounds__(TcDims<N>::THREADS, 1) tc_stage_kernel(const StageArgs A) {
   using D = TcDims<N>;
-  constexpr int E = D::E, Np = D::Np, Nfp = D::Nfp, NF = D::NF, FSTR = D::FSTR;
+  constexpr int E = D::E, Np = D::Np, Nfp = D::Nfp, FSTR = D::FSTR;
   extern __shared__ __align__(1024) unsigned char smem[];
   __shared__ uint32_t s_tmem;
   __shared__ __align__(8) uint64_t s_u_full[D::NSU];
@@ -333,6 +495,7 @@ __global__ void __launch_bounds__(TcDims<N>::THREADS, 1) tc_stage_kernel(const S
   float* sF = reinterpret_cast<float*>(smem + D::OFF_F);
   float* sScale = reinterpret_cast<float*>(smem + D::OFF_SC);
   float* sBound = reinterpret_cast<float*>(smem + D::OFF_BND);
+  float* sF2 = reinterpret_cast<float*>(smem + D::OFF_F2);
   unsigned char* sFmask = smem + D::OFF_TAB;
   unsigned char* sPerm = sFmask + 4 * Nfp;
 
@@ -372,6 +535,27 @@ __global__ void __launch_bounds__(TcDims<N>::THREADS, 1) tc_stage_kernel(const S
       if (RK) tc_load_res<N>(A, blockIdx.x, sR, &s_r_full[0]);
     }
     __syncwarp();
+    // Flux items of elements E0 .. E-1 (warps 1..3), computed one tile ahead
+    // into the buffer of that tile's parity (tile 0 now, tile j+1 in iteration
+    // j), then signalled at the flux barrier of that tile by all four warps.
+    // The buffer of parity t & 1 was last read by the flux-block builders of
+    // tile t-2, before A(t-2).
+    uint32_t eitem[D::EITEMS];
+#pragma unroll
+    for (int q = 0; q < D::EITEMS; ++q)
+      eitem[q] = tc_item<N>(D::E0 * D::NF + (tid - 32) + 96 * q, E, sFmask);
+    auto epilogue_fluxes = [&](int t) {
+      if (warp != 0) {
+        const int slot = t % D::NSU;
+        const int k0t = (int(blockIdx.x) + t * int(gridDim.x)) * E, Evt = min(E, K - k0t);
+        wait_or_flag(&s_u_full[slot], (t / D::NSU) & 1, A.status);
+        tc_flux_items<N, EXT, D::EITEMS>(eitem, A, k0t, Evt, sU + slot * D::U_FLOATS,
+                                         sG + slot * D::G_FLOATS, sF2 + (t & 1) * D::F2_FLOATS,
+                                         E - D::E0, D::E0);
+      }
+      named_arrive(3 + (t & 1), D::FCOUNT);
+    };
+    if constexpr (D::EPI > 0) epilogue_fluxes(0);
     constexpr uint32_t IDESC = tc::idesc_f16(128, D::NN);
     constexpr uint32_t LBO = (D::NN / 8) * 128;
     for (int j = 0; j <= ntiles; ++j) {
@@ -397,6 +581,9 @@ __global__ void __launch_bounds__(TcDims<N>::THREADS, 1) tc_stage_kernel(const S
         }
         tc::mma_commit_warp(&s_mma_done[buf]);
         __syncwarp();
+      }
+      if constexpr (D::EPI > 0) {
+        if (j + 1 < ntiles) epilogue_fluxes(j + 1);
       }
       if (j >= 1) {                                  // epilogue of tile t = j - 1
         const int t = j - 1, buf = t & 1;
@@ -510,21 +697,10 @@ __global__ void __launch_bounds__(TcDims<N>::THREADS, 1) tc_stage_kernel(const S
     const int fb = rc < 3 ? 3 + (o + 1) % 3 : (o + 1) % 3;
     const float sgn = rc < 3 ? 1.f : -1.f;
     // Item idx = pt + q * PRODUCERS is face node m of element e (idx = e * NF + m), so
-    // a warp's items are consecutive face nodes of one or two elements; in the
-    // last round the producer numbering is rotated by half, so that its items go
-    // to roles 2 and 3 first.  Tile-independent decode: e | m << 5 | f << 12 |
-    // idM << 14, bit 31 past the end.
+    // a warp's items are consecutive face nodes of one or two elements (e < E0).
     uint32_t item[D::ITEMS];
 #pragma unroll
-    for (int q = 0; q < D::ITEMS; ++q) {
-      const int idx = q < D::ITEMS - 1 ? pt + q * D::PRODUCERS
-                                       : (D::ITEMS - 1) * D::PRODUCERS +
-                                             (pt + D::PRODUCERS / 2) % D::PRODUCERS;
-      const int e = idx / NF, m = idx - e * NF;
-      item[q] = idx < E * NF ? uint32_t(e) | uint32_t(m) << 5 | uint32_t(m / Nfp) << 12 |
-                                   uint32_t(sFmask[m]) << 14
-                             : 0x80000000u;
-    }
+    for (int q = 0; q < D::ITEMS; ++q) item[q] = tc_item<N>(pt + q * D::PRODUCERS, D::E0, sFmask);
     for (int t = 0; t < ntiles; ++t) {
       const int tile = blockIdx.x + t * gridDim.x;
       const int k0 = tile * E, Ev = min(E, K - k0);
@@ -533,146 +709,17 @@ __global__ void __launch_bounds__(TcDims<N>::THREADS, 1) tc_stage_kernel(const S
       const float* sg = sG + slot * D::G_FLOATS;
       float* F = sF;
       wait_or_flag(&s_u_full[slot], (t / D::NSU) & 1, A.status);
-      // ---- fluxes (Alg. 3).  Classify every item (0 none, 1 wall, 2 neighbour in
-      // the tile, 3 neighbour outside it) and start the gathers of kind 3: the six
-      // neighbour values go by 4-byte asynchronous copies into the flux-buffer
-      // words this item's flux will overwrite (no registers, no extra space).
-      // F was last read in the build of tile t-1, before its barrier.
-      const unsigned char* nodes = reinterpret_cast<const unsigned char*>(sg + kTcGeoWords * E);
-      uint32_t info[D::ITEMS];          // kind | ofs << 2
-      const bool last_round = !D::SPLIT || role >= 2;   // this warp takes last-round items
-#pragma unroll
-      for (int q = 0; q < D::ITEMS; ++q) {
-        if (q == D::ITEMS - 1 && !last_round) {
-          info[q] = 0u;
-          continue;
-        }
-        const uint32_t it = item[q];
-        const int e = it & 31, m = (it >> 5) & 127, f = (it >> 12) & 3, idM = (it >> 14) & 63;
-        const bool ok = !(it >> 31) && e < Ev;
-        const int ec = ok ? e : 0;
-        const unsigned code = (__float_as_uint(sg[9 * E + ec]) >> (8 * f)) & 0xffu;
-        const int k2 = __float_as_int(sg[(26 + f) * E + ec]);
-        const int i2 = nodes[ec * NF + m];
-        const int e2 = k2 - k0;
-        // absorbing faces (EXT): a wall whose exterior state is zero
-        const bool absorbing = EXT && code == kAbsorbingCode;
-        const uint32_t kind = !ok ? 0u
-                              : (code == 0u || absorbing) ? 1u
-                              : unsigned(e2) < unsigned(Ev) ? 2u : 3u;
-        if (kind == 3u) {
-          const float* src = A.u_in + size_t(k2) * Np + i2;
-#pragma unroll
-          for (int c = 0; c < 6; ++c)
-            tc::cp_async4(F + (c * E + e) * FSTR + m, src + size_t(c) * K * Np);
-        }
-        info[q] = kind | uint32_t(kind == 2u ? e2 * Np + i2 : ec * Np + idM) << 2 |
-                  (absorbing ? 0x80000000u : 0u);
-      }
-      tc::cp_async_commit();
-      tc::cp_async_wait_all();
-      // upwind flux of every face node (PEC ghost state E+ = -E-, H+ = H- on walls):
-      // every item's operands are loaded before any store into the flux buffer,
-      // then items are processed two at a time in packed FP32x2 arithmetic
-      {
-        constexpr int NQ = (D::ITEMS + 1) & ~1;
-        float uM[NQ][6], up[NQ][6], nv[NQ][4];
-        float4 cf[EXT ? NQ : 1];          // EXT: Z+, B_E, Y+, B_H of the item's face
-        uint32_t kinds[NQ];
-#pragma unroll
-        for (int q = 0; q < NQ; ++q) {
-          if (q >= D::ITEMS || (q == D::ITEMS - 1 && !last_round)) {
-            kinds[q] = 0u;
-#pragma unroll
-            for (int c = 0; c < 6; ++c) uM[q][c] = up[q][c] = 0.f;
-#pragma unroll
-            for (int w = 0; w < 4; ++w) nv[q][w] = 0.f;
-            if constexpr (EXT) cf[q] = make_float4(1.f, 0.5f, 1.f, 0.5f);
-            continue;
-          }
-          const uint32_t it = item[q], kind = info[q] & 3u;
-          kinds[q] = kind;
-          const int e = kind ? int(it & 31) : 0, m = (it >> 5) & 127, f = (it >> 12) & 3;
-          const int idM = (it >> 14) & 63;
-          const float* pp = kind == 3u ? F + e * FSTR + m
-                                       : su + (EXT ? (info[q] >> 2) & 0x1FFFFFFFu : info[q] >> 2);
-          const int ps = kind == 3u ? E * FSTR : E * Np;
-          const bool zero_ext = EXT && (info[q] >> 31);          // absorbing: u+ = 0
-#pragma unroll
-          for (int c = 0; c < 6; ++c) {
-            uM[q][c] = su[c * E * Np + e * Np + idM];
-            up[q][c] = zero_ext ? 0.f : pp[c * ps];
-          }
-#pragma unroll
-          for (int w = 0; w < 4; ++w) nv[q][w] = sg[(10 + 4 * f + w) * E + e];
-          if constexpr (EXT)
-            cf[q] = A.mat && kind ? __ldg(A.mat + size_t(k0 + e) * kMatVecs + 1 + f)
-                                  : make_float4(1.f, 0.5f, 1.f, 0.5f);
-        }
-        const float2 m1 = f2(-1.f), nal = f2(-A.alpha), al = f2(A.alpha);
-#pragma unroll
-        for (int q = 0; q < NQ; q += 2) {
-          if (q >= D::ITEMS - 1 && !last_round) continue;   // a pair of last-round items only
-          const int r = q + 1;
-          auto P = [&](const float (*v)[6], int c) { return make_float2(v[q][c], v[r][c]); };
-          const float2 nwe = make_float2(kinds[q] == 1u ? 1.f : -1.f, kinds[r] == 1u ? 1.f : -1.f);
-          const float2 dEx = __ffma2_rn(nwe, P(up, 0), P(uM, 0));
-          const float2 dEy = __ffma2_rn(nwe, P(up, 1), P(uM, 1));
-          const float2 dEz = __ffma2_rn(nwe, P(up, 2), P(uM, 2));
-          const float2 dHx = __ffma2_rn(m1, P(up, 3), P(uM, 3));
-          const float2 dHy = __ffma2_rn(m1, P(up, 4), P(uM, 4));
-          const float2 dHz = __ffma2_rn(m1, P(up, 5), P(uM, 5));
-          const float2 nx = make_float2(nv[q][0], nv[r][0]), ny = make_float2(nv[q][1], nv[r][1]);
-          const float2 nz = make_float2(nv[q][2], nv[r][2]);
-          const float2 sc = __fmul2_rn(f2(0.5f), make_float2(nv[q][3], nv[r][3]));
-          // EXT: B_E (Z+ (-n x dH) + ...), B_H (Y+ (n x dE) + ...) with Fscale
-          float2 zp = f2(1.f), yp = f2(1.f), scE = sc, scH = sc;
-          if constexpr (EXT) {
-            zp = make_float2(cf[q].x, cf[r].x);
-            yp = make_float2(cf[q].z, cf[r].z);
-            scE = __fmul2_rn(make_float2(cf[q].y, cf[r].y), make_float2(nv[q][3], nv[r][3]));
-            scH = __fmul2_rn(make_float2(cf[q].w, cf[r].w), make_float2(nv[q][3], nv[r][3]));
-          }
-          const float2 mx = __fmul2_rn(m1, nx), my = __fmul2_rn(m1, ny), mz = __fmul2_rn(m1, nz);
-          const float2 aE = __fmul2_rn(al, __ffma2_rn(nz, dEz, __ffma2_rn(ny, dEy, __fmul2_rn(nx, dEx))));
-          const float2 aH = __fmul2_rn(al, __ffma2_rn(nz, dHz, __ffma2_rn(ny, dHy, __fmul2_rn(nx, dHx))));
-          // fluxE = -n x dH + alpha (n (n.dE) - dE), fluxH = n x dE + alpha (n (n.dH) - dH)
-          float2 fl[6];
-          if constexpr (!EXT) {
-            fl[0] = __ffma2_rn(nal, dEx, __ffma2_rn(nx, aE, __ffma2_rn(my, dHz, __fmul2_rn(nz, dHy))));
-            fl[1] = __ffma2_rn(nal, dEy, __ffma2_rn(ny, aE, __ffma2_rn(mz, dHx, __fmul2_rn(nx, dHz))));
-            fl[2] = __ffma2_rn(nal, dEz, __ffma2_rn(nz, aE, __ffma2_rn(mx, dHy, __fmul2_rn(ny, dHx))));
-            fl[3] = __ffma2_rn(nal, dHx, __ffma2_rn(nx, aH, __ffma2_rn(mz, dEy, __fmul2_rn(ny, dEz))));
-            fl[4] = __ffma2_rn(nal, dHy, __ffma2_rn(ny, aH, __ffma2_rn(mx, dEz, __fmul2_rn(nz, dEx))));
-            fl[5] = __ffma2_rn(nal, dHz, __ffma2_rn(nz, aH, __ffma2_rn(my, dEx, __fmul2_rn(nx, dEy))));
-          } else {
-            fl[0] = __ffma2_rn(nal, dEx, __ffma2_rn(nx, aE, __fmul2_rn(zp, __ffma2_rn(my, dHz, __fmul2_rn(nz, dHy)))));
-            fl[1] = __ffma2_rn(nal, dEy, __ffma2_rn(ny, aE, __fmul2_rn(zp, __ffma2_rn(mz, dHx, __fmul2_rn(nx, dHz)))));
-            fl[2] = __ffma2_rn(nal, dEz, __ffma2_rn(nz, aE, __fmul2_rn(zp, __ffma2_rn(mx, dHy, __fmul2_rn(ny, dHx)))));
-            fl[3] = __ffma2_rn(nal, dHx, __ffma2_rn(nx, aH, __fmul2_rn(yp, __ffma2_rn(mz, dEy, __fmul2_rn(ny, dEz)))));
-            fl[4] = __ffma2_rn(nal, dHy, __ffma2_rn(ny, aH, __fmul2_rn(yp, __ffma2_rn(mx, dEz, __fmul2_rn(nz, dEx)))));
-            fl[5] = __ffma2_rn(nal, dHz, __ffma2_rn(nz, aH, __fmul2_rn(yp, __ffma2_rn(my, dEx, __fmul2_rn(nx, dEy)))));
-          }
-#pragma unroll
-          for (int c = 0; c < 6; ++c) fl[c] = __fmul2_rn(c < 3 ? scE : scH, fl[c]);
-          if (kinds[q]) {
-            float* fr = F + int(item[q] & 31) * FSTR + int((item[q] >> 5) & 127);
-#pragma unroll
-            for (int c = 0; c < 6; ++c) fr[c * E * FSTR] = fl[c].x;
-          }
-          if (r < D::ITEMS && kinds[r]) {
-            float* fr = F + int(item[r < D::ITEMS ? r : 0] & 31) * FSTR +
-                        int((item[r < D::ITEMS ? r : 0] >> 5) & 127);
-#pragma unroll
-            for (int c = 0; c < 6; ++c) fr[c * E * FSTR] = fl[c].y;
-          }
-        }
-      }
+      // ---- fluxes (Alg. 3) of elements 0 .. E0-1 (the epilogue warps did the
+      // rest one tile ahead).  F was last read in the build of tile t-1, before
+      // its barrier.
+      tc_flux_items<N, EXT, D::ITEMS>(item, A, k0, Ev, su, sg, F, E, 0);
       // The flux buffer is complete once every producer has stored its items:
       // roles 2 and 3 (which read it) wait for that; roles 0 and 1 only signal
       // and go on with the g blocks.
-      if (role < 2) named_arrive(3, D::PRODUCERS);
-      else named_sync(3, D::PRODUCERS);
+      // (barriers 3 and 4 alternate by tile, so the epilogue threads' arrivals
+      // for tile t+1 never meet tile t's)
+      if (role < 2) named_arrive(3 + (t & 1), D::FCOUNT);
+      else named_sync(3 + (t & 1), D::FCOUNT);
       // ---- A rows of tile t
       const bool live = row < D::ROWS && re < Ev;
       const uint32_t a_hi = tbase + lane_off + buf * D::BUF_COLS;
@@ -680,7 +727,11 @@ __global__ void __launch_bounds__(TcDims<N>::THREADS, 1) tc_stage_kernel(const S
       if (role >= 2) {
         // roles 2 and 3: the first and second half of the flux block's columns
         constexpr int HC = (D::COLS_F + 1) / 2;
-        const FRow fr{F + (rc * E + re) * FSTR, sBound, t, row, live, a_hi + 3 * D::COLS_G,
+        // flux rows of elements >= E0 are in the epilogue threads' buffer
+        const float* frow = re < D::E0 ? F + (rc * E + re) * FSTR
+                                       : sF2 + (t & 1) * D::F2_FLOATS +
+                                             (rc * (E - D::E0) + re - D::E0) * FSTR;
+        const FRow fr{frow, sBound, t, row, live, a_hi + 3 * D::COLS_G,
                       a_lo + 3 * D::COLS_G, &s_mma_done[buf], A.status};
         if (role == 2)
           build_flux_half<N, 0, HC>(fr, 2);
