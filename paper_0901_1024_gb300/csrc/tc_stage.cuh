@@ -65,6 +65,10 @@ template <int N> struct TcDims {
   static_assert(2 * ACOLS + NN <= BUF_COLS, "tensor-memory buffer overflow");
   static constexpr int COLS_G = KB / 2;               // columns of one mu block
   static constexpr int COLS_F = KF / 2;               // columns of the flux block
+  // FP16 split residual by mixed-precision FMAs (fewer instructions: 1-1.5 %
+  // faster at N = 2, 3; 2.5 % slower at N = 4, where the kernel sits at its
+  // register cap)
+  static constexpr bool MIXED_SPLIT = N != 4;
   static constexpr int FSTR = NF + 2;                // flux row stride: 8-byte pair reads of
                                                       // a warp's 32 rows are conflict-free
   static constexpr int THREADS = 640;                 // 4 epilogue + 16 producer warps
@@ -131,18 +135,18 @@ __device__ __forceinline__ void tmem_store_cols(uint32_t taddr, const uint32_t* 
 // Columns [C0, C0 + NC) of one row: column p holds the pair val(p) (a float2 of
 // values 2p, 2p + 1), split into FP16 hi/lo and stored 8 columns at a time
 // (pairs are produced only as they are stored, so few registers are live).
-template <int NC, int C0 = 0, typename Val>
+template <int NC, int C0 = 0, bool MIXED = false, typename Val>
 __device__ __forceinline__ void split_store_fn(const Val& val, uint32_t t_hi, uint32_t t_lo) {
   constexpr int CH = NC < 8 ? NC : 8;
   uint32_t hi[CH], lo[CH];
 #pragma unroll
   for (int p = 0; p < CH; ++p) {
     const float2 v = val(C0 + p);
-    tc::split2(v.x, v.y, hi[p], lo[p]);
+    tc::split2<MIXED>(v.x, v.y, hi[p], lo[p]);
   }
   tmem_store_cols<CH>(t_hi + C0, hi);
   tmem_store_cols<CH>(t_lo + C0, lo);
-  if constexpr (NC > CH) split_store_fn<NC - CH, C0 + CH>(val, t_hi, t_lo);
+  if constexpr (NC > CH) split_store_fn<NC - CH, C0 + CH, MIXED>(val, t_hi, t_lo);
 }
 
 __device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
@@ -274,7 +278,7 @@ __device__ __forceinline__ void build_g_half(const GRow& g, int role) {
   for (int mu = 0; mu < 3; ++mu) {
     const float ca = g.live ? g.sgn * g.sg[(3 * mu + (g.o + 1) % 3) * E + g.re] : 0.f;
     const float cb = g.live ? -g.sgn * g.sg[(3 * mu + (g.o + 2) % 3) * E + g.re] : 0.f;
-    split_store_fn<NPH, P0>(
+    split_store_fn<NPH, P0, D::MIXED_SPLIT>(
         [&](int p) { return __ffma2_rn(f2(ca), ua[p - P0], __fmul2_rn(f2(cb), ub[p - P0])); },
         g.a_hi + mu * D::COLS_G, g.a_lo + mu * D::COLS_G);
   }
@@ -314,7 +318,7 @@ __device__ __forceinline__ void build_flux_half(const FRow& g, int role) {
   // A[buf] is free once the MMAs of tile t-2 have completed
   if (g.t >= 2) wait_or_flag(g.mma_done, ((g.t - 2) >> 1) & 1, g.status);
   tc::fence_after_sync();
-  split_store_fn<NPH, P0>([&](int p) { return __fmul2_rn(w[p - P0], f2(s)); }, g.a_hi, g.a_lo);
+  split_store_fn<NPH, P0, D::MIXED_SPLIT>([&](int p) { return __fmul2_rn(w[p - P0], f2(s)); }, g.a_hi, g.a_lo);
 }
 
 // Decode of flux item idx = e * NF + m (face node m of element e), for idx <

@@ -232,13 +232,26 @@ __device__ __forceinline__ void bulk_wait_all() {
 // (x0, x1) -> packed hi, lo with x ~= hi + lo: hi = x rounded to nearest FP16,
 // lo = x - hi (exact in FP32: hi agrees with x in all but the last bits)
 // rounded to FP16, i.e. about 22 significant bits for |x| in FP16's normal
-// range.  One conversion per pair for each piece and one packed subtraction.
+// range.  One conversion per pair for each piece; the residual either by one
+// packed FP32 FMA on hi converted back to FP32, or (MIXED) by two
+// mixed-precision FMAs hi * -1 + x with FP16 multiplicands and an FP32 addend,
+// which need no conversion back.  Both give the same bits.
+template <bool MIXED = false>
 __device__ __forceinline__ void split2(float x0, float x1, uint32_t& hi, uint32_t& lo) {
   const __half2 h = __floats2half2_rn(x0, x1);
-  const float2 hf = __half22float2(h);
-  const float2 l = __ffma2_rn(hf, make_float2(-1.f, -1.f), make_float2(x0, x1));
-  const __half2 lh = __float22half2_rn(l);
   hi = *reinterpret_cast<const uint32_t*>(&h);
+  float2 l;
+  if constexpr (MIXED) {
+    asm("{\n\t.reg .b16 h0, h1, m1;\n\t"
+        "mov.b32 {h0, h1}, %2;\n\t"
+        "mov.b16 m1, 0xBC00;\n\t"
+        "fma.rn.f32.f16 %0, h0, m1, %3;\n\t"
+        "fma.rn.f32.f16 %1, h1, m1, %4;\n\t}"
+        : "=f"(l.x), "=f"(l.y) : "r"(hi), "f"(x0), "f"(x1));
+  } else {
+    l = __ffma2_rn(__half22float2(h), make_float2(-1.f, -1.f), make_float2(x0, x1));
+  }
+  const __half2 lh = __float22half2_rn(l);
   lo = *reinterpret_cast<const uint32_t*>(&lh);
 }
 
