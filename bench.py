@@ -327,6 +327,10 @@ def run_ours(args):
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = time_oracle(w, verts, tets, budget_s=args.cpu_budget)
+        cpu["host_cores"] = os.cpu_count()
+        cpu["blas"] = "none: the oracle's contractions are numpy.einsum loops (one thread)"
+        if args.cpu_all_cores > 0:
+            cpu["all_cores"] = time_oracle_all_cores(w, verts, tets, seconds=args.cpu_all_cores)
 
     if rank == 0:
         line = {
@@ -396,6 +400,62 @@ def time_oracle(w, verts, tets, budget_s=15.0, layers=None, steps=None):
             "sample": f"{done} LSERK4 step(s) on the first {layers} z-layer(s) of hexes "
                       f"({om.K} of {len(tets)} tets) of the same mesh, FP64 NumPy oracle "
                       f"(single-threaded einsum), {el:.1f} s"}
+
+
+def _oracle_process(job):
+    """One process of the all-cores oracle timing: builds the sample mesh and
+    steps it for about `seconds`; returns (DOF-updates, seconds taken)."""
+    w, verts, tets, seconds = job
+    import oracle
+    om = oracle.build_mesh(verts, tets, w["N"])
+    u = initial_fields(w, np.stack([om.x, om.y, om.z]))
+    dt = oracle.cfl_dt(om)
+    res = np.zeros_like(u)
+    t0 = time.perf_counter()
+    done = 0
+    while True:
+        u, res = oracle.lserk4_run(om, u, dt, 1, res)
+        done += 1
+        el = time.perf_counter() - t0
+        if el >= seconds or done >= 200:
+            break
+    return 6 * om.K * om.Np * 5 * done, el
+
+
+def time_oracle_all_cores(w, verts, tets, seconds=10.0, layers=1, procs=None):
+    """The FP64 oracle on every host core: one spawned process per core, each
+    stepping its own copy of the same bounded sample (independent solves, as
+    in the multi-GPU benchmark); the value is the sum of the processes' rates.
+    A child that dies or overruns turns into an "error" entry, never a hang."""
+    import concurrent.futures as cf
+    import multiprocessing as mp
+    procs = procs or os.cpu_count() or 1
+    Ks = 6 * w["n"] * w["n"] * layers
+    Np = (w["N"] + 1) * (w["N"] + 2) * (w["N"] + 3) // 6
+    keys = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")
+    saved = {k: os.environ.get(k) for k in keys}
+    os.environ.update({k: "1" for k in keys})       # one thread per child
+    ex = cf.ProcessPoolExecutor(procs, mp_context=mp.get_context("spawn"))
+    try:
+        futs = [ex.submit(_oracle_process, (w, verts, tets[:Ks], seconds)) for _ in range(procs)]
+        out = [f.result(timeout=4 * seconds + 120) for f in futs]
+    except Exception as err:                         # broken pool, timeout
+        for p in list(getattr(ex, "_processes", {}).values()):
+            p.kill()
+        ex.shutdown(wait=False, cancel_futures=True)
+        return {"error": f"{type(err).__name__}: {err}"[:200], "cores": procs}
+    finally:
+        for k, v in saved.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+    ex.shutdown()
+    steps = sum(d for d, _ in out) // (6 * Ks * Np * 5)
+    return {"value": sum(d / e for d, e in out), "unit": METRIC, "cores": procs, "kind": "oracle",
+            "sample": f"{procs} processes (one per host core), each stepping its own copy of the "
+                      f"first {layers} z-layer(s) of hexes ({Ks} tets) for ~{seconds:.0f} s; "
+                      f"{steps} LSERK4 steps in all"}
 
 
 def run_reference(args):
@@ -597,6 +657,8 @@ def main():
     ap.add_argument("--no-accuracy", action="store_true",
                     help="skip the 200-step comparison of the default and the plain FP32 path")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--cpu-all-cores", type=float, default=10.0,
+                    help="seconds of the all-cores oracle timing (0: skip)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)          # at least 3 untimed warm-up steps
     if args.impl == "reference":

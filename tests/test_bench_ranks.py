@@ -63,3 +63,14 @@ def test_reference_arm_prints_on_rank_zero_only(monkeypatch, capsys):
         workload, steps, warmup = "pulse_n24_N4", 1, 3
     assert bench.run_reference(Args()) is None
     assert capsys.readouterr().out == ""
+
+
+def test_all_cores_oracle_timing_sums_independent_processes():
+    """The all-cores oracle baseline: two spawned processes, each stepping its
+    own copy of a one-layer sample of the 384-tet cavity mesh; the value is
+    the sum of their rates and the sample names the step count."""
+    w, verts, tets = bench.workload_inputs("cavity_n4_N3")
+    r = bench.time_oracle_all_cores(w, verts, tets, seconds=0.5, procs=2)
+    assert "error" not in r, r
+    assert r["cores"] == 2 and r["kind"] == "oracle" and r["value"] > 0
+    assert "96 tets" in r["sample"]
