@@ -164,3 +164,21 @@ def test_absorbing_box_lets_a_pulse_leave():
     up, _ = oracle.lserk4_run(om, u0, dt, steps)
     assert oracle.energy(om, ua) < 0.02 * e0
     assert oracle.energy(om, up) > 0.5 * e0
+
+
+def test_material_energy_of_elementwise_constant_fields():
+    """For fields constant on each element the energy is the exact integral
+    1/2 sum_k vol_k (eps_k |E_k|^2 + mu_k |H_k|^2), with each volume taken from
+    the vertices (|det| / 6), not from J or the mass matrix.  Swapped or
+    missing eps, mu weights, or a lost factor 1/2, fail it."""
+    verts, tets = kuhn_box_mesh(2, 0.15, 4)
+    om = oracle.build_mesh(verts, tets, 3)
+    rng = np.random.default_rng(17)
+    eps = rng.uniform(0.5, 4.0, om.K)
+    mu = rng.uniform(0.5, 3.0, om.K)
+    E, H = rng.standard_normal((3, om.K)), rng.standard_normal((3, om.K))
+    u = np.concatenate([E, H])[:, :, None] * np.ones(om.Np)
+    X = verts[om.tets]
+    vol = np.abs(np.linalg.det(np.stack([X[:, 1] - X[:, 0], X[:, 2] - X[:, 0], X[:, 3] - X[:, 0]], 1))) / 6
+    want = 0.5 * np.sum(vol * (eps * np.sum(E ** 2, 0) + mu * np.sum(H ** 2, 0)))
+    assert abs(oracle.energy(om, u, eps, mu) - want) < 1e-12 * want

@@ -1,0 +1,174 @@
+"""Planted mistakes in the oracle, caught by its pins (CPU only).
+
+Each case below is a plausible slip in one oracle module: a dropped term, a
+wrong sign, a transposed or swapped operand, a wrong weight, a wrong
+constant.  The case builds a mutant of that module from its own source with
+exactly that one substitution, swaps the mutant's functions in for the real
+ones wherever the oracle package refers to them, and runs a named pin from
+tests/test_oracle_*.py.  The pin must fail with an AssertionError.  The pins
+compare against closed forms, exact solutions, energy identities and the
+paper's own flux form, never against the oracle code itself, so a mistake
+that none of them notices would show up here as a surviving mutant.
+"""
+import importlib.util
+import os
+import types
+
+import pytest
+
+import oracle
+import oracle.maxwell
+import oracle.mesh
+import oracle.partition
+import oracle.refelem
+from workloads import kuhn_box_mesh
+
+TESTS = os.path.dirname(os.path.abspath(__file__))
+ORACLE = os.path.join(os.path.dirname(TESTS), "oracle")
+
+
+def _pin_module(name):
+    spec = importlib.util.spec_from_file_location(f"_pins_{name}", os.path.join(TESTS, name + ".py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    return mod
+
+
+PINS = {n: _pin_module(n) for n in ("test_oracle_maxwell", "test_oracle_materials",
+                                     "test_oracle_mesh", "test_oracle_refelem",
+                                     "test_oracle_partition")}
+
+# (id, oracle module, exact source text, replacement, pin module, pin, pin arguments)
+CASES = [
+    ("curl-H-component-sign", "maxwell", "curlH = np.stack([dy[5] - dz[4],",
+     "curlH = np.stack([dz[4] - dy[5],",
+     "test_oracle_maxwell", "test_rhs_exact_curl_on_interior_elements", {"N": 2}),
+    ("minus-curl-E-dropped", "maxwell", "return np.concatenate([curlH, -curlE])",
+     "return np.concatenate([curlH, curlE])",
+     "test_oracle_maxwell", "test_rhs_exact_curl_on_interior_elements", {"N": 2}),
+    ("metric-transposed-in-d/dx", "maxwell",
+     "dx = c(mesh.rx) * ur + c(mesh.sx) * us + c(mesh.tx) * ut",
+     "dx = c(mesh.rx) * ur + c(mesh.ry) * us + c(mesh.rz) * ut",
+     "test_oracle_maxwell", "test_rhs_exact_curl_on_interior_elements", {"N": 2}),
+    ("Ds-used-for-Dt", "maxwell", 'ut = np.einsum("ij,fkj->fki", ref.Dt, u)',
+     'ut = np.einsum("ij,fkj->fki", ref.Ds, u)',
+     "test_oracle_maxwell", "test_rhs_exact_curl_on_interior_elements", {"N": 2}),
+    ("PEC-ghost-E-not-mirrored", "maxwell",
+     "uP[:3] = np.where(pec[None, :, :, None], -uM[:3], uP[:3])",
+     "uP[:3] = np.where(pec[None, :, :, None], uM[:3], uP[:3])",
+     "test_oracle_maxwell", "test_upwind_flux_two_tets_by_hand", {"N": 1}),
+    ("upwind-penalty-sign", "maxwell", "(zp * nxjH[i] - alpha * nxnxjE[i])",
+     "(zp * nxjH[i] + alpha * nxnxjE[i])",
+     "test_oracle_maxwell", "test_energy_rate_central_zero_upwind_dissipative", {}),
+    ("jump-taken-the-other-way", "maxwell", "jE = uP[:3] - uM[:3]", "jE = uM[:3] - uP[:3]",
+     "test_oracle_maxwell", "test_energy_rate_central_zero_upwind_dissipative", {}),
+    ("Fscale-dropped", "maxwell", "flux = np.stack(fE + fH) * mesh.Fscale[None, :, :, None]",
+     "flux = np.stack(fE + fH)",
+     "test_oracle_maxwell", "test_upwind_flux_two_tets_by_hand", {"N": 1}),
+    ("Z-minus-for-Z-plus-in-E-row", "maxwell", "fE = [cE * (zp * nxjH[i]",
+     "fE = [cE * (ZM[:, :, None] * nxjH[i]",
+     "test_oracle_materials", "test_material_upwind_flux_is_the_exact_riemann_flux", {"N": 1}),
+    ("Y-average-misweighted", "maxwell", "cH = (1.0 / (YM + YP))[:, :, None]",
+     "cH = (1.0 / (ZM + ZP))[:, :, None]",
+     "test_oracle_materials", "test_material_energy_conserved_by_central_flux_and_dissipated_by_upwind",
+     {"N": 2}),
+    ("1/eps-weight-dropped", "maxwell", "np.repeat(1.0 / eps[None, :], 3, axis=0)",
+     "np.repeat(np.ones_like(eps)[None, :], 3, axis=0)",
+     "test_oracle_materials", "test_material_energy_conserved_by_central_flux_and_dissipated_by_upwind",
+     {"N": 2}),
+    ("absorbing-face-treated-as-wall", "maxwell", "uP = np.where(absorb[None, :, :, None], 0.0, uP)",
+     "uP = np.where(absorb[None, :, :, None], uP, uP)",
+     "test_oracle_materials", "test_material_upwind_flux_is_the_exact_riemann_flux", {"N": 1}),
+    ("dt-dropped-in-stage", "maxwell", "res = a * res + dt * r", "res = a * res + r",
+     "test_oracle_maxwell", "test_energy_non_increasing_and_conserved_direction", {}),
+    ("RK-coefficient-digit", "maxwell", "Fraction(5161836677717, 13612068292357)",
+     "Fraction(5161836677718, 13612068292357)",
+     "test_oracle_maxwell", "test_lserk4_order_conditions_exact", {}),
+    ("energy-half-dropped", "maxwell", "return 0.5 * float(np.sum(", "return float(np.sum(",
+     "test_oracle_maxwell", "test_energy_non_increasing_and_conserved_direction", {}),
+    ("energy-mu-weight-on-E", "maxwell",
+     "w = np.concatenate([np.repeat(eps[None, :], 3, axis=0), np.repeat(mu[None, :], 3, axis=0)])",
+     "w = np.concatenate([np.repeat(mu[None, :], 3, axis=0), np.repeat(eps[None, :], 3, axis=0)])",
+     "test_oracle_materials", "test_material_energy_of_elementwise_constant_fields", {}),
+    ("CFL-wave-speed", "maxwell", "slow = np.sqrt(eps * mu)[:, None]", "slow = np.sqrt(eps / mu)[:, None]",
+     "test_oracle_materials", "test_material_scaling_law", {}),
+    ("metric-row-transposed", "mesh",
+     "m.rx, m.ry, m.rz = inv[:, 0, 0], inv[:, 0, 1], inv[:, 0, 2]",
+     "m.rx, m.ry, m.rz = inv[:, 0, 0], inv[:, 1, 0], inv[:, 2, 0]",
+     "test_oracle_maxwell", "test_rhs_exact_curl_on_interior_elements", {"N": 2}),
+    ("normals-inward", "mesh", "n[out < 0] *= -1", "n[out > 0] *= -1",
+     "test_oracle_maxwell", "test_energy_rate_central_zero_upwind_dissipative", {}),
+    ("face-jacobian-not-halved", "mesh", "m.sJ = area / 2", "m.sJ = area",
+     "test_oracle_mesh", "test_face_geometry", {"mesh3": None}),
+    ("jacobian-scaled", "mesh", "m.J = np.linalg.det(A)  ", "m.J = 8 * np.linalg.det(A)  ",
+     "test_oracle_mesh", "test_volumes_and_jacobians", {"mesh3": None}),
+    ("Dr-from-s-derivative", "refelem", "self.Dr = Vr @ Vinv", "self.Dr = Vs @ Vinv",
+     "test_oracle_refelem", "test_differentiation_exact_on_polynomials", {"N": 2}),
+    ("mass-quadrature-too-low", "refelem", "qr, qs, qt, qw = tet_quadrature(N + 2)",
+     "qr, qs, qt, qw = tet_quadrature(N)",
+     "test_oracle_refelem", "test_mass_matrix_integrates_products_exactly", {"N": 3}),
+    ("LIFT-without-inverse-mass", "refelem", "self.LIFT = self.Minv @ E", "self.LIFT = E",
+     "test_oracle_maxwell", "test_upwind_flux_two_tets_by_hand", {"N": 1}),
+    ("greedy-ties-to-last-queued", "partition",
+     "if shared.get(queue[i], 0) > shared.get(queue[best], 0):",
+     "if shared.get(queue[i], 0) >= shared.get(queue[best], 0):",
+     "test_oracle_partition", "test_first_grid_block_in_queue_order", {}),
+    ("shared-faces-not-counted", "partition", "shared[f] = shared.get(f, 0) + 1", "shared[f] = 1",
+     "test_oracle_partition", "test_grid_and_mesh_follow_the_greedy_rule", {}),
+    ("next-seed-from-queue-end", "partition", "carry = queue[0] if queue else None",
+     "carry = queue[-1] if queue else None",
+     "test_oracle_partition", "test_next_block_seeded_by_the_first_queue_entry", {}),
+]
+
+
+def _mutant(modname, old, new):
+    path = os.path.join(ORACLE, modname + ".py")
+    src = open(path).read()
+    assert src.count(old) == 1, f"mutation site not unique or gone: {old!r}"
+    mod = types.ModuleType(f"oracle._mutant_{modname}")
+    mod.__package__ = "oracle"
+    mod.__file__ = path
+    exec(compile(src.replace(old, new), path, "exec"), mod.__dict__)
+    return mod
+
+
+def _install(monkeypatch, modname, mutant):
+    """Every name that refers to an object of the real module (its own
+    namespace, the package's re-exports, other modules' `from .x import y`,
+    the pin modules' imports) is pointed at the mutant's object of that name."""
+    real = getattr(oracle, modname)
+    swap = {id(v): getattr(mutant, k) for k, v in vars(real).items()
+            if not k.startswith("__") and hasattr(mutant, k)
+            and (isinstance(v, (types.FunctionType, type)) or hasattr(v, "cache_info"))}
+    for m in (oracle, oracle.maxwell, oracle.mesh, oracle.partition, oracle.refelem,
+              *PINS.values()):
+        for k, v in list(vars(m).items()):
+            if id(v) in swap:
+                monkeypatch.setattr(m, k, swap[id(v)])
+
+
+@pytest.mark.parametrize("case", CASES, ids=[c[0] for c in CASES])
+def test_planted_mistake_is_caught(case, monkeypatch):
+    _, modname, old, new, pin_mod, pin, kwargs = case
+    _install(monkeypatch, modname, _mutant(modname, old, new))
+    kwargs = dict(kwargs)
+    if "mesh3" in kwargs:                      # the pin's module fixture, built by the mutant
+        verts, tets = kuhn_box_mesh(3, 0.15, 0)
+        kwargs["mesh3"] = (oracle.build_mesh(verts, tets, 3), verts)
+    with pytest.raises(AssertionError):
+        getattr(PINS[pin_mod], pin)(**kwargs)
+
+
+def test_unmutated_oracle_passes_the_same_pins():
+    """The harness itself: with no mutation every pin used above passes."""
+    seen = set()
+    for _, _, _, _, pin_mod, pin, kwargs in CASES:
+        key = (pin_mod, pin, tuple(sorted(kwargs)))
+        if key in seen:
+            continue
+        seen.add(key)
+        kwargs = dict(kwargs)
+        if "mesh3" in kwargs:
+            verts, tets = kuhn_box_mesh(3, 0.15, 0)
+            kwargs["mesh3"] = (oracle.build_mesh(verts, tets, 3), verts)
+        getattr(PINS[pin_mod], pin)(**kwargs)

@@ -53,6 +53,16 @@ def test_first_grid_block_in_queue_order():
     assert greedy_partition(grid_neighbours(4), 4)[0] == [0, 4, 1, 5]
 
 
+def test_next_block_seeded_by_the_first_queue_entry():
+    """4 x 4 grid, blocks of 4, worked by hand: block one (0, 4, 1, 5) leaves
+    the queue as (8, 2), element 0 having been taken again and skipped; the
+    next block grows from the queue's first entry, 8: then 12 (tied with 9 at
+    one shared face, queued first), 9, and 13 (two shared faces)."""
+    blocks = greedy_partition(grid_neighbours(4), 4)
+    assert blocks[0] == [0, 4, 1, 5]
+    assert blocks[1] == [8, 12, 9, 13]
+
+
 def check_greedy_choices(nb, blocks):
     """Every element after a block's first is, at the moment it is placed,
     adjacent to the block and shares a maximal number of faces with it among the
