@@ -109,6 +109,16 @@ CASES = [
      "test_oracle_refelem", "test_mass_matrix_integrates_products_exactly", {"N": 3}),
     ("LIFT-without-inverse-mass", "refelem", "self.LIFT = self.Minv @ E", "self.LIFT = E",
      "test_oracle_maxwell", "test_upwind_flux_two_tets_by_hand", {"N": 1}),
+    ("face-mass-on-the-next-face", "refelem", "fr, fs, ft = face_points(f, pp, pq)",
+     "fr, fs, ft = face_points((f + 1) % 4, pp, pq)",
+     "test_oracle_refelem", "test_face_mass_integrates_exactly", {"N": 2}),
+    ("face-order-s-and-t-swapped", "refelem",
+     "on_face = (np.abs(1 + t) < tol, np.abs(1 + s) < tol,",
+     "on_face = (np.abs(1 + s) < tol, np.abs(1 + t) < tol,",
+     "test_oracle_refelem", "test_fmask_faces", {}),
+    ("neighbour-node-off-by-one", "mesh", "vmapP[k, f] = k2 * Np + idP[j2]",
+     "vmapP[k, f] = k2 * Np + idP[(j2 + 1) % Nfp]",
+     "test_oracle_mesh", "test_connectivity_invariants", {"N": 2}),
     ("greedy-ties-to-last-queued", "partition",
      "if shared.get(queue[i], 0) > shared.get(queue[best], 0):",
      "if shared.get(queue[i], 0) >= shared.get(queue[best], 0):",
