@@ -2,8 +2,8 @@
 ranks: plan invariants, and 2- and 3-rank gloo runs whose per-rank stage is the
 FP64 oracle's LSERK4 stage on the rank's local mesh.  After the per-stage
 trace exchange every owned element must follow the single-domain oracle run.
-(The CUDA path runs the same driver with dg_rk_stage per rank; this pool gives
-one GPU per run, so the multi-rank path is tested here.)"""
+(The CUDA path runs the same stepping loop with dg_rk_stage on each rank's
+GPU; the multi-rank exchange itself is exercised here, on CPU ranks.)"""
 import os
 import socket
 
