@@ -380,11 +380,10 @@ def oracle_sample(w, verts, tets, layers):
     return om, u0
 
 
-def time_oracle(w, verts, tets, budget_s=15.0, layers=None, steps=None):
-    """Times the FP64 oracle's LSERK4 steps on a bounded sample of the workload."""
+def _run_oracle(om, u, budget_s, steps=None, cap=50):
+    """Steps the oracle's LSERK4 from u for `steps` steps, or until about
+    budget_s seconds (at most `cap` steps); returns (steps done, seconds)."""
     import oracle
-    layers = layers or 2
-    om, u = oracle_sample(w, verts, tets, layers)
     dt = oracle.cfl_dt(om)
     res = np.zeros_like(u)
     t0 = time.perf_counter()
@@ -393,8 +392,15 @@ def time_oracle(w, verts, tets, budget_s=15.0, layers=None, steps=None):
         u, res = oracle.lserk4_run(om, u, dt, 1, res)
         done += 1
         el = time.perf_counter() - t0
-        if (steps and done >= steps) or (not steps and (el >= budget_s or done >= 50)):
-            break
+        if (steps and done >= steps) or (not steps and (el >= budget_s or done >= cap)):
+            return done, el
+
+
+def time_oracle(w, verts, tets, budget_s=15.0, layers=None, steps=None):
+    """Times the FP64 oracle's LSERK4 steps on a bounded sample of the workload."""
+    layers = layers or 2
+    om, u = oracle_sample(w, verts, tets, layers)
+    done, el = _run_oracle(om, u, budget_s, steps)
     dof = 6 * om.K * om.Np * 5 * done
     return {"value": dof / el, "unit": METRIC, "cores": 1, "kind": "oracle",
             "sample": f"{done} LSERK4 step(s) on the first {layers} z-layer(s) of hexes "
@@ -405,20 +411,9 @@ def time_oracle(w, verts, tets, budget_s=15.0, layers=None, steps=None):
 def _oracle_process(job):
     """One process of the all-cores oracle timing: builds the sample mesh and
     steps it for about `seconds`; returns (DOF-updates, seconds taken)."""
-    w, verts, tets, seconds = job
-    import oracle
-    om = oracle.build_mesh(verts, tets, w["N"])
-    u = initial_fields(w, np.stack([om.x, om.y, om.z]))
-    dt = oracle.cfl_dt(om)
-    res = np.zeros_like(u)
-    t0 = time.perf_counter()
-    done = 0
-    while True:
-        u, res = oracle.lserk4_run(om, u, dt, 1, res)
-        done += 1
-        el = time.perf_counter() - t0
-        if el >= seconds or done >= 200:
-            break
+    w, verts, tets, layers, seconds = job
+    om, u = oracle_sample(w, verts, tets, layers)
+    done, el = _run_oracle(om, u, seconds, cap=200)
     return 6 * om.K * om.Np * 5 * done, el
 
 
@@ -437,7 +432,7 @@ def time_oracle_all_cores(w, verts, tets, seconds=10.0, layers=1, procs=None):
     os.environ.update({k: "1" for k in keys})       # one thread per child
     ex = cf.ProcessPoolExecutor(procs, mp_context=mp.get_context("spawn"))
     try:
-        futs = [ex.submit(_oracle_process, (w, verts, tets[:Ks], seconds)) for _ in range(procs)]
+        futs = [ex.submit(_oracle_process, (w, verts, tets, layers, seconds)) for _ in range(procs)]
         out = [f.result(timeout=4 * seconds + 120) for f in futs]
     except Exception as err:                         # broken pool, timeout
         for p in list(getattr(ex, "_processes", {}).values()):
