@@ -327,7 +327,7 @@ def run_ours(args):
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = time_oracle(w, verts, tets, budget_s=args.cpu_budget)
-        cpu["host_cores"] = os.cpu_count()
+        cpu["host_cores"] = usable_cores()
         cpu["blas"] = "none: the oracle's contractions are numpy.einsum loops (one thread)"
         if args.cpu_all_cores > 0:
             cpu["all_cores"] = time_oracle_all_cores(w, verts, tets, seconds=args.cpu_all_cores)
@@ -417,14 +417,22 @@ def _oracle_process(job):
     return 6 * om.K * om.Np * 5 * done, el
 
 
+def usable_cores():
+    """Cores this process may run on (its affinity mask where the OS has one)."""
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
 def time_oracle_all_cores(w, verts, tets, seconds=10.0, layers=1, procs=None):
-    """The FP64 oracle on every host core: one spawned process per core, each
+    """The FP64 oracle on every usable host core: one spawned process per core, each
     stepping its own copy of the same bounded sample (independent solves, as
     in the multi-GPU benchmark); the value is the sum of the processes' rates.
     A child that dies or overruns turns into an "error" entry, never a hang."""
     import concurrent.futures as cf
     import multiprocessing as mp
-    procs = procs or os.cpu_count() or 1
+    procs = procs or usable_cores()
     Ks = 6 * w["n"] * w["n"] * layers
     Np = (w["N"] + 1) * (w["N"] + 2) * (w["N"] + 3) // 6
     keys = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")
