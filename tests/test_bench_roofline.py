@@ -2,6 +2,8 @@
 flops per element and RK stage, built here from their parts, and the
 per-order table they give (bytes / flops per element for N = 1..9, and
 289.6 MB per stage on the 82 944-tet N = 4 workload)."""
+import os
+
 import pytest
 
 import bench
@@ -48,3 +50,27 @@ def test_per_order_table(N, bytes_, flops):
 def test_headline_workload_bytes():
     Np, _ = _dofs(4)
     assert bench.stage_bytes_per_elem(Np) * 82944 == 289_640_448
+
+
+@pytest.mark.parametrize("workload,family", [("pulse_n24_N4", "tc"), ("cavity_n16_N6", "tt")])
+def test_stage_profiles_are_machine_readable(workload, family):
+    """The committed ncu summary of each benchmark workload carries the source
+    digest of the kernel family it measured and the DRAM bytes per launch; the
+    bench reports those bytes only while the digest matches the source."""
+    import os
+    import re
+    text = open(os.path.join(bench.ROOT, "profiles", f"stage_kernel_{workload}.md")).read()
+    digest = re.search(r"kernel_source_digest:\s*([0-9a-f]{16})\b", text)
+    traffic = re.search(r"dram_bytes_per_launch:\s*([0-9]+)\b", text)
+    assert digest and traffic and int(traffic.group(1)) > 0
+    got = bench.profiled_traffic(workload, family)
+    fresh = digest.group(1) == bench.kernel_source_digest(family)
+    assert got == (float(traffic.group(1)) if fresh else None)
+
+
+def test_kernel_family_of_each_stage_path():
+    assert [bench.kernel_family(N, True) for N in range(1, 7)] == ["tc"] * 4 + ["tt"] * 2
+    assert {bench.kernel_family(N, False) for N in range(1, 10)} == {"fp32"}
+    for files in bench.KERNEL_SOURCES.values():
+        for f in files:
+            assert os.path.exists(os.path.join(bench.ROOT, "paper_0901_1024_gb300", "csrc", f))
