@@ -3,6 +3,7 @@ flops per element and RK stage, built here from their parts, and the
 per-order table they give (bytes / flops per element for N = 1..9, and
 289.6 MB per stage on the 82 944-tet N = 4 workload)."""
 import os
+import re
 
 import pytest
 
@@ -57,8 +58,6 @@ def test_stage_profiles_are_machine_readable(workload, family):
     """The committed ncu summary of each benchmark workload carries the source
     digest of the kernel family it measured and the DRAM bytes per launch; the
     bench reports those bytes only while the digest matches the source."""
-    import os
-    import re
     text = open(os.path.join(bench.ROOT, "profiles", f"stage_kernel_{workload}.md")).read()
     digest = re.search(r"kernel_source_digest:\s*([0-9a-f]{16})\b", text)
     traffic = re.search(r"dram_bytes_per_launch:\s*([0-9]+)\b", text)
