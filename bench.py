@@ -87,6 +87,12 @@ def flops_per_elem_stage(N, Np, Nfp):
     return 36 * Np * Np + 66 * Np + 60 * 4 * Nfp + 12 * Np * 4 * Nfp + 6 * Np + 30 * Np
 
 
+def fp32_peak_tflops(sms: int, peaks: dict) -> float:
+    """FP32 FMA peak in TFLOP/s: SMs (queried from the device) x 128 FP32 lanes x
+    2 flop x the maximum SM clock (MEASURED_PEAKS.json, else 2070 MHz)."""
+    return sms * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+
+
 def load_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -144,7 +150,7 @@ class ClockSampler:
         self.p = None
         try:
             self.p = subprocess.Popen(["nvidia-smi", f"--id={index}", f"--query-gpu={self.Q}",
-                                       "--format=csv,noheader,nounits", "-lms", "50"],
+                                       "--format=csv,noheader,nounits", "-lms", "20"],
                                       stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except (OSError, ValueError):
             return
@@ -298,7 +304,8 @@ def run_ours(args):
     achieved = algo_bytes / avg_stage_s / 1e9
     traffic = profiled_traffic(args.workload, kernel_family(w["N"], tc_path))
     flops = flops_per_elem_stage(w["N"], Np, Nfp) * K
-    fp32_peak = 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12   # TFLOP/s, FP32 FMA
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    fp32_peak = fp32_peak_tflops(sms, peaks)
 
     e2e = None
     if not args.no_e2e:
@@ -356,7 +363,8 @@ def run_ours(args):
                          else "fallback 6.8 TB/s"},
             "fp32_alu": {"achieved_tflops": flops / avg_stage_s / 1e12, "peak_tflops": fp32_peak,
                          "frac": flops / avg_stage_s / 1e12 / fp32_peak,
-                         "peak_derivation": "152 SMs x 128 FP32 lanes x 2 flop x sm_max_mhz"},
+                         "peak_derivation": f"{sms} SMs (device query) x 128 FP32 lanes x 2 flop "
+                                            "x sm_max_mhz"},
             "gflops": flops * 5 * args.steps / (ms * 1e-3) / 1e9 * world,
             "energy": energy,
             "clocks": clocks,
@@ -598,7 +606,8 @@ def run_sweep(args):
     import torch
     import paper_0901_1024_gb300 as dg
     peaks, _ = load_peaks()
-    fp32_peak = 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    fp32_peak = fp32_peak_tflops(sms, peaks)
     rows = []
     for N in range(1, 10):
         Np, Nfp = (N + 1) * (N + 2) * (N + 3) // 6, (N + 1) * (N + 2) // 2

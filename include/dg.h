@@ -263,10 +263,28 @@ int dg_energy_range(dg_mesh* mesh, const float* u, int64_t k0, int64_t k1, doubl
  *   res : host RK register, [6][K][Np] FP32, in/out, or NULL: then only u
  *         crosses the bus and the device register starts from zero (a step's
  *         result does not depend on it: the first LSERK4 stage has a = 0).
- * Uses library-owned device buffers; synchronises `stream`.
+ * Uses library-owned device buffers; synchronises `stream`.  With the energy
+ * check on (dg_set_energy_check) it also computes the energy of the incoming
+ * state and returns DG_ERR_UNSTABLE, after copying the fields back and
+ * writing *energy, if the energy grew by more than the allowed factor.
  */
 int dg_step_host(dg_mesh* mesh, float* u, float* res, double dt, int nsteps,
                  double* energy, void* stream);
+
+/*
+ * Instability detector for dg_step_host (the paper has no counterpart; a
+ * library service).  With upwind or central flux and perfect-conductor or
+ * absorbing boundaries the discrete energy of a stable run does not grow
+ * (Section 6's dissipative upwind flux; LSERK4 inside its stability region),
+ * so growth flags a time step above the stability limit or a corrupted state.
+ *   max_growth >= 0: dg_step_host computes E_in (the incoming state) and
+ *                    E_out (the result) and fails with DG_ERR_UNSTABLE when
+ *                    E_out > E_in (1 + max_growth) or E_out is not finite;
+ *                    about 1e-6 per step covers FP32 rounding;
+ *   max_growth <  0: off (the default).
+ * Costs one more energy evaluation and host synchronisation per call.  Host
+ * only.  Errors: DG_ERR_ARG (NULL mesh, NaN). */
+int dg_set_energy_check(dg_mesh* mesh, double max_growth);
 
 /* Number of kernel launches the last dg_rhs / dg_step / dg_energy /
  * dg_step_host call on this mesh issued (for launch accounting). */
@@ -310,9 +328,16 @@ int dg_trace_read(dg_mesh* mesh, double* ms, int32_t* kind, int64_t cap, int64_t
  * 4 194 304 tetrahedra (DG_ERR_ARG otherwise).  The mesh must already be on
  * the current device (one earlier dg_rhs, dg_step or dg_energy call on it,
  * else DG_ERR_STATE), because uploading it would allocate.  The first call on
- * a device looks up that device's address of the array; make that first call
- * before any stream capture.  Asynchronous on `stream`; no host sync.  All
- * calls share the array: calls that overlap on the GPU race on it.
+ * a device looks up that device's address of the array (again after the
+ * device's context has been replaced, e.g. by cudaDeviceReset); with lazy
+ * module loading that first lookup loads the library's device code and with it
+ * the array, so the first call is not itself free of allocation: make it
+ * during set-up, before any stream capture.  Asynchronous on `stream`; no host
+ * sync, and unlike dg_energy it reads no pipeline status word and does not
+ * check the energy for finiteness: callers check the result themselves (e.g.
+ * isfinite after their own copy, or a dg_energy call).  While tracing is on
+ * (dg_trace_enable) its two launches are recorded as kinds 2 and 3.  All calls
+ * share the array: calls that overlap on the GPU race on it.
  */
 int dg_energy_noalloc(dg_mesh* mesh, const float* u, double* energy, void* stream);
 

@@ -138,6 +138,11 @@ class Mesh:
         """0 = auto (tensor cores for N = 2..6), 1 = FP32 CUDA cores, 2 = tensor cores."""
         check(self._lib.dg_set_stage_impl(self._h, int(impl)), "dg_set_stage_impl")
 
+    def set_energy_check(self, max_growth: float):
+        """dg_set_energy_check: step_host fails with DG_ERR_UNSTABLE when the
+        energy grows by more than the factor 1 + max_growth (< 0: off)."""
+        check(self._lib.dg_set_energy_check(self._h, float(max_growth)), "dg_set_energy_check")
+
     def nodes(self) -> np.ndarray:
         out = np.empty((3, self.K, self.Np), np.float64)
         check(self._lib.dg_nodes(self._h, _dptr(out, np.float64)), "dg_nodes")

@@ -318,6 +318,13 @@ int dg_set_flux(dg_mesh* m, double alpha) {
   return DG_OK;
 }
 
+int dg_set_energy_check(dg_mesh* m, double max_growth) {
+  if (int rc = check_mesh(m, false)) return rc;
+  if (std::isnan(max_growth)) return fail(DG_ERR_ARG, "max_growth is NaN");
+  m->energy_check = max_growth;
+  return DG_OK;
+}
+
 int dg_set_stage_impl(dg_mesh* m, int impl) {
   if (int rc = check_mesh(m, false)) return rc;
   if (impl != DG_STAGE_AUTO && impl != DG_STAGE_FP32 && impl != DG_STAGE_TC)

@@ -4,6 +4,7 @@
 #include <cstdint>
 #include <initializer_list>
 #include <cmath>
+#include <cstdio>
 #include <cstring>
 #include <string>
 #include <map>
@@ -384,6 +385,11 @@ static cudaError_t traced(dg_mesh* m, cudaStream_t s, int kind, F&& fn) {
 }
 
 int ensure_device(dg_mesh* m, std::string& err);
+
+int trace_launch(dg_mesh* m, void* stream, int kind, int (*launch)(void*), void* ctx) {
+  return static_cast<int>(traced(m, static_cast<cudaStream_t>(stream), kind,
+                                 [&] { return static_cast<cudaError_t>(launch(ctx)); }));
+}
 
 int device_trace_reset(dg_mesh* m, int reserve, std::string& err) {
   int rc = ensure_device(m, err);
@@ -856,13 +862,32 @@ int device_step_host(dg_mesh* m, float* u, float* res, double dt, int nsteps, do
   // LSERK4 stage has a = 0, so a step's result does not depend on it)
   if (res) DG_CUDA(cudaMemcpyAsync(d->h_res, res, bytes, cudaMemcpyHostToDevice, s), "cudaMemcpyAsync H2D");
   else DG_CUDA(cudaMemsetAsync(d->h_res, 0, bytes, s), "cudaMemsetAsync");
+  // energy-growth check (opt-in): the energy of the incoming state first
+  const bool check = m->energy_check >= 0.0;
+  double e_in = 0.0;
+  int64_t launches = 0;
+  if (check) {
+    if ((rc = energy_impl(m, d->h_u, &e_in, s, err))) return rc;
+    launches += 2;
+  }
   if ((rc = step_impl(m, d->h_u, d->h_res, dt, nsteps, s, err))) return rc;
-  int64_t launches = m->last_launches;
+  launches += m->last_launches;
   DG_CUDA(cudaMemcpyAsync(u, d->h_u, bytes, cudaMemcpyDeviceToHost, s), "cudaMemcpyAsync D2H");
   if (res) DG_CUDA(cudaMemcpyAsync(res, d->h_res, bytes, cudaMemcpyDeviceToHost, s), "cudaMemcpyAsync D2H");
-  if (energy) {
-    if ((rc = energy_impl(m, d->h_u, energy, s, err))) return rc;
+  if (energy || check) {
+    double e_out = 0.0;
+    rc = energy_impl(m, d->h_u, &e_out, s, err);
     launches += 2;
+    m->last_launches = launches;
+    if (energy) *energy = e_out;
+    if (rc) return rc;                       // includes a non-finite energy (DG_ERR_UNSTABLE)
+    if (check && e_out > e_in * (1.0 + m->energy_check)) {
+      char buf[160];
+      std::snprintf(buf, sizeof buf, "energy grew from %.9g to %.9g over %d steps "
+                    "(allowed factor 1 + %g): unstable run", e_in, e_out, nsteps, m->energy_check);
+      err = buf;
+      return DG_ERR_UNSTABLE;
+    }
   } else {
     DG_CUDA(cudaStreamSynchronize(s), "cudaStreamSynchronize");
     if ((rc = check_status(m, err))) return rc;

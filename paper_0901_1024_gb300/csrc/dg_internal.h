@@ -69,6 +69,7 @@ struct dg_mesh {
   int64_t last_launches = 0;
   bool trace = false;
   int stage_impl = DG_STAGE_AUTO;
+  double energy_check = -1.0;     // dg_step_host energy-growth limit (< 0: off)
 };
 
 namespace dg {
@@ -103,4 +104,8 @@ int device_resident(const dg_mesh* m, const float** M, const void** geo, const v
                     int64_t* K, int* Np, std::string& err);
 int device_trace_read(dg_mesh* m, double* ms, int32_t* kind, int64_t cap, int64_t* count,
                       std::string& err);
+// Calls launch(ctx) (which launches one kernel on `stream` and returns its
+// cudaError_t as an int); while tracing is on, brackets it with a pair of
+// events recorded under `kind` (the record of dg_trace_read).
+int trace_launch(dg_mesh* m, void* stream, int kind, int (*launch)(void*), void* ctx);
 }  // namespace dg

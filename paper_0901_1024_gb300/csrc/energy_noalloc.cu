@@ -14,9 +14,14 @@
 // mesh and any stream of a device, uses the same array, and it keeps the last
 // call's contents; each call writes every slot it later reads, so nothing has
 // to be cleared, but calls that overlap on the GPU race on it.
+//
+// Unlike dg_energy() the call does not synchronise: it neither reads the
+// pipeline status word of the stage kernels nor checks the energy for
+// finiteness (callers test the result themselves, or call dg_energy).
 #include <mutex>
 #include <string>
 
+#include <cuda.h>            // CUcontext / CUresult types only (no driver library link)
 #include <cuda_runtime.h>
 
 #include "device.h"
@@ -85,10 +90,54 @@ energy_final_sum(const double* __restrict__ partials, int n, double* out) {
   if (t == 0) out[0] = 0.5 * s[0];
 }
 
-// Device address of g_energy_partials per device, looked up once per device
-// (with that device current) on the first call made on it.
+// Device address of g_energy_partials per device, looked up with that device
+// current on the first call made on it, and again whenever the device's
+// current context has changed since (after cudaDeviceReset the module is
+// loaded anew and the array gets a new address).  cuCtxGetCurrent is reached
+// through the runtime's driver entry points, so the library needs no link
+// against the driver library.
+using CtxGetCurrent = CUresult (*)(CUcontext*);
 std::mutex g_mu;
-void* g_addr[64] = {};
+struct SymbolAddr {
+  CUcontext ctx = nullptr;
+  void* addr = nullptr;
+};
+SymbolAddr g_addr[64];
+
+CtxGetCurrent ctx_get_current() {
+  static CtxGetCurrent fn = [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) !=
+            cudaSuccess || q != cudaDriverEntryPointSuccess)
+      p = nullptr;
+    return reinterpret_cast<CtxGetCurrent>(p);
+  }();
+  return fn;
+}
+
+struct LaunchCtx {
+  const float* u;
+  const float* M;
+  const float* geo;
+  const float4* mat;
+  int K, Np, blocks;
+  double* partials;
+  double* energy;
+  cudaStream_t s;
+};
+
+int launch_block_sums(void* p) {
+  const LaunchCtx& c = *static_cast<const LaunchCtx*>(p);
+  energy_block_sums<<<c.blocks, kThreads, 0, c.s>>>(c.u, c.M, c.geo, c.mat, c.K, c.Np, c.partials);
+  return static_cast<int>(cudaGetLastError());
+}
+
+int launch_final_sum(void* p) {
+  const LaunchCtx& c = *static_cast<const LaunchCtx*>(p);
+  energy_final_sum<<<1, kSumThreads, 0, c.s>>>(c.partials, c.blocks, c.energy);
+  return static_cast<int>(cudaGetLastError());
+}
 
 }  // namespace
 
@@ -117,27 +166,30 @@ extern "C" int dg_energy_noalloc(dg_mesh* m, const float* u, double* energy, voi
   void* partials = nullptr;
   {
     std::lock_guard<std::mutex> lk(g_mu);
-    if (!g_addr[dev]) {
-      e = cudaGetSymbolAddress(&g_addr[dev], g_energy_partials);
+    CUcontext ctx = nullptr;
+    if (CtxGetCurrent get = ctx_get_current()) get(&ctx);
+    if (!g_addr[dev].addr || g_addr[dev].ctx != ctx) {
+      void* addr = nullptr;
+      e = cudaGetSymbolAddress(&addr, g_energy_partials);
       if (e != cudaSuccess) {
-        g_addr[dev] = nullptr;
+        g_addr[dev] = SymbolAddr{};
         dg::set_error(std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
         return DG_ERR_CUDA;
       }
+      // the first lookup of a context happens before it is cached, after any
+      // lazy module load, so the context is read again
+      if (CtxGetCurrent get = ctx_get_current()) get(&ctx);
+      g_addr[dev] = SymbolAddr{ctx, addr};
     }
-    partials = g_addr[dev];
+    partials = g_addr[dev].addr;
   }
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
-  const int blocks = static_cast<int>((K + kElemsPerBlock - 1) / kElemsPerBlock);
-  energy_block_sums<<<blocks, kThreads, 0, s>>>(u, M, static_cast<const float*>(geo),
-                                                static_cast<const float4*>(mat),
-                                                static_cast<int>(K), Np,
-                                                static_cast<double*>(partials));
-  e = cudaGetLastError();
-  if (e == cudaSuccess) {
-    energy_final_sum<<<1, kSumThreads, 0, s>>>(static_cast<const double*>(partials), blocks, energy);
-    e = cudaGetLastError();
-  }
+  LaunchCtx c{u, M, static_cast<const float*>(geo), static_cast<const float4*>(mat),
+              static_cast<int>(K), Np, static_cast<int>((K + kElemsPerBlock - 1) / kElemsPerBlock),
+              static_cast<double*>(partials), energy, static_cast<cudaStream_t>(stream)};
+  // launches are traced (dg_trace_enable) like those of dg_energy: kinds 2 and 3
+  e = static_cast<cudaError_t>(dg::trace_launch(m, stream, 2, launch_block_sums, &c));
+  if (e == cudaSuccess)
+    e = static_cast<cudaError_t>(dg::trace_launch(m, stream, 3, launch_final_sum, &c));
   if (e != cudaSuccess) {
     dg::set_error(std::string("energy kernel launch: ") + cudaGetErrorString(e));
     return DG_ERR_CUDA;

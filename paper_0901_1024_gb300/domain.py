@@ -88,6 +88,11 @@ def build_plans(mesh, tets, world: int, align: int = 4):
             cand = sorted(set().union(*(nbr.get(g, set()) for g in sorted(ghost_set | set(pad))))
                           - taken) if ghost_set or pad else []
             pad.append(cand[0] if cand else min(set(range(K)) - taken))
+        # every face neighbour of an owned element is owned or a traced ghost, so
+        # a padding element (taken from outside both) never touches an owned
+        # element: owned elements read no untraced (zero) values
+        owned_set = set(owned.tolist())
+        assert all(not (nbr.get(q, set()) & owned_set) for q in pad), "pad next to an owned element"
         ghosts = np.array(sorted(ghost_set) + pad, dtype=np.int64)
         plan = RankPlan(r, world, Np, owned, ghosts, tets[np.concatenate([owned, ghosts])])
         pos = np.full(K, -1, np.int64)

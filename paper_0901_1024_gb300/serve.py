@@ -68,6 +68,12 @@ def solve_bytes(K: int, Np: int) -> int:
     return 3 * 24 * K * Np + 4 * K + 128 * K + 180 * K + 4 * K * Np
 
 
+def carry_bytes(K: int, Np: int) -> int:
+    """Transient device bytes of one solve while its pack is rebuilt: the copy
+    of its u and res (FP32 [6][K][Np] each) carried into the new pack."""
+    return 2 * 24 * K * Np
+
+
 class _Live:
     def __init__(self, req: Request, now: float):
         self.req = req
@@ -81,6 +87,7 @@ class _Live:
         self.offset = 0
         self.finished = False
         self.bytes = solve_bytes(self.K, self.Np)
+        self.carry = carry_bytes(self.K, self.Np)
 
 
 class _Pack:
@@ -149,6 +156,15 @@ class _Pack:
     def state(self):
         return self.u if self.parity == 0 else self.work
 
+    def release(self):
+        """Drop the pack's graphs, fields and packed mesh (device memory goes
+        back to the caching allocator at once, before the next pack is built)."""
+        self.graphs = None
+        self.u = self.res = self.work = self.dt_elem = None
+        if self.mesh is not None:
+            self.mesh.close()
+            self.mesh = None
+
     def step(self):
         if self.graphs:
             self.graphs[self.parity].replay()
@@ -165,7 +181,13 @@ class Server:
     The autotuner's choices (stage implementation per order, decade of K and
     device) are kept for the life of the process, shared by every Server.
 
-    hbm_budget : bytes of device memory the live solves may hold.
+    hbm_budget : bytes of device memory the live solves may hold, including
+                 the transient copies of a pack rebuild: a solve is admitted
+                 only while the bytes of every admitted solve (solve_bytes)
+                 plus the carried copies of all of them (carry_bytes) fit, which
+                 bounds the peak of any rebuild (the old pack is released
+                 before tuning or allocating the new one).  stats["model_peak"]
+                 is the largest total of that accounting during the run.
     batch      : pack the solves of one order into one stage launch; False
                  steps every live solve with its own launches (same arithmetic).
     graphs     : replay each pack's step from a CUDA graph.
@@ -198,45 +220,84 @@ class Server:
             self._padding[N] = Mesh(v, np.array([[0, 1, 2, 3]]), N)
         return self._padding[N]
 
+    def _tune_key(self, N, solves):
+        K = sum(s.K for s in solves)
+        return (self.torch.cuda.current_device(), N,
+                min(3, int(math.log10(max(K, 1))) - 2))     # <1e3, <1e4, <1e5, more
+
+    def _time_impl(self, N, solves, impl):
+        """Milliseconds of 3 steps of a scratch pack of `solves` on `impl`; the
+        pack is released before returning."""
+        torch = self.torch
+        self._charge(sum(s.bytes for s in solves))
+        p = _Pack(torch, N, solves, None, self._pad_mesh(N), impl, False, self.stream)
+        for _ in range(2):                       # warm-up
+            p.step()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(self.stream)
+        for _ in range(3):
+            p.step()
+        e1.record(self.stream)
+        e1.synchronize()
+        p.release()
+        self._charge(-sum(s.bytes for s in solves))
+        return e0.elapsed_time(e1)
+
     def _choose_impl(self, N, solves):
         if not self.autotune:
             return self.impl
         if N > 6:
             return Mesh.STAGE_FP32
-        K = sum(s.K for s in solves)
-        key = (self.torch.cuda.current_device(), N,
-               min(3, int(math.log10(max(K, 1))) - 2))     # <1e3, <1e4, <1e5, more
+        key = self._tune_key(N, solves)
         if key not in self._tuned:
-            torch = self.torch
-            times = {}
-            for impl in (Mesh.STAGE_TC, Mesh.STAGE_FP32):
-                p = _Pack(torch, N, solves, None, self._pad_mesh(N), impl, False, self.stream)
-                for _ in range(2):                       # warm-up
-                    p.step()
-                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                e0.record(self.stream)
-                for _ in range(3):
-                    p.step()
-                e1.record(self.stream)
-                e1.synchronize()
-                times[impl] = e0.elapsed_time(e1)
+            times = {impl: self._time_impl(N, solves, impl)
+                     for impl in (Mesh.STAGE_TC, Mesh.STAGE_FP32)}
             self._tuned[key] = min(times, key=times.get)
         return self._tuned[key]
 
-    # ---- the loop ----------------------------------------------------------
+    # ---- device-memory accounting (a model of what the loop allocates) ------
+    def _charge(self, nbytes):
+        m = self.stats
+        m["model_now"] = m.get("model_now", 0) + nbytes
+        m["model_peak"] = max(m.get("model_peak", 0), m["model_now"])
+
+    # ---- pack rebuilds -------------------------------------------------------
+    def _carry(self, old, members):
+        """Copies of (u, res) of the old pack's solves that go on in `members`."""
+        state = old.state()
+        carry = {}
+        for s in old.solves:
+            if s in members:
+                sl = slice(s.offset, s.offset + s.K)
+                carry[id(s)] = (state[:, sl].clone(), old.res[:, sl].clone())
+                self._charge(s.carry)
+        return carry
+
+    def _release(self, pack):
+        pack.release()
+        self._charge(-sum(s.bytes for s in pack.solves))
+
+    def _new_pack(self, N, members, carry, impl):
+        self._charge(sum(s.bytes for s in members))
+        return _Pack(self.torch, N, members, carry, self._pad_mesh(N), impl, self.graphs,
+                     self.stream)
+
     def _build(self, N, members, old, st):
         """A pack of `members` (live solves of order N), continuing from the
-        old pack's state for those that were in it."""
-        torch = self.torch
+        old pack's state for those that were in it.  The carried copies are
+        taken first, then the old pack is released, then the implementation is
+        tuned (scratch packs, one at a time) and the new pack allocated: the
+        peak is the admitted solves' bytes plus the carried copies."""
         carry = {}
         if old is not None:
-            state = old.state()
-            for s in old.solves:
-                if s in members:
-                    sl = slice(s.offset, s.offset + s.K)
-                    carry[id(s)] = (state[:, sl].clone(), old.res[:, sl].clone())
+            carry = self._carry(old, members)
+            self._release(old)
         impl = self._choose_impl(N, members)
-        p = _Pack(torch, N, members, carry, self._pad_mesh(N), impl, self.graphs, self.stream)
+        p = self._new_pack(N, members, carry, impl)
+        for s in members:
+            if id(s) in carry:
+                self._charge(-s.carry)
+        carry.clear()
         p.built_at = st["iterations"]
         st["packs_built"] += 1
         return p
@@ -268,22 +329,26 @@ class Server:
         `max_iterations` bounds the loop (RuntimeError when exceeded)."""
         pending = sorted(requests, key=lambda r: (r.arrival, r.rid))
         waiting, packs, results = [], [], []
-        held = 0
+        held = 0                      # bytes of every admitted solve not yet released
+        reserve = 0                   # their carried copies during a rebuild
         t0 = time.perf_counter()
         now = lambda: time.perf_counter() - t0  # noqa: E731
         st = self.stats = dict(admit_s=0.0, pack_s=0.0, step_s=0.0, retire_s=0.0, packs_built=0,
-                               iterations=0)
+                               iterations=0, model_now=0, model_peak=0)
         every = self.rebuild_every if self.batch else 0
         while pending or waiting or packs:
             if max_iterations is not None and st["iterations"] > max_iterations:
                 raise RuntimeError("serve loop exceeded max_iterations")
             for p in [p for p in packs if not p.alive]:     # finished packs free their memory
                 packs.remove(p)
+                self._release(p)
                 held -= sum(s.bytes for s in p.solves)
+                reserve -= sum(s.carry for s in p.solves)
             while pending and pending[0].arrival <= now():
                 req = pending[0]
-                need = solve_bytes(len(req.tets), (req.N + 1) * (req.N + 2) * (req.N + 3) // 6)
-                if held > 0 and held + need > self.budget:
+                Np = (req.N + 1) * (req.N + 2) * (req.N + 3) // 6
+                need = solve_bytes(len(req.tets), Np) + carry_bytes(len(req.tets), Np)
+                if held > 0 and held + reserve + need > self.budget:
                     break                                # first come, first served
                 pending.pop(0)
                 ta = time.perf_counter()
@@ -291,6 +356,7 @@ class Server:
                 st["admit_s"] += time.perf_counter() - ta
                 waiting.append(s)
                 held += s.bytes
+                reserve += s.carry
             if not waiting and not packs:
                 if not pending:
                     break                                # the last packs just finished
@@ -312,8 +378,10 @@ class Server:
                         keep = [s for s in old.solves if not s.finished] if old is not None else []
                         if old is not None:
                             packs.remove(old)
-                            held -= sum(s.bytes for s in old.solves if s.finished)
                         packs.append(self._build(N, keep + new, old, st))
+                        if old is not None:                  # released by the rebuild
+                            held -= sum(s.bytes for s in old.solves if s.finished)
+                            reserve -= sum(s.carry for s in old.solves if s.finished)
                         waiting = [s for s in waiting if s.req.N != N]
                 else:
                     for s in waiting:

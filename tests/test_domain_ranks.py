@@ -31,6 +31,34 @@ def _mesh(dg, n=3, N=2, seed=3):
     return verts, tets, dg.Mesh(verts, tets, N)
 
 
+@pytest.mark.parametrize("n,world", [(2, 7), (2, 9), (2, 13)])
+def test_padding_falls_back_to_far_elements_and_never_touches_owned(dg, n, world):
+    """Meshes so small that a rank's owned elements and ghosts are nearly the
+    whole mesh: padding takes the lowest-numbered free element (the fallback
+    when no free neighbour of a ghost is left); no padding element shares a
+    face with an owned element of its rank."""
+    from paper_0901_1024_gb300.domain import build_plans
+    verts, tets, mesh = _mesh(dg, n=n)
+    plans = build_plans(mesh, tets, world)
+    K, Np = mesh.K, mesh.Np
+    vM, vP = mesh.connectivity()
+    nb = {}
+    for a, b in zip(vM // Np, vP // Np):
+        if a != b:
+            nb.setdefault(int(a), set()).add(int(b))
+    fell_back = False
+    for p in plans:
+        mine = set(p.owned.tolist())
+        needed = set().union(*(nb.get(k, set()) for k in p.owned)) - mine
+        pads = [int(g) for g in p.ghosts if int(g) not in needed]
+        for q in pads:
+            assert not nb.get(q, set()) & mine
+        near = set().union(*(nb.get(g, set()) for g in needed)) if needed else set()
+        fell_back |= any(q not in near for q in pads)
+        assert p.n_local % 4 == 0 or p.n_local == K
+    assert fell_back
+
+
 @pytest.mark.parametrize("world", [1, 2, 3, 5])
 def test_plans_cover_the_mesh_and_match_pairwise(dg, world):
     from paper_0901_1024_gb300.domain import build_plans

@@ -16,7 +16,9 @@ class FakeLive:
         self.req, self.K, self.steps, self.dt = req, len(req.tets), int(req.T), 1.0
         self.done, self.admitted, self.offset, self.finished = 0, now, 0, False
         self.stepped = 0
-        self.bytes = serve.solve_bytes(self.K, (req.N + 1) * (req.N + 2) * (req.N + 3) // 6)
+        Np = (req.N + 1) * (req.N + 2) * (req.N + 3) // 6
+        self.bytes = serve.solve_bytes(self.K, Np)
+        self.carry = serve.carry_bytes(self.K, Np)
 
 
 class FakePack:
@@ -27,6 +29,12 @@ class FakePack:
         for s in self.solves:
             if not s.finished:
                 s.stepped += 1
+
+    def state(self):
+        return None
+
+    def release(self):
+        self.released = True
 
 
 class FakeServer(serve.Server):
@@ -43,6 +51,9 @@ class FakeServer(serve.Server):
         st["packs_built"] += 1
         self.live_log.append(len(members))
         return FakePack(N, members, st["iterations"])
+
+    def _release(self, pack):
+        pack.release()
 
     def _retire(self, p, s, now):
         assert s.stepped == s.steps
@@ -98,3 +109,53 @@ def test_rebuilds_are_paced_and_unbatched_packs_are_per_solve():
 def test_loop_bound_raises():
     with pytest.raises(RuntimeError):
         FakeServer().run(requests(3), max_iterations=1)
+
+
+class LedgerServer(FakeServer):
+    """The real rebuild sequence (Server._build: carry, release the old pack,
+    tune on scratch packs, allocate the new pack) and the real device-memory
+    accounting, with packs that hold no memory: only the accounting runs."""
+    _build = serve.Server._build
+    _release = serve.Server._release
+
+    def __init__(self, budget, rebuild_every=2):
+        super().__init__(budget=budget, rebuild_every=rebuild_every)
+        self.carried = 0
+
+    def _carry(self, old, members):
+        carry = {}
+        for s in old.solves:
+            if s in members:
+                carry[id(s)] = None
+                self._charge(s.carry)
+                self.carried += 1
+        return carry
+
+    def _choose_impl(self, N, solves):
+        for _ in range(2):                     # two scratch packs, one at a time
+            self._charge(sum(s.bytes for s in solves))
+            self._charge(-sum(s.bytes for s in solves))
+        return 0
+
+    def _new_pack(self, N, members, carry, impl):
+        self._charge(sum(s.bytes for s in members))
+        self.live_log.append(len(members))
+        return FakePack(N, members, 0)
+
+
+@pytest.mark.parametrize("every", [1, 2, 8])
+def test_rebuild_peak_stays_within_the_budget(every):
+    """Admissions as budget frees up join live packs, so packs are rebuilt while they hold carried
+    solves; the accounted device bytes (admitted solves, the carried copies of
+    a rebuild, the tuner's scratch packs) never exceed the budget, although
+    several solves are live at once."""
+    reqs = requests(40, seed=3)
+    per = [serve.solve_bytes(len(q.tets), (q.N + 1) * (q.N + 2) * (q.N + 3) // 6) +
+           serve.carry_bytes(len(q.tets), (q.N + 1) * (q.N + 2) * (q.N + 3) // 6) for q in reqs]
+    budget = 4 * max(per)
+    srv = LedgerServer(budget, rebuild_every=every)
+    res = srv.run(reqs, max_iterations=100_000)
+    assert [r.rid for r in res] == list(range(len(reqs)))
+    assert srv.carried > 0 and max(srv.live_log) > 1
+    assert 0 < srv.stats["model_peak"] <= budget
+    assert srv.stats["model_now"] == 0                # everything released at the end
