@@ -88,7 +88,7 @@ template <int N> struct TcDims {
   static constexpr int G_FLOATS = tc_geo_floats(N);  // word-major [w][E], node bytes
   static constexpr int F_FLOATS = ROWS * FSTR;
   static constexpr int B_BYTES = NN * KT * 2;         // one FP16 piece
-  static constexpr int TAB_BYTES = (4 * Nfp + 96 * Nfp + 15) & ~15;
+  static constexpr int TAB_BYTES = (4 * Nfp + 15) & ~15;
   static constexpr int OFF_B = 0;                     // 2 pieces
   static constexpr int OFF_U = OFF_B + 2 * B_BYTES;   // NSU slots
   static constexpr int OFF_G = OFF_U + NSU * U_FLOATS * 4;
@@ -212,6 +212,14 @@ __device__ __forceinline__ void tc_load_res(const StageArgs& A, int tile, float*
   for (int c = 0; c < 6; ++c)
     tc::bulk_g2s(sr + c * D::E * D::Np, A.res + (size_t(c) * K + k0) * D::Np, fb, bar);
 }
+
+// Programmatic dependent launch: let the next kernel of the stream start its
+// set-up while this grid runs, and wait for the previous grid's results
+// before touching any field it may write or read.
+__device__ __forceinline__ void pdl_launch_dependents() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 
 // One g-block builder row (a producer thread of role 0 or 1) of tile t.
 struct GRow {
@@ -487,10 +495,12 @@ __global__ void __launch_bounds__(TcDims<N>::THREADS, 1) tc_stage_kernel(const S
   __shared__ __align__(8) uint64_t s_u_full[D::NSU];
   __shared__ __align__(8) uint64_t s_r_full[D::NSR];
   __shared__ __align__(8) uint64_t s_a_full[2], s_mma_done[2];
+  __shared__ __align__(8) uint64_t s_b_full;
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int K = A.K;
   const int ntiles = (A.num_tiles - int(blockIdx.x) + int(gridDim.x) - 1) / int(gridDim.x);
+  pdl_launch_dependents();
   if (ntiles <= 0) return;
 
   float* sU = reinterpret_cast<float*>(smem + D::OFF_U);
@@ -501,19 +511,13 @@ __global__ void __launch_bounds__(TcDims<N>::THREADS, 1) tc_stage_kernel(const S
   float* sBound = reinterpret_cast<float*>(smem + D::OFF_BND);
   float* sF2 = reinterpret_cast<float*>(smem + D::OFF_F2);
   unsigned char* sFmask = smem + D::OFF_TAB;
-  unsigned char* sPerm = sFmask + 4 * Nfp;
 
-  // ---- set-up: B pieces, tables, tensor memory, barriers -------------------
-  {
-    const uint4* src = reinterpret_cast<const uint4*>(A.tcB);
-    uint4* dst = reinterpret_cast<uint4*>(smem + D::OFF_B);
-    for (int i = tid; i < 2 * D::B_BYTES / 16; i += D::THREADS) dst[i] = __ldg(src + i);
-    for (int i = tid; i < 4 * Nfp; i += D::THREADS) sFmask[i] = __ldg(A.fmask + i);
-    for (int i = tid; i < 96 * Nfp; i += D::THREADS) sPerm[i] = __ldg(A.perm + i);
-  }
-  tc::fence_proxy_async_smem();
+  // ---- set-up: B pieces (one bulk copy, constant data: it may overlap the
+  // previous kernel), face-node table, tensor memory, barriers ----------------
+  for (int i = tid; i < 4 * Nfp; i += D::THREADS) sFmask[i] = __ldg(A.fmask + i);
   if (warp == 0) tc::tmem_alloc(&s_tmem, 512);
   if (tid == 0) {
+    tc::mbar_init(&s_b_full, 1);
     for (int i = 0; i < D::NSU; ++i) tc::mbar_init(&s_u_full[i], 1);
     for (int i = 0; i < D::NSR; ++i) tc::mbar_init(&s_r_full[i], 1);
     for (int i = 0; i < 2; ++i) {
@@ -521,11 +525,15 @@ __global__ void __launch_bounds__(TcDims<N>::THREADS, 1) tc_stage_kernel(const S
       tc::mbar_init(&s_mma_done[i], 1);
     }
     tc::fence_mbar_init();
+    tc::mbar_expect_tx(&s_b_full, 2u * D::B_BYTES);
+    tc::bulk_g2s(smem + D::OFF_B, A.tcB, 2u * D::B_BYTES, &s_b_full);
   }
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
   const uint32_t tbase = s_tmem;
+  // the previous kernel of the stream has finished writing (and reading) the fields
+  pdl_wait();
 
   if (warp < 4) {
     // ======================= MMA issue + epilogue warps ========================
@@ -571,6 +579,7 @@ __global__ void __launch_bounds__(TcDims<N>::THREADS, 1) tc_stage_kernel(const S
       }
       if (j < ntiles && warp == 0) {                 // MMAs of tile j
         const int buf = j & 1;
+        if (j == 0) wait_or_flag(&s_b_full, 0, A.status);   // B pieces in shared memory
         tc::fence_after_sync();
         const uint32_t d_acc = tbase + buf * D::BUF_COLS + 2 * D::ACOLS;
         const uint32_t a_base = tbase + buf * D::BUF_COLS;
@@ -763,6 +772,25 @@ __global__ void __launch_bounds__(TcDims<N>::THREADS, 1) tc_stage_kernel(const S
   if (warp == 0) tc::tmem_dealloc(tbase, 512);
 }
 
+// Launch with programmatic stream serialization: the kernel may start while
+// the previous kernel of the stream finishes; it calls griddepcontrol.wait
+// before its first access to the fields (every grid here is at most one CTA
+// per SM, so a waiting CTA never holds an SM the previous grid still needs).
+inline cudaError_t launch_pdl(void (*kern)(const StageArgs), int grid, int threads, int smem,
+                              cudaStream_t s, const StageArgs& a) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(threads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, a);
+}
+
 template <int N>
 cudaError_t launch_tc_stage_n(bool rk, const StageArgs& a, int num_sms, cudaStream_t s) {
   using D = TcDims<N>;
@@ -785,8 +813,7 @@ cudaError_t launch_tc_stage_n(bool rk, const StageArgs& a, int num_sms, cudaStre
   }
   const int grid = a.num_tiles < num_sms ? a.num_tiles : num_sms;
   if (grid <= 0) return cudaSuccess;
-  kern<<<grid, D::THREADS, smem, s>>>(a);
-  return cudaGetLastError();
+  return launch_pdl(kern, grid, D::THREADS, smem, s, a);
 }
 
 }  // namespace dgdev
