@@ -620,7 +620,7 @@ def run_serve(args):
 def run_sweep(args):
     """Roofline curve over the order: for N = 1..9 a pulse workload on a box mesh
     with n chosen so that 6 K Np is about 1.7e7, timed per stage launch (CUDA
-    events) after warm-up, for the default stage kernel (tensor cores for
+    events around back-to-back steps, divided by the stage count) after warm-up, for the default stage kernel (tensor cores for
     N = 2..6, FP32 CUDA cores otherwise) and, for N = 2..6, the FP32 kernel as well."""
     import torch
     import paper_0901_1024_gb300 as dg
@@ -640,12 +640,17 @@ def run_sweep(args):
             u = torch.from_numpy(u0).cuda()
             res = torch.zeros_like(u)
             mesh.step(u, res, mesh.dt_cfl, 3)
-            mesh.trace_enable(5 * args.sweep_steps)
-            mesh.step(u, res, mesh.dt_cfl, args.sweep_steps)
-            torch.cuda.synchronize()
-            ms, kinds = mesh.trace_read()
+            mesh.trace_enable(8)                   # which kernel runs (one traced step)
+            mesh.step(u, res, mesh.dt_cfl, 1)
+            _, kinds = mesh.trace_read()
             mesh.trace_enable(0)
-            stage = statistics.fmean(t for t, k in zip(ms, kinds) if k in (0, 4)) * 1e-3
+            steps = args.sweep_steps + args.sweep_steps % 2      # even: no copy-back inside
+            f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            f0.record()
+            mesh.step(u, res, mesh.dt_cfl, steps)
+            f1.record()
+            torch.cuda.synchronize()
+            stage = f0.elapsed_time(f1) * 1e-3 / (5 * steps)
             K = mesh.K
             gbs = stage_bytes_per_elem(Np) * K / stage / 1e9
             tf = flops_per_elem_stage(N, Np, Nfp) * K / stage / 1e12

@@ -30,6 +30,7 @@
 #include <cuda_runtime.h>
 
 #include "device.h"
+#include "launch.cuh"
 
 namespace dgdev {
 
@@ -68,6 +69,7 @@ __global__ void __launch_bounds__(StageDims<N>::T) stage_kernel(const StageArgs 
   const float4* D4 = A.D4;
   const float4* LIFT4 = A.LIFT4;
   const int tid = threadIdx.x;
+  pdl_launch_dependents();
   if constexpr (D::OPS_SMEM) {
     float4* sops = reinterpret_cast<float4*>(sg + D::GT);
     for (int i = tid; i < Np * Np; i += D::T) sops[i] = __ldg(A.D4 + i);
@@ -78,6 +80,7 @@ __global__ void __launch_bounds__(StageDims<N>::T) stage_kernel(const StageArgs 
   }
   const int e = tid % E, g = tid / E;
   const int K = A.K;
+  pdl_wait();        // the previous kernel's fields are complete (operators are constant)
 
   for (int tile = blockIdx.x; tile < A.num_tiles; tile += gridDim.x) {
     const int k0 = tile * E;
@@ -308,8 +311,7 @@ cudaError_t launch_stage_n(bool rk, const StageArgs& a, int num_sms, cudaStream_
   }
   const int grid = a.num_tiles < num_sms * o ? a.num_tiles : num_sms * o;
   if (grid <= 0) return cudaSuccess;
-  kern<<<grid, D::T, D::smem_bytes, s>>>(a);
-  return cudaGetLastError();
+  return launch_pdl(kern, grid, D::T, int(D::smem_bytes), s, a);
 }
 
 }  // namespace dgdev

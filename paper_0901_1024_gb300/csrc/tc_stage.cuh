@@ -44,6 +44,7 @@
 #include <cuda_runtime.h>
 
 #include "device.h"
+#include "launch.cuh"
 #include "tcgen05.cuh"
 
 namespace dgdev {
@@ -212,14 +213,6 @@ __device__ __forceinline__ void tc_load_res(const StageArgs& A, int tile, float*
   for (int c = 0; c < 6; ++c)
     tc::bulk_g2s(sr + c * D::E * D::Np, A.res + (size_t(c) * K + k0) * D::Np, fb, bar);
 }
-
-// Programmatic dependent launch: let the next kernel of the stream start its
-// set-up while this grid runs, and wait for the previous grid's results
-// before touching any field it may write or read.
-__device__ __forceinline__ void pdl_launch_dependents() {
-  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-}
-__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 
 // One g-block builder row (a producer thread of role 0 or 1) of tile t.
 struct GRow {
@@ -770,25 +763,6 @@ __global__ void __launch_bounds__(TcDims<N>::THREADS, 1) tc_stage_kernel(const S
   tc::fence_before_sync();
   __syncthreads();
   if (warp == 0) tc::tmem_dealloc(tbase, 512);
-}
-
-// Launch with programmatic stream serialization: the kernel may start while
-// the previous kernel of the stream finishes; it calls griddepcontrol.wait
-// before its first access to the fields (every grid here is at most one CTA
-// per SM, so a waiting CTA never holds an SM the previous grid still needs).
-inline cudaError_t launch_pdl(void (*kern)(const StageArgs), int grid, int threads, int smem,
-                              cudaStream_t s, const StageArgs& a) {
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(grid);
-  cfg.blockDim = dim3(threads);
-  cfg.dynamicSmemBytes = smem;
-  cfg.stream = s;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-  attr[0].val.programmaticStreamSerializationAllowed = 1;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, kern, a);
 }
 
 template <int N>

@@ -146,6 +146,7 @@ __global__ void __launch_bounds__(TtDims<N>::THREADS, 1) tt_stage_kernel(const S
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int K = A.K;
   const int ntiles = (A.num_tiles - int(blockIdx.x) + int(gridDim.x) - 1) / int(gridDim.x);
+  pdl_launch_dependents();
   if (ntiles <= 0) return;
 
   unsigned char* sXhi = smem + D::OFF_X;
@@ -214,6 +215,9 @@ __global__ void __launch_bounds__(TtDims<N>::THREADS, 1) tt_stage_kernel(const S
     __syncthreads();                                 // staging area free again
     tc::fence_after_sync();
   }
+  // the set-up above reads only constant data; the previous kernel of the
+  // stream has finished writing (and reading) the fields from here on
+  pdl_wait();
 
   if (warp < 4) {
     // ======================= MMA issue + epilogue warps ========================
@@ -574,8 +578,7 @@ cudaError_t launch_tt_stage_n(bool rk, const StageArgs& a, int num_sms, cudaStre
   }
   const int grid = a.num_tiles < num_sms ? a.num_tiles : num_sms;
   if (grid <= 0) return cudaSuccess;
-  kern<<<grid, D::THREADS, smem, s>>>(a);
-  return cudaGetLastError();
+  return launch_pdl(kern, grid, D::THREADS, smem, s, a);
 }
 
 }  // namespace dgdev
