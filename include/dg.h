@@ -240,6 +240,36 @@ int dg_rk_stage_elem(dg_mesh* mesh, const float* u_in, float* u_out, float* res,
                      const float* dt_elem, void* stream);
 
 /*
+ * One LSERK4 stage i (0..4) of several meshes -- e.g. the packed meshes
+ * (dg_mesh_pack) of a batch of solves of different orders -- in as few
+ * launches as possible: the meshes that run on the tensor cores at orders
+ * 1..4 share one persistent launch, those at orders 5, 6 another; each launch
+ * splits its CTAs (one per SM) among the meshes in proportion to their tiles x
+ * tile_cost, so all of them advance side by side on the GPU.  Meshes on the
+ * FP32 CUDA-core stage (orders >= 7, forced FP32, unaligned sizes) get their own
+ * launch.  For mesh i the result is bit for bit that of
+ *   dg_rk_stage_elem(meshes[i], u_in[i], u_out[i], res[i], stage, dt_elem[i])
+ * (or of dg_rk_stage with dt where dt_elem or dt_elem[i] is NULL): the paper's
+ * element-local work (Section 5) assigned across solves.
+ *   meshes    : host array of n distinct meshes, all resident on the current
+ *               device (an order set on each);
+ *   u_in, u_out, res : host arrays of n device pointers, as in dg_rk_stage;
+ *   dt_elem   : host array of n device pointers to [K_i] FP32 steps, or NULL;
+ *   tile_cost : host array of n positive costs of one tile on one SM (any unit,
+ *               e.g. from timing each mesh alone), or NULL for the library's
+ *               per-order defaults; only the ratios matter.
+ * Up to 8 meshes share a launch (more take more launches).  While tracing is on
+ * (meshes[0]'s trace) a shared launch is recorded as kind 6.
+ * dg_last_launch_count(meshes[0]) gives the launches issued.  Asynchronous on
+ * `stream`.  Errors: DG_ERR_ARG (NULL arrays or buffers, n < 1, a repeated
+ * mesh, aliased buffers, stage outside 0..4, dt <= 0, meshes on different
+ * devices), DG_ERR_STATE (no order set), DG_ERR_CUDA.
+ */
+int dg_rk_stage_multi(dg_mesh* const* meshes, int n, const float* const* u_in,
+                      float* const* u_out, float* const* res, const float* const* dt_elem,
+                      int stage, double dt, const double* tile_cost, void* stream);
+
+/*
  * Discrete energy 1/2 sum_k J_k sum_c u_kc^T M u_kc (FP32 products, FP64
  * accumulation across elements) written to *out (host).
  *   u : device, [6][K][Np] FP32.
@@ -309,7 +339,8 @@ int dg_trace_enable(dg_mesh* mesh, int n);
  *   kind : host, receives the kernel of each launch (0 = fused RK stage and
  *          1 = right-hand side on CUDA cores, 4 = fused RK stage and 5 =
  *          right-hand side on tensor cores, 2 = energy partial sums, 3 =
- *          energy final sum); may be NULL;
+ *          energy final sum, 6 = one launch of dg_rk_stage_multi over several
+ *          meshes); may be NULL;
  *   count: receives the number of recorded launches (may exceed cap).
  * Waits for the last recorded event.  Errors: DG_ERR_STATE if nothing was traced.
  */

@@ -201,6 +201,25 @@ class Mesh:
                                          int(stage), _devptr(dt_elem), _stream_handle(stream)),
               "dg_rk_stage_elem")
 
+    @staticmethod
+    def rk_stage_multi(meshes, u_in, u_out, res, stage: int, dt: float = 1.0, dt_elem=None,
+                       tile_cost=None, stream=None):
+        """dg_rk_stage_multi: one LSERK4 stage of several meshes in shared
+        launches (orders 1..4 in one, 5..6 in another); dt_elem is a list of
+        device FP32 step tensors (or None entries / None: the scalar dt) and
+        tile_cost a list of per-mesh tile costs (None: library defaults)."""
+        lib = load()
+        n = len(meshes)
+        arr = lambda xs: (C.c_void_p * n)(*[None if x is None else _devptr_any(x).value for x in xs])  # noqa: E731
+        hs = (C.c_void_p * n)(*[m._h.value for m in meshes])
+        dts = None if dt_elem is None else arr(dt_elem)
+        costs = None if tile_cost is None else (C.c_double * n)(*[float(c) for c in tile_cost])
+        for xs in (u_in, u_out, res):
+            for x in xs:
+                _devptr(x)
+        check(lib.dg_rk_stage_multi(hs, n, arr(u_in), arr(u_out), arr(res), dts, int(stage),
+                                    float(dt), costs, _stream_handle(stream)), "dg_rk_stage_multi")
+
     def energy(self, u, stream=None) -> float:
         out = C.c_double()
         check(self._lib.dg_energy(self._h, _devptr(u), C.byref(out), _stream_handle(stream)),

@@ -37,6 +37,9 @@ SIGNATURES = {
     "dg_step": (C.c_int, [_vp, _vp, _vp, C.c_double, C.c_int, _vp]),
     "dg_rk_stage": (C.c_int, [_vp, _vp, _vp, _vp, C.c_int, C.c_double, _vp]),
     "dg_rk_stage_elem": (C.c_int, [_vp, _vp, _vp, _vp, C.c_int, _vp, _vp]),
+    "dg_rk_stage_multi": (C.c_int, [C.POINTER(_vp), C.c_int, C.POINTER(_vp), C.POINTER(_vp),
+                                    C.POINTER(_vp), C.POINTER(_vp), C.c_int, C.c_double,
+                                    C.POINTER(C.c_double), _vp]),
     "dg_energy": (C.c_int, [_vp, _vp, _dp, _vp]),
     "dg_energy_range": (C.c_int, [_vp, _vp, C.c_int64, C.c_int64, _dp, _vp]),
     "dg_energy_noalloc": (C.c_int, [_vp, _vp, _vp, _vp]),

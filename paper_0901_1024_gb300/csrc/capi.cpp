@@ -381,6 +381,29 @@ int dg_rk_stage_elem(dg_mesh* m, const float* u_in, float* u_out, float* res, in
   return DG_OK;
 }
 
+int dg_rk_stage_multi(dg_mesh* const* meshes, int n, const float* const* u_in,
+                      float* const* u_out, float* const* res, const float* const* dt_elem,
+                      int stage, double dt, const double* tile_cost, void* stream) {
+  if (!meshes || n < 1 || !u_in || !u_out || !res)
+    return fail(DG_ERR_ARG, "meshes, u_in, u_out or res is NULL, or n < 1");
+  if (stage < 0 || stage > 4) return fail(DG_ERR_ARG, "stage must be 0..4");
+  if (!(dt > 0.0) || !std::isfinite(dt)) return fail(DG_ERR_ARG, "dt must be positive and finite");
+  for (int i = 0; i < n; ++i) {
+    if (int rc = check_mesh(meshes[i], true)) return rc;
+    if (!u_in[i] || !u_out[i] || !res[i])
+      return fail(DG_ERR_ARG, "u_in, u_out or res of mesh " + std::to_string(i) + " is NULL");
+    if (u_in[i] == u_out[i] || res[i] == u_in[i] || res[i] == u_out[i])
+      return fail(DG_ERR_ARG, "u_in, u_out and res must be three different buffers");
+    for (int j = 0; j < i; ++j)
+      if (meshes[j] == meshes[i]) return fail(DG_ERR_ARG, "a mesh appears twice");
+  }
+  std::string err;
+  if (int rc = dg::device_stage_multi(meshes, n, u_in, u_out, res, dt_elem, stage, dt, tile_cost,
+                                      stream, err))
+    return fail(rc, err);
+  return DG_OK;
+}
+
 int dg_energy_range(dg_mesh* m, const float* u, int64_t k0, int64_t k1, double* out,
                     void* stream) {
   if (int rc = check_mesh(m, true)) return rc;

@@ -778,6 +778,106 @@ int device_stage(dg_mesh* m, const float* u_in, float* u_out, float* res, int st
   return DG_OK;
 }
 
+// Default cost of one tile on one SM in microseconds, orders 1..6 on the
+// tensor cores (GB300: stage time x CTAs / tiles of the order sweep), used to
+// split a mixed launch's CTAs when the caller gives no costs.
+static double default_tile_cost(int N) {
+  static const double c[7] = {1.0, 1.6, 1.9, 2.7, 3.6, 3.1, 3.9};
+  return N >= 1 && N <= 6 ? c[N] : 1.0;
+}
+
+// CTAs of a mixed launch: one per group at least, `total` in all, each further
+// CTA to the group whose span ceil(tiles / ctas) x cost is then the longest
+// (so the groups of one launch finish together).
+static std::vector<int> split_ctas(const std::vector<int64_t>& tiles,
+                                   const std::vector<double>& cost, int total) {
+  const size_t n = tiles.size();
+  std::vector<int> c(n, 1);
+  int used = static_cast<int>(n);
+  auto span = [&](size_t g) {
+    return static_cast<double>((tiles[g] + c[g] - 1) / c[g]) * cost[g];
+  };
+  while (used < total) {
+    size_t best = n;
+    for (size_t g = 0; g < n; ++g)
+      if (c[g] < tiles[g] && (best == n || span(g) > span(best))) best = g;
+    if (best == n) break;
+    ++c[best];
+    ++used;
+  }
+  return c;
+}
+
+int device_stage_multi(dg_mesh* const* ms, int n, const float* const* u_in, float* const* u_out,
+                       float* const* res, const float* const* dt_elem, int stage, double dt,
+                       const double* tile_cost, void* stream, std::string& err) {
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  int64_t launches = 0;
+  std::vector<int> fam(n, 0);        // 0: its own launch, 1: orders 1..4, 2: orders 5, 6
+  for (int i = 0; i < n; ++i) {
+    if (int rc = ensure_device(ms[i], err)) return rc;
+    if (ms[i]->dev->device != ms[0]->dev->device) {
+      err = "every mesh of one call must be on the same device";
+      return DG_ERR_ARG;
+    }
+    if (use_tc(ms[i], {u_in[i], u_out[i], res[i]})) fam[i] = ms[i]->N <= 4 ? 1 : 2;
+  }
+  for (int i = 0; i < n; ++i)
+    if (fam[i] == 0) {
+      if (int rc = device_stage(ms[i], u_in[i], u_out[i], res[i], stage, dt,
+                                dt_elem ? dt_elem[i] : nullptr, stream, err))
+        return rc;
+      ++launches;
+    }
+  const int sms = ms[0]->dev->num_sms;
+  for (int f = 1; f <= 2; ++f) {
+    std::vector<int> idx;
+    for (int i = 0; i < n; ++i)
+      if (fam[i] == f) idx.push_back(i);
+    for (size_t c0 = 0; c0 < idx.size(); c0 += dgdev::kMaxMixedGroups) {
+      const size_t ng = std::min(idx.size() - c0, static_cast<size_t>(dgdev::kMaxMixedGroups));
+      std::vector<int64_t> tiles(ng);
+      std::vector<double> cost(ng);
+      dgdev::MixedArgs M{};
+      M.ngroups = static_cast<int>(ng);
+      int64_t all = 0;
+      for (size_t g = 0; g < ng; ++g) {
+        const int i = idx[c0 + g];
+        dgdev::StageArgs a = stage_args(ms[i], true);
+        a.u_in = u_in[i];
+        a.u_out = u_out[i];
+        a.res = res[i];
+        a.dt = static_cast<float>(dt);
+        a.dt_elem = dt_elem ? dt_elem[i] : nullptr;
+        a.a = static_cast<float>(kRkA[stage]);
+        a.b = static_cast<float>(kRkB[stage]);
+        M.g[g].a = a;
+        M.g[g].N = ms[i]->N;
+        M.g[g].ext = (a.mat || a.absorbing) ? 1 : 0;
+        tiles[g] = a.num_tiles;
+        cost[g] = tile_cost && tile_cost[i] > 0.0 ? tile_cost[i] : default_tile_cost(ms[i]->N);
+        all += a.num_tiles;
+      }
+      const int total = static_cast<int>(std::min<int64_t>(sms, all));
+      const std::vector<int> c = split_ctas(tiles, cost, total);
+      int first = 0;
+      for (size_t g = 0; g < ng; ++g) {
+        M.g[g].first = first;
+        M.g[g].count = c[g];
+        first += c[g];
+      }
+      DG_CUDA(traced(ms[idx[c0]], s, 6, [&] {
+                return f == 1 ? dgdev::launch_tc_mixed(M, first, s)
+                              : dgdev::launch_tt_mixed(M, first, s);
+              }), "mixed stage kernel launch");
+      ++launches;
+    }
+  }
+  for (int i = 0; i < n; ++i) ms[i]->last_launches = 0;
+  ms[0]->last_launches = launches;
+  return DG_OK;
+}
+
 int device_step(dg_mesh* m, float* u, float* res, double dt, int nsteps, void* stream,
                 std::string& err) {
   int rc = ensure_device(m, err);

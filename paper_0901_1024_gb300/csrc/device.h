@@ -90,6 +90,25 @@ __host__ __device__ constexpr int tc_b_bytes(int N) {
          ((3 * ((((N + 1) * (N + 2) * (N + 3) / 6) + 1) & ~1) + 4 * ((N + 1) * (N + 2) / 2) + 15) & ~15);
 }
 
+// One launch over the packs of several meshes (a group per mesh): the grid's
+// CTAs are split among the groups, CTAs [first, first + count) running group g
+// (its mesh, its order, its fields) as a persistent stage of `count` CTAs.
+constexpr int kMaxMixedGroups = 8;
+struct MixedGroup {
+  StageArgs a;
+  int N;
+  int ext;                 // 1: materials or absorbing faces (the EXT instantiation)
+  int first, count;
+};
+struct MixedArgs {
+  MixedGroup g[kMaxMixedGroups];
+  int ngroups;
+};
+// Fused RK stages of groups of orders 1..4 (tensor cores, one 640-thread CTA
+// per SM) or of orders 5, 6 (tensor cores, operator in tensor memory).
+cudaError_t launch_tc_mixed(const MixedArgs& m, int grid, cudaStream_t s);
+cudaError_t launch_tt_mixed(const MixedArgs& m, int grid, cudaStream_t s);
+
 // Launches one RK stage (rk = true: res <- a res + dt rhs, u_out <- u_in + b res)
 // or one bare right-hand-side evaluation (rk = false: rhs <- rhs(u_in)).
 cudaError_t launch_stage(int N, bool rk, const StageArgs& a, int num_sms, cudaStream_t s);

@@ -91,6 +91,9 @@ int device_stage(dg_mesh* m, const float* u_in, float* u_out, float* res, int st
                  const float* dt_elem, void* stream, std::string& err);
 int device_step(dg_mesh* m, float* u, float* res, double dt, int nsteps, void* stream,
                 std::string& err);
+int device_stage_multi(dg_mesh* const* ms, int n, const float* const* u_in, float* const* u_out,
+                       float* const* res, const float* const* dt_elem, int stage, double dt,
+                       const double* tile_cost, void* stream, std::string& err);
 int device_energy(dg_mesh* m, const float* u, double* out, void* stream, std::string& err);
 int device_energy_range(dg_mesh* m, const float* u, int64_t k0, int64_t k1, double* out,
                         void* stream, std::string& err);

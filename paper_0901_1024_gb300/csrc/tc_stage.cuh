@@ -479,8 +479,11 @@ __device__ __forceinline__ void tc_flux_items(const uint32_t (&item)[NI], const 
 
 // EXT: meshes with materials (A.mat) or absorbing faces; the vacuum instantiation
 // has none of that arithmetic.
+// The stage as run by one CTA: `cta` of `ncta` CTAs that share the tiles of A
+// (tile cta, cta + ncta, ...).  The kernels below run it as CTA cta of
+// the grid; the mixed-order kernel runs it for the group its CTA belongs to.
 template <int N, bool RK, bool EXT>
-__global__ void __launch_bounds__(TcDims<N>::THREADS, 1) tc_stage_kernel(const StageArgs A) {
+__device__ __forceinline__ void tc_stage_body(const StageArgs& A, const int cta, const int ncta) {
   using D = TcDims<N>;
   constexpr int E = D::E, Np = D::Np, Nfp = D::Nfp, FSTR = D::FSTR;
   extern __shared__ __align__(1024) unsigned char smem[];
@@ -492,8 +495,7 @@ __global__ void __launch_bounds__(TcDims<N>::THREADS, 1) tc_stage_kernel(const S
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int K = A.K;
-  const int ntiles = (A.num_tiles - int(blockIdx.x) + int(gridDim.x) - 1) / int(gridDim.x);
-  pdl_launch_dependents();
+  const int ntiles = (A.num_tiles - cta + ncta - 1) / ncta;
   if (ntiles <= 0) return;
 
   float* sU = reinterpret_cast<float*>(smem + D::OFF_U);
@@ -535,9 +537,9 @@ __global__ void __launch_bounds__(TcDims<N>::THREADS, 1) tc_stage_kernel(const S
     const uint32_t lane_off = uint32_t(warp * 32) << 16;
     if (warp == 0 && tc::elect_one()) {   // first loads: fields of tiles 0..NSU-2, res of tile 0
       for (int t = 0; t < D::NSU - 1 && t < ntiles; ++t)
-        tc_load_u<N>(A, blockIdx.x + t * gridDim.x, sU + t * D::U_FLOATS, sG + t * D::G_FLOATS,
+        tc_load_u<N>(A, cta + t * ncta, sU + t * D::U_FLOATS, sG + t * D::G_FLOATS,
                      &s_u_full[t]);
-      if (RK) tc_load_res<N>(A, blockIdx.x, sR, &s_r_full[0]);
+      if (RK) tc_load_res<N>(A, cta, sR, &s_r_full[0]);
     }
     __syncwarp();
     // Flux items of elements E0 .. E-1 (warps 1..3), computed one tile ahead
@@ -552,7 +554,7 @@ __global__ void __launch_bounds__(TcDims<N>::THREADS, 1) tc_stage_kernel(const S
     auto epilogue_fluxes = [&](int t) {
       if (warp != 0) {
         const int slot = t % D::NSU;
-        const int k0t = (int(blockIdx.x) + t * int(gridDim.x)) * E, Evt = min(E, K - k0t);
+        const int k0t = (cta + t * ncta) * E, Evt = min(E, K - k0t);
         wait_or_flag(&s_u_full[slot], (t / D::NSU) & 1, A.status);
         tc_flux_items<N, EXT, D::EITEMS>(eitem, A, k0t, Evt, sU + slot * D::U_FLOATS,
                                          sG + slot * D::G_FLOATS, sF2 + (t & 1) * D::F2_FLOATS,
@@ -593,7 +595,7 @@ __global__ void __launch_bounds__(TcDims<N>::THREADS, 1) tc_stage_kernel(const S
       }
       if (j >= 1) {                                  // epilogue of tile t = j - 1
         const int t = j - 1, buf = t & 1;
-        const int tile = blockIdx.x + t * gridDim.x;
+        const int tile = cta + t * ncta;
         const int k0 = tile * E, Ev = min(E, K - k0);
         float* su = sU + (t % D::NSU) * D::U_FLOATS;
         float* sr = sR + (t % D::NSR) * D::U_FLOATS;
@@ -604,12 +606,12 @@ __global__ void __launch_bounds__(TcDims<N>::THREADS, 1) tc_stage_kernel(const S
           tc::fence_proxy_async_smem();
           if (t + D::NSU - 1 < ntiles) {
             const int s = (t + D::NSU - 1) % D::NSU;
-            tc_load_u<N>(A, tile + (D::NSU - 1) * gridDim.x, sU + s * D::U_FLOATS,
+            tc_load_u<N>(A, tile + (D::NSU - 1) * ncta, sU + s * D::U_FLOATS,
                          sG + s * D::G_FLOATS, &s_u_full[s]);
           }
           if (RK && t + 1 < ntiles) {
             const int s = (t + 1) % D::NSR;
-            tc_load_res<N>(A, tile + gridDim.x, sR + s * D::U_FLOATS, &s_r_full[s]);
+            tc_load_res<N>(A, tile + ncta, sR + s * D::U_FLOATS, &s_r_full[s]);
           }
         }
         __syncwarp();
@@ -708,7 +710,7 @@ __global__ void __launch_bounds__(TcDims<N>::THREADS, 1) tc_stage_kernel(const S
 #pragma unroll
     for (int q = 0; q < D::ITEMS; ++q) item[q] = tc_item<N>(pt + q * D::PRODUCERS, D::E0, sFmask);
     for (int t = 0; t < ntiles; ++t) {
-      const int tile = blockIdx.x + t * gridDim.x;
+      const int tile = cta + t * ncta;
       const int k0 = tile * E, Ev = min(E, K - k0);
       const int slot = t % D::NSU, buf = t & 1;
       const float* su = sU + slot * D::U_FLOATS;
@@ -763,6 +765,12 @@ __global__ void __launch_bounds__(TcDims<N>::THREADS, 1) tc_stage_kernel(const S
   tc::fence_before_sync();
   __syncthreads();
   if (warp == 0) tc::tmem_dealloc(tbase, 512);
+}
+
+template <int N, bool RK, bool EXT>
+__global__ void __launch_bounds__(TcDims<N>::THREADS, 1) tc_stage_kernel(const __grid_constant__ StageArgs A) {
+  pdl_launch_dependents();
+  tc_stage_body<N, RK, EXT>(A, int(blockIdx.x), int(gridDim.x));
 }
 
 template <int N>

@@ -133,8 +133,11 @@ __device__ __forceinline__ void lds8(const float* p, float* v) {
 
 // EXT: meshes with materials (A.mat) or absorbing faces; the vacuum instantiation
 // has none of that arithmetic.
+// The stage as run by one CTA: `cta` of `ncta` CTAs that share the tiles of A
+// (tile cta, cta + ncta, ...).  The kernels below run it as CTA cta of
+// the grid; the mixed-order kernel runs it for the group its CTA belongs to.
 template <int N, bool RK, bool EXT>
-__global__ void __launch_bounds__(TtDims<N>::THREADS, 1) tt_stage_kernel(const StageArgs A) {
+__device__ __forceinline__ void tt_stage_body(const StageArgs& A, const int cta, const int ncta) {
   using D = TtDims<N>;
   constexpr int E = D::E, Np = D::Np, Nfp = D::Nfp, NF = D::NF, FSTR = D::FSTR, ROWS = D::ROWS;
   extern __shared__ __align__(1024) unsigned char smem[];
@@ -145,8 +148,7 @@ __global__ void __launch_bounds__(TtDims<N>::THREADS, 1) tt_stage_kernel(const S
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int K = A.K;
-  const int ntiles = (A.num_tiles - int(blockIdx.x) + int(gridDim.x) - 1) / int(gridDim.x);
-  pdl_launch_dependents();
+  const int ntiles = (A.num_tiles - cta + ncta - 1) / ncta;
   if (ntiles <= 0) return;
 
   unsigned char* sXhi = smem + D::OFF_X;
@@ -232,16 +234,16 @@ __global__ void __launch_bounds__(TtDims<N>::THREADS, 1) tt_stage_kernel(const S
     const uint32_t lane_off = uint32_t(warp * 32) << 16;
     if (warp == 3 && tc::elect_one()) {   // first loads: fields of tiles 0..NSU-2, res of tile 0
       for (int t = 0; t < D::NSU - 1 && t < ntiles; ++t)
-        tt_load_u<N>(A, blockIdx.x + t * gridDim.x, sU + t * D::U_FLOATS, sG + t * D::G_FLOATS,
+        tt_load_u<N>(A, cta + t * ncta, sU + t * D::U_FLOATS, sG + t * D::G_FLOATS,
                      &s_u_full[t]);
-      if (RK) tt_load_res<N>(A, blockIdx.x, sR, &s_r_full[0]);
+      if (RK) tt_load_res<N>(A, cta, sR, &s_r_full[0]);
     }
     __syncwarp();
     constexpr uint32_t IDESC = tc::idesc_f16(128, D::NN);
     constexpr uint32_t LBO = (D::NN / 8) * 128;
     for (int j = 0; j <= ntiles; ++j) {
       const int t = j - 1, buf = t & 1;               // tile whose update runs in iteration j
-      const int tile = blockIdx.x + t * gridDim.x;
+      const int tile = cta + t * ncta;
       const int k0 = tile * E, Ev = min(E, K - k0);
       if (warp == 3) {
         if (j < ntiles) {                              // MMAs of tile j into accumulator j & 1
@@ -267,12 +269,12 @@ __global__ void __launch_bounds__(TtDims<N>::THREADS, 1) tt_stage_kernel(const S
           tc::fence_proxy_async_smem();
           if (t + D::NSU - 1 < ntiles) {
             const int s = (t + D::NSU - 1) % D::NSU;
-            tt_load_u<N>(A, tile + (D::NSU - 1) * gridDim.x, sU + s * D::U_FLOATS,
+            tt_load_u<N>(A, tile + (D::NSU - 1) * ncta, sU + s * D::U_FLOATS,
                          sG + s * D::G_FLOATS, &s_u_full[s]);
           }
           if (RK && t + 1 < ntiles) {
             const int s = (t + 1) % D::NSR;
-            tt_load_res<N>(A, tile + gridDim.x, sR + s * D::U_FLOATS, &s_r_full[s]);
+            tt_load_res<N>(A, tile + ncta, sR + s * D::U_FLOATS, &s_r_full[s]);
           }
         }
         __syncwarp();
@@ -377,7 +379,7 @@ __global__ void __launch_bounds__(TtDims<N>::THREADS, 1) tt_stage_kernel(const S
     }
     float* F = sF;
     for (int t = 0; t < ntiles; ++t) {
-      const int tile = blockIdx.x + t * gridDim.x;
+      const int tile = cta + t * ncta;
       const int k0 = tile * E, Ev = min(E, K - k0);
       const int slot = t % D::NSU;
       const float* su = sU + slot * D::U_FLOATS;
@@ -554,6 +556,12 @@ __global__ void __launch_bounds__(TtDims<N>::THREADS, 1) tt_stage_kernel(const S
   tc::fence_before_sync();
   __syncthreads();
   if (warp == 0) tc::tmem_dealloc(tbase, 512);
+}
+
+template <int N, bool RK, bool EXT>
+__global__ void __launch_bounds__(TtDims<N>::THREADS, 1) tt_stage_kernel(const __grid_constant__ StageArgs A) {
+  pdl_launch_dependents();
+  tt_stage_body<N, RK, EXT>(A, int(blockIdx.x), int(gridDim.x));
 }
 
 template <int N>

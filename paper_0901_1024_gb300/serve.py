@@ -156,6 +156,17 @@ class _Pack:
     def state(self):
         return self.u if self.parity == 0 else self.work
 
+    def set_parity(self, parity):
+        """Put the state in the buffer of `parity` (0: u, 1: work) by swapping the
+        two tensors, so packs stepped together share one ping-pong parity."""
+        if parity != self.parity:
+            self.u, self.work = self.work, self.u
+            self.parity = parity
+
+    def buffers(self):
+        """(source, destination) of the next stage."""
+        return (self.u, self.work) if self.parity == 0 else (self.work, self.u)
+
     def release(self):
         """Drop the pack's graphs, fields and packed mesh (device memory goes
         back to the caching allocator at once, before the next pack is built)."""
@@ -194,14 +205,22 @@ class Server:
     autotune   : pick each pack's stage implementation by timing; else `impl`.
     keep_fields: return every solve's final fields (host FP32) in its Result.
     rebuild_every: steps a pack runs before waiting solves may join it.
+    mixed      : (with batch) advance all packs, of every order, with one
+                 dg_rk_stage_multi call per RK stage -- one shared persistent
+                 launch for orders 1..4 and one for 5, 6 -- its CTAs split by
+                 the tuned cost of a tile of each pack; graphs capture the five
+                 shared stages of the current set of packs.
     """
 
     def __init__(self, hbm_budget: float = 150e9, batch: bool = True, graphs: bool = True,
                  autotune: bool = True, impl: int = Mesh.STAGE_AUTO, keep_fields: bool = True,
-                 rebuild_every: int = 32):
+                 rebuild_every: int = 32, mixed: bool = True):
         import torch
         self.torch = torch
         self.budget, self.batch, self.graphs = hbm_budget, batch, graphs
+        self.mixed = mixed and batch
+        self._gparity = 0              # ping-pong parity shared by the packs (mixed)
+        self._gcache = {}              # (pack ids, parity) -> captured graph, or None: seen once
         self.rebuild_every = rebuild_every
         self.autotune, self.impl, self.keep = autotune, impl, keep_fields
         self.stream = torch.cuda.Stream()
@@ -212,6 +231,7 @@ class Server:
         self.stats = {}
 
     _tuned = {}                        # (device, N, decade of K) -> stage implementation
+    _cost = {}                         # (device, N, decade of K) -> ms per tile on one SM
 
     # ---- stage implementation per (N, K) ---------------------------------
     def _pad_mesh(self, N):
@@ -239,9 +259,15 @@ class Server:
             p.step()
         e1.record(self.stream)
         e1.synchronize()
+        ms = e0.elapsed_time(e1)
+        if impl == Mesh.STAGE_TC and N <= 6:
+            # one tile's cost on one SM: stage time x CTAs in use / tiles
+            tiles = -(-p.K // (20 if N <= 4 else 8))
+            sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+            self._cost[self._tune_key(N, solves)] = ms / 15 * min(tiles, sms) / tiles
         p.release()
         self._charge(-sum(s.bytes for s in solves))
-        return e0.elapsed_time(e1)
+        return ms
 
     def _choose_impl(self, N, solves):
         if not self.autotune:
@@ -279,8 +305,51 @@ class Server:
 
     def _new_pack(self, N, members, carry, impl):
         self._charge(sum(s.bytes for s in members))
-        return _Pack(self.torch, N, members, carry, self._pad_mesh(N), impl, self.graphs,
-                     self.stream)
+        p = _Pack(self.torch, N, members, carry, self._pad_mesh(N), impl,
+                  self.graphs and not self.mixed, self.stream)
+        if self.mixed:
+            p.set_parity(self._gparity)
+            p.cost = self._cost.get(self._tune_key(N, members))
+        return p
+
+    # ---- all packs in shared launches ------------------------------------------
+    def _stages_mixed(self, packs, par):
+        meshes = [p.mesh for p in packs]
+        bufs = [p.buffers() for p in packs]
+        src, dst = [b[0] for b in bufs], [b[1] for b in bufs]
+        res = [p.res for p in packs]
+        dts = [p.dt_elem for p in packs]
+        costs = None
+        if all(getattr(p, "cost", None) for p in packs):
+            costs = [p.cost for p in packs]
+        for i in range(_RK_STAGES):
+            Mesh.rk_stage_multi(meshes, src, dst, res, i, dt_elem=dts, tile_cost=costs,
+                                stream=self.stream)
+            src, dst = dst, src
+
+    def _step_mixed(self, packs):
+        """One LSERK4 step of every pack: five dg_rk_stage_multi calls, replayed
+        from a graph once the same set of packs is stepped a second time."""
+        torch = self.torch
+        key = (tuple(id(p) for p in packs), self._gparity)
+        g = self._gcache.get(key, False)
+        if g is False or not self.graphs:
+            if self.graphs:
+                # a new set of packs: forget the graphs of earlier sets
+                self._gcache = {k: v for k, v in self._gcache.items() if k[0] == key[0]}
+                self._gcache[key] = None
+            self._stages_mixed(packs, self._gparity)
+        elif g is None:
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g, stream=self.stream):
+                self._stages_mixed(packs, self._gparity)
+            self._gcache[key] = g
+            g.replay()
+        else:
+            g.replay()
+        for p in packs:
+            p.parity ^= 1
+        self._gparity ^= 1
 
     def _build(self, N, members, old, st):
         """A pack of `members` (live solves of order N), continuing from the
@@ -389,8 +458,11 @@ class Server:
                     waiting = []
                 ts = time.perf_counter()
                 st["pack_s"] += ts - tp
-                for p in packs:
-                    p.step()
+                if self.mixed and packs:
+                    self._step_mixed(packs)
+                else:
+                    for p in packs:
+                        p.step()
                 st["iterations"] += 1
                 tr = time.perf_counter()
                 st["step_s"] += tr - ts

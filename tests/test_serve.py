@@ -1,7 +1,8 @@
 """Serving loop (paper_0901_1024_gb300/serve.py) on the GPU: every solve's
 fields are the same alone and in the mix -- bit for bit on the same stage
 implementation -- whether solves are packed into one launch per order or
-stepped one by one, replayed from CUDA graphs or launched directly, admitted
+stepped one by one, packs of all orders advanced by shared launches or one
+launch per pack, replayed from CUDA graphs or launched directly, admitted
 together or one at a time by a small HBM budget."""
 import numpy as np
 import pytest
@@ -46,11 +47,15 @@ def _check_against_alone(serve, dg, results, reqs, impl):
         assert res.finished >= res.admitted >= res.arrival - 1e-9
 
 
-@pytest.mark.parametrize("batch,graphs", [(True, True), (True, False), (False, False)])
-def test_same_alone_and_in_the_mix(env, batch, graphs):
+@pytest.mark.parametrize("batch,graphs,mixed", [(True, True, True), (True, False, True),
+                                                 (True, True, False), (False, False, False)])
+def test_same_alone_and_in_the_mix(env, batch, graphs, mixed):
+    """mixed: every pack, of every order, advanced by shared launches
+    (dg_rk_stage_multi); else one launch per pack and stage."""
     torch, dg, serve = env
     reqs = _requests(serve)
-    srv = serve.Server(batch=batch, graphs=graphs, autotune=False, impl=dg.Mesh.STAGE_TC)
+    srv = serve.Server(batch=batch, graphs=graphs, autotune=False, impl=dg.Mesh.STAGE_TC,
+                       mixed=mixed)
     results = srv.run(reqs, max_iterations=200_000)
     _check_against_alone(serve, dg, results, reqs, dg.Mesh.STAGE_TC)
 

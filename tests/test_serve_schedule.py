@@ -40,7 +40,7 @@ class FakePack:
 class FakeServer(serve.Server):
     def __init__(self, budget=1e18, batch=True, rebuild_every=4):
         self.budget, self.batch, self.rebuild_every = budget, batch, rebuild_every
-        self.graphs, self.autotune, self.keep = False, False, False
+        self.graphs, self.autotune, self.keep, self.mixed = False, False, False, False
         self.stats, self.live_log = {}, []
 
     def _admit(self, req, now):
