@@ -552,12 +552,14 @@ SERVE_CONFIGS = {
 
 
 def run_serve(args):
-    """Solves/s and latency percentiles of a request set, three ways on the same
-    GPU: the continuous-batching server (packed launches, CUDA graphs, autotuned
-    stage kernels); the per-solve form with the same kernels (one solve at a
-    time, its own launches); and the plain per-solve form (one solve at a time
-    on the FP32 CUDA-core stage).  `--serve-config served` is a Poisson stream
-    at `--rate`; `batched` releases all solves at once."""
+    """Solves/s and latency percentiles of a request set, four ways on the same
+    GPU: the continuous-batching server (one packed launch per order and stage,
+    CUDA graphs, autotuned stage kernels); the same server advancing the packs
+    of every order by shared launches (dg_rk_stage_multi); the per-solve form
+    with the same kernels (one solve at a time, its own launches); and the plain
+    per-solve form (one solve at a time on the FP32 CUDA-core stage).
+    `--serve-config served` is a Poisson stream at `--rate`; `batched` releases
+    all solves at once."""
     import torch
     from paper_0901_1024_gb300 import Mesh
     from paper_0901_1024_gb300.serve import Server
@@ -588,7 +590,9 @@ def run_serve(args):
         return res, summary(res, time.perf_counter() - t0, srv)
 
     served, ours = timed(Server(batch=True, graphs=not args.serve_no_graphs, autotune=True,
-                                rebuild_every=args.rebuild_every))
+                                rebuild_every=args.rebuild_every, mixed=False))
+    _, shared = timed(Server(batch=True, graphs=not args.serve_no_graphs, autotune=True,
+                             rebuild_every=args.rebuild_every, mixed=True))
     same, base = timed(Server(hbm_budget=1.0, batch=False, graphs=False, autotune=False))
     plain_res, plain = timed(Server(hbm_budget=1.0, batch=False, graphs=False, autotune=False,
                                     impl=Mesh.STAGE_FP32))
@@ -609,7 +613,9 @@ def run_serve(args):
             "config": {"workload": workload,
                        "server": "continuous batching: one packed launch per RK stage and order, "
                                  "CUDA graphs, autotuned stage kernel per (N, K), HBM budget 150 GB"},
-            "served": ours, "one_at_a_time_same_kernels": base, "plain_one_at_a_time_fp32": plain,
+            "served": ours, "shared_launch_all_orders": shared,
+            "one_at_a_time_same_kernels": base, "plain_one_at_a_time_fp32": plain,
+            "speedup_of_shared_launch": shared["solves_per_s"] / ours["solves_per_s"],
             "speedup_vs_same_kernels": ours["solves_per_s"] / base["solves_per_s"],
             "speedup_vs_plain": ours["solves_per_s"] / plain["solves_per_s"],
             "max_rel_l2_vs_same_kernels": worst(served, same),
@@ -620,8 +626,9 @@ def run_serve(args):
 def run_sweep(args):
     """Roofline curve over the order: for N = 1..9 a pulse workload on a box mesh
     with n chosen so that 6 K Np is about 1.7e7, timed per stage launch (CUDA
-    events around back-to-back steps, divided by the stage count) after warm-up, for the default stage kernel (tensor cores for
-    N = 2..6, FP32 CUDA cores otherwise) and, for N = 2..6, the FP32 kernel as well."""
+    events around back-to-back steps, divided by the stage count) after warm-up,
+    for the default stage kernel (tensor cores for N = 2..6, FP32 CUDA cores
+    otherwise) and, for N = 2..6, the FP32 kernel as well."""
     import torch
     import paper_0901_1024_gb300 as dg
     peaks, _ = load_peaks()

@@ -860,15 +860,15 @@ int device_stage_multi(dg_mesh* const* ms, int n, const float* const* u_in, floa
       }
       const int total = static_cast<int>(std::min<int64_t>(sms, all));
       const std::vector<int> c = split_ctas(tiles, cost, total);
-      int first = 0;
+      int grid = 0;
       for (size_t g = 0; g < ng; ++g) {
-        M.g[g].first = first;
+        M.g[g].first = grid;
         M.g[g].count = c[g];
-        first += c[g];
+        grid += c[g];
       }
-      DG_CUDA(traced(ms[idx[c0]], s, 6, [&] {
-                return f == 1 ? dgdev::launch_tc_mixed(M, first, s)
-                              : dgdev::launch_tt_mixed(M, first, s);
+      DG_CUDA(traced(ms[0], s, 6, [&] {
+                return f == 1 ? dgdev::launch_tc_mixed(M, grid, s)
+                              : dgdev::launch_tt_mixed(M, grid, s);
               }), "mixed stage kernel launch");
       ++launches;
     }

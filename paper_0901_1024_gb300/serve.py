@@ -209,12 +209,15 @@ class Server:
                  dg_rk_stage_multi call per RK stage -- one shared persistent
                  launch for orders 1..4 and one for 5, 6 -- its CTAs split by
                  the tuned cost of a tile of each pack; graphs capture the five
-                 shared stages of the current set of packs.
+                 shared stages of the current set of packs.  Off by default:
+                 on GB300 different orders side by side in one grid measured
+                 12 % slower than one launch per order (packs of one order
+                 gain 10 %), see the benchmark's serve mode.
     """
 
     def __init__(self, hbm_budget: float = 150e9, batch: bool = True, graphs: bool = True,
                  autotune: bool = True, impl: int = Mesh.STAGE_AUTO, keep_fields: bool = True,
-                 rebuild_every: int = 32, mixed: bool = True):
+                 rebuild_every: int = 32, mixed: bool = False):
         import torch
         self.torch = torch
         self.budget, self.batch, self.graphs = hbm_budget, batch, graphs
