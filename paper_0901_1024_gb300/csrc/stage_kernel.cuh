@@ -31,6 +31,7 @@
 
 #include "device.h"
 #include "launch.cuh"
+#include "tcgen05.cuh"
 
 namespace dgdev {
 
@@ -50,9 +51,19 @@ template <int N> struct StageDims {
   // per CTA, next to the tile (they fit there; above N = 6 they are read through L1)
   static constexpr bool OPS_SMEM = N == 5 || N == 6;
   static constexpr int OT = OPS_SMEM ? 4 * Np * Np + Np * NF : 0;
-  static constexpr size_t smem_bytes = size_t(UT + FT + GT + OT) * sizeof(float);
+  // orders 7, 8: Dr/Ds/Dt (230, 436 KB) are streamed through shared memory in
+  // chunks of JC columns, two buffers: the copy of chunk c+1 (16-byte
+  // asynchronous copies) runs while chunk c is multiplied (12 % faster than
+  // reading them through L1; at N = 9 the chunks that fit, 11 columns, cost
+  // more in barriers than they save, so N = 9 reads through L1)
+  static constexpr bool OPS_STREAM = N == 7 || N == 8;
+  static constexpr int JC = N == 7 ? 24 : 15;                 // divides Np
+  static constexpr int NCH = (Np + JC - 1) / JC;
+  static constexpr int CT = OPS_STREAM ? 2 * 4 * Np * JC : 0;  // floats of the two chunk buffers
+  static constexpr size_t smem_bytes = size_t(UT + FT + GT + OT + CT) * sizeof(float);
   static_assert(smem_bytes <= 227 * 1024, "shared memory budget");
-  static_assert((UT % 4) == 0 && (FT % 4) == 0, "tiles must stay 16-byte aligned");
+  static_assert((UT % 4) == 0 && (FT % 4) == 0 && (GT % 4) == 0, "tiles must stay 16-byte aligned");
+  static_assert(!OPS_STREAM || Np % JC == 0, "operator chunks tile the columns");
 };
 
 // EXT: meshes with materials (A.mat) or absorbing faces; the vacuum
@@ -80,11 +91,27 @@ __global__ void __launch_bounds__(StageDims<N>::T) stage_kernel(const StageArgs 
   }
   const int e = tid % E, g = tid / E;
   const int K = A.K;
+  // orders 7, 8: chunk c (columns [c JC, c JC + JC) of Dr/Ds/Dt, all rows) goes to
+  // buffer gc & 1, gc = pass * NCH + c counting the chunks of a tile's two passes
+  float4* cbuf = reinterpret_cast<float4*>(sg + D::GT + D::OT);
+  auto issue_chunk = [&](int c, int b) {
+    if constexpr (D::OPS_STREAM) {
+      float4* dst = cbuf + b * Np * D::JC;
+      for (int i = tid; i < Np * D::JC; i += D::T) {
+        const int r = i / D::JC, jj = i - r * D::JC;
+        tc::cp_async16(dst + i, A.D4 + r * Np + c * D::JC + jj);
+      }
+      tc::cp_async_commit();
+    }
+  };
   pdl_wait();        // the previous kernel's fields are complete (operators are constant)
 
   for (int tile = blockIdx.x; tile < A.num_tiles; tile += gridDim.x) {
     const int k0 = tile * E;
     const int Ev = min(E, K - k0);
+    // the first operator chunk flies while the tile is staged and its fluxes formed
+    // (buffer 0 was last read before the previous tile's final barriers)
+    issue_chunk(0, 0);
 
     // ---- 1. stage geometry and fields -------------------------------------
     for (int idx = tid; idx < Ev * (kGeoWords / 4); idx += D::T)
@@ -191,21 +218,45 @@ __global__ void __launch_bounds__(StageDims<N>::T) stage_kernel(const StageArgs 
           for (int d = 0; d < 3; ++d)
 #pragma unroll
             for (int q = 0; q < R; ++q) acc[c][d][q] = 0.f;
-#pragma unroll 5
-        for (int j = 0; j < Np; ++j) {
-          const float v0 = u0[j], v1 = u1[j], v2 = u2[j];
+        auto mac = [&](const float4& dm, int q, float v0, float v1, float v2) {
+          acc[0][0][q] = fmaf(dm.x, v0, acc[0][0][q]);
+          acc[0][1][q] = fmaf(dm.y, v0, acc[0][1][q]);
+          acc[0][2][q] = fmaf(dm.z, v0, acc[0][2][q]);
+          acc[1][0][q] = fmaf(dm.x, v1, acc[1][0][q]);
+          acc[1][1][q] = fmaf(dm.y, v1, acc[1][1][q]);
+          acc[1][2][q] = fmaf(dm.z, v1, acc[1][2][q]);
+          acc[2][0][q] = fmaf(dm.x, v2, acc[2][0][q]);
+          acc[2][1][q] = fmaf(dm.y, v2, acc[2][1][q]);
+          acc[2][2][q] = fmaf(dm.z, v2, acc[2][2][q]);
+        };
+        if constexpr (D::OPS_STREAM) {
+#pragma unroll 1
+          for (int c = 0; c < D::NCH; ++c) {
+            const int gc = pass * D::NCH + c;
+            if (gc + 1 < 2 * D::NCH) {
+              issue_chunk((gc + 1) % D::NCH, (gc + 1) & 1);
+              tc::cp_async_wait_group<1>();            // chunk gc has landed (this thread's)
+            } else {
+              tc::cp_async_wait_group<0>();
+            }
+            __syncthreads();                           // everyone's copies of chunk gc
+            const float4* cb = cbuf + (gc & 1) * Np * D::JC;
+#pragma unroll 4
+            for (int jj = 0; jj < D::JC; ++jj) {
+              const int j = c * D::JC + jj;
+              const float v0 = u0[j], v1 = u1[j], v2 = u2[j];
 #pragma unroll
-          for (int q = 0; q < R; ++q) {
-            const float4 dm = D::OPS_SMEM ? D4[row[q] * Np + j] : __ldg(&A.D4[row[q] * Np + j]);
-            acc[0][0][q] = fmaf(dm.x, v0, acc[0][0][q]);
-            acc[0][1][q] = fmaf(dm.y, v0, acc[0][1][q]);
-            acc[0][2][q] = fmaf(dm.z, v0, acc[0][2][q]);
-            acc[1][0][q] = fmaf(dm.x, v1, acc[1][0][q]);
-            acc[1][1][q] = fmaf(dm.y, v1, acc[1][1][q]);
-            acc[1][2][q] = fmaf(dm.z, v1, acc[1][2][q]);
-            acc[2][0][q] = fmaf(dm.x, v2, acc[2][0][q]);
-            acc[2][1][q] = fmaf(dm.y, v2, acc[2][1][q]);
-            acc[2][2][q] = fmaf(dm.z, v2, acc[2][2][q]);
+              for (int q = 0; q < R; ++q) mac(cb[row[q] * D::JC + jj], q, v0, v1, v2);
+            }
+            __syncthreads();                           // buffer gc & 1 may be refilled
+          }
+        } else {
+#pragma unroll 5
+          for (int j = 0; j < Np; ++j) {
+            const float v0 = u0[j], v1 = u1[j], v2 = u2[j];
+#pragma unroll
+            for (int q = 0; q < R; ++q)
+              mac(D::OPS_SMEM ? D4[row[q] * Np + j] : __ldg(&A.D4[row[q] * Np + j]), q, v0, v1, v2);
           }
         }
 #pragma unroll
