@@ -591,8 +591,10 @@ def run_serve(args):
 
     served, ours = timed(Server(batch=True, graphs=not args.serve_no_graphs, autotune=True,
                                 rebuild_every=args.rebuild_every, mixed=False))
-    _, shared = timed(Server(batch=True, graphs=not args.serve_no_graphs, autotune=True,
-                             rebuild_every=args.rebuild_every, mixed=True))
+    shared = None
+    if args.serve_shared:
+        _, shared = timed(Server(batch=True, graphs=not args.serve_no_graphs, autotune=True,
+                                 rebuild_every=args.rebuild_every, mixed=True))
     same, base = timed(Server(hbm_budget=1.0, batch=False, graphs=False, autotune=False))
     plain_res, plain = timed(Server(hbm_budget=1.0, batch=False, graphs=False, autotune=False,
                                     impl=Mesh.STAGE_FP32))
@@ -615,7 +617,8 @@ def run_serve(args):
                                  "CUDA graphs, autotuned stage kernel per (N, K), HBM budget 150 GB"},
             "served": ours, "shared_launch_all_orders": shared,
             "one_at_a_time_same_kernels": base, "plain_one_at_a_time_fp32": plain,
-            "speedup_of_shared_launch": shared["solves_per_s"] / ours["solves_per_s"],
+            "speedup_of_shared_launch": (shared["solves_per_s"] / ours["solves_per_s"]
+                                         if shared else None),
             "speedup_vs_same_kernels": ours["solves_per_s"] / base["solves_per_s"],
             "speedup_vs_plain": ours["solves_per_s"] / plain["solves_per_s"],
             "max_rel_l2_vs_same_kernels": worst(served, same),
@@ -690,6 +693,8 @@ def main():
     ap.add_argument("--rebuild-every", type=int, default=32,
                     help="serve mode: steps a pack runs before waiting solves join it")
     ap.add_argument("--serve-no-graphs", action="store_true")
+    ap.add_argument("--serve-shared", action="store_true",
+                    help="serve mode: also time the server with shared launches of all orders")
     ap.add_argument("--rate", type=float, default=200.0)
     ap.add_argument("--serve-config", default="served", choices=sorted(SERVE_CONFIGS),
                     help="request set of --mode serve: a Poisson stream, or solves released together")
