@@ -105,9 +105,10 @@ def load_peaks():
 # Source files of each stage kernel family: a profile summary records the
 # digest of the family it measured.
 KERNEL_SOURCES = {
-    "tc": ("tc_stage.cuh", "tcgen05.cuh", "device.h"),                    # tensor cores, N <= 4
-    "tt": ("tc_stage_t.cuh", "tc_stage.cuh", "tcgen05.cuh", "device.h"),  # tensor cores, N = 5, 6
-    "fp32": ("stage_kernel.cuh", "device.h"),                             # CUDA cores
+    "tc": ("tc_stage.cuh", "tcgen05.cuh", "launch.cuh", "device.h"),      # tensor cores, N <= 4
+    "tt": ("tc_stage_t.cuh", "tc_stage.cuh", "tcgen05.cuh", "launch.cuh",
+           "device.h"),                                                   # tensor cores, N = 5, 6
+    "fp32": ("stage_kernel.cuh", "tcgen05.cuh", "launch.cuh", "device.h"),  # CUDA cores
 }
 
 

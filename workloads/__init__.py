@@ -146,4 +146,7 @@ WORKLOADS = {
     "pulse_n24_N4": dict(n=24, N=4, jitter=0.15, seed=0, init="pulse", width=0.2, pulse_seed=1, steps=100),
     # Higher order: N=6 on 16^3 x 6 = 24 576 tets, cavity mode, 200 steps.
     "cavity_n16_N6": dict(n=16, N=6, jitter=0.10, seed=0, init="cavity", steps=200),
+    # Highest order of the served stream: N=7 on 16^3 x 6 = 24 576 tets, Gaussian pulse.
+    "pulse_n16_N7": dict(n=16, N=7, jitter=0.15, seed=0, init="pulse", width=0.2, pulse_seed=1,
+                         steps=20),
 }
