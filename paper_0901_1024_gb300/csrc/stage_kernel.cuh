@@ -59,11 +59,15 @@ template <int N> struct StageDims {
   static constexpr bool OPS_STREAM = N == 7 || N == 8;
   static constexpr int JC = N == 7 ? 24 : 15;                 // divides Np
   static constexpr int NCH = (Np + JC - 1) / JC;
+  // then LIFT in chunks of MC float4 columns (4 MC face nodes) through the same buffers
+  static constexpr int MC = N == 7 ? 18 : 15;
+  static constexpr int NLC = NF / 4 / MC;
   static constexpr int CT = OPS_STREAM ? 2 * 4 * Np * JC : 0;  // floats of the two chunk buffers
   static constexpr size_t smem_bytes = size_t(UT + FT + GT + OT + CT) * sizeof(float);
   static_assert(smem_bytes <= 227 * 1024, "shared memory budget");
   static_assert((UT % 4) == 0 && (FT % 4) == 0 && (GT % 4) == 0, "tiles must stay 16-byte aligned");
-  static_assert(!OPS_STREAM || Np % JC == 0, "operator chunks tile the columns");
+  static_assert(!OPS_STREAM || (Np % JC == 0 && NF / 4 % MC == 0 && MC <= JC),
+                "operator chunks tile the columns and fit the buffers");
 };
 
 // EXT: meshes with materials (A.mat) or absorbing faces; the vacuum
@@ -91,15 +95,25 @@ __global__ void __launch_bounds__(StageDims<N>::T) stage_kernel(const StageArgs 
   }
   const int e = tid % E, g = tid / E;
   const int K = A.K;
-  // orders 7, 8: chunk c (columns [c JC, c JC + JC) of Dr/Ds/Dt, all rows) goes to
-  // buffer gc & 1, gc = pass * NCH + c counting the chunks of a tile's two passes
+  // orders 7, 8: a tile streams 2 NCH + NLC chunks, chunk gc into buffer gc & 1:
+  // gc < 2 NCH columns [c JC, c JC + JC) of Dr/Ds/Dt (c = gc mod NCH, once per
+  // pass), then LIFT columns [lc MC, lc MC + MC) of the float4 rows (lc = gc - 2 NCH)
   float4* cbuf = reinterpret_cast<float4*>(sg + D::GT + D::OT);
-  auto issue_chunk = [&](int c, int b) {
+  auto issue_chunk = [&](int gc, int b) {
     if constexpr (D::OPS_STREAM) {
       float4* dst = cbuf + b * Np * D::JC;
-      for (int i = tid; i < Np * D::JC; i += D::T) {
-        const int r = i / D::JC, jj = i - r * D::JC;
-        tc::cp_async16(dst + i, A.D4 + r * Np + c * D::JC + jj);
+      if (gc < 2 * D::NCH) {
+        const int c = gc % D::NCH;
+        for (int i = tid; i < Np * D::JC; i += D::T) {
+          const int r = i / D::JC, jj = i - r * D::JC;
+          tc::cp_async16(dst + i, A.D4 + r * Np + c * D::JC + jj);
+        }
+      } else {
+        const int lc = gc - 2 * D::NCH;
+        for (int i = tid; i < Np * D::MC; i += D::T) {
+          const int r = i / D::MC, mm = i - r * D::MC;
+          tc::cp_async16(dst + i, A.LIFT4 + r * (NF / 4) + lc * D::MC + mm);
+        }
       }
       tc::cp_async_commit();
     }
@@ -233,12 +247,8 @@ __global__ void __launch_bounds__(StageDims<N>::T) stage_kernel(const StageArgs 
 #pragma unroll 1
           for (int c = 0; c < D::NCH; ++c) {
             const int gc = pass * D::NCH + c;
-            if (gc + 1 < 2 * D::NCH) {
-              issue_chunk((gc + 1) % D::NCH, (gc + 1) & 1);
-              tc::cp_async_wait_group<1>();            // chunk gc has landed (this thread's)
-            } else {
-              tc::cp_async_wait_group<0>();
-            }
+            issue_chunk(gc + 1, (gc + 1) & 1);         // the next chunk (LIFT after the last)
+            tc::cp_async_wait_group<1>();              // chunk gc has landed (this thread's)
             __syncthreads();                           // everyone's copies of chunk gc
             const float4* cb = cbuf + (gc & 1) * Np * D::JC;
 #pragma unroll 4
@@ -279,7 +289,43 @@ __global__ void __launch_bounds__(StageDims<N>::T) stage_kernel(const StageArgs 
     }
 
     // ---- 4. lifting ------------------------------------------------------
-    {
+    if constexpr (D::OPS_STREAM) {
+      const float4* f4[6];
+#pragma unroll
+      for (int c = 0; c < 6; ++c) f4[c] = reinterpret_cast<const float4*>(sf + (c * E + e) * FS);
+#pragma unroll 1
+      for (int lc = 0; lc < D::NLC; ++lc) {
+        const int gc = 2 * D::NCH + lc;
+        if (lc + 1 < D::NLC) {
+          issue_chunk(gc + 1, (gc + 1) & 1);
+          tc::cp_async_wait_group<1>();
+        } else {
+          tc::cp_async_wait_group<0>();
+        }
+        __syncthreads();
+        const float4* cb = cbuf + (gc & 1) * Np * D::JC;
+#pragma unroll 3
+        for (int mm = 0; mm < D::MC; ++mm) {
+          float4 fv[6];
+#pragma unroll
+          for (int c = 0; c < 6; ++c) fv[c] = f4[c][lc * D::MC + mm];
+#pragma unroll
+          for (int q = 0; q < R; ++q) {
+            const float4 L = cb[row[q] * D::MC + mm];
+#pragma unroll
+            for (int c = 0; c < 6; ++c) {
+              float s = rhs[c][q];
+              s = fmaf(L.x, fv[c].x, s);
+              s = fmaf(L.y, fv[c].y, s);
+              s = fmaf(L.z, fv[c].z, s);
+              s = fmaf(L.w, fv[c].w, s);
+              rhs[c][q] = s;
+            }
+          }
+        }
+        __syncthreads();
+      }
+    } else {
       const float4* f4[6];
 #pragma unroll
       for (int c = 0; c < 6; ++c) f4[c] = reinterpret_cast<const float4*>(sf + (c * E + e) * FS);
