@@ -189,6 +189,16 @@ int dg_set_boundary(dg_mesh* mesh, const int8_t* kind);
 #define DG_STAGE_TC   2
 int dg_set_stage_impl(dg_mesh* mesh, int impl);
 
+/* Tile shape of the FP32 CUDA-core stage (orders 1 and >= 7 by default, any
+ * order with DG_STAGE_FP32): 0 (default) the tile sizes measured fastest on
+ * large meshes, 1 half the tetrahedra per tile with the same matrix rows per
+ * thread (twice the CTAs of a small mesh, half the shared tiles).  The tile
+ * size is the analogue of the work partitioning the paper tunes empirically
+ * (Section 6); the serving loop's autotuner picks it per order and size.
+ * Results are the same to rounding.  Host only.  Errors: DG_ERR_ARG (NULL
+ * mesh, shape other than 0 or 1). */
+int dg_set_stage_shape(dg_mesh* mesh, int shape);
+
 /*
  * One evaluation of the semi-discrete operator (Eq. semidiscrete-dg):
  * rhs = curl terms (local differentiation, Alg. 4) + LIFT * flux (flux

@@ -138,6 +138,11 @@ class Mesh:
         """0 = auto (tensor cores for N = 2..6), 1 = FP32 CUDA cores, 2 = tensor cores."""
         check(self._lib.dg_set_stage_impl(self._h, int(impl)), "dg_set_stage_impl")
 
+    def set_stage_shape(self, shape: int):
+        """dg_set_stage_shape: FP32 stage tile shape, 0 (default) or 1 (half the
+        tetrahedra per tile)."""
+        check(self._lib.dg_set_stage_shape(self._h, int(shape)), "dg_set_stage_shape")
+
     def set_energy_check(self, max_growth: float):
         """dg_set_energy_check: step_host fails with DG_ERR_UNSTABLE when the
         energy grows by more than the factor 1 + max_growth (< 0: off)."""

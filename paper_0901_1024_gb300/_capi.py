@@ -33,6 +33,7 @@ SIGNATURES = {
     "dg_set_boundary": (C.c_int, [_vp, _vp]),
     "dg_set_stage_impl": (C.c_int, [_vp, C.c_int]),
     "dg_set_energy_check": (C.c_int, [_vp, C.c_double]),
+    "dg_set_stage_shape": (C.c_int, [_vp, C.c_int]),
     "dg_rhs": (C.c_int, [_vp, _vp, _vp, _vp]),
     "dg_step": (C.c_int, [_vp, _vp, _vp, C.c_double, C.c_int, _vp]),
     "dg_rk_stage": (C.c_int, [_vp, _vp, _vp, _vp, C.c_int, C.c_double, _vp]),

@@ -8,6 +8,7 @@
 #include <new>
 #include <string>
 
+#include "device.h"
 #include "dg_internal.h"
 
 namespace {
@@ -322,6 +323,13 @@ int dg_set_energy_check(dg_mesh* m, double max_growth) {
   if (int rc = check_mesh(m, false)) return rc;
   if (std::isnan(max_growth)) return fail(DG_ERR_ARG, "max_growth is NaN");
   m->energy_check = max_growth;
+  return DG_OK;
+}
+
+int dg_set_stage_shape(dg_mesh* m, int shape) {
+  if (int rc = check_mesh(m, false)) return rc;
+  if (shape < 0 || shape >= dgdev::kStageShapes) return fail(DG_ERR_ARG, "unknown stage shape");
+  m->stage_shape = shape;
   return DG_OK;
 }
 

@@ -21,7 +21,7 @@
 namespace dgdev {
 
 template <int N>
-cudaError_t launch_stage_n(bool rk, const StageArgs& a, int num_sms, cudaStream_t s);
+cudaError_t launch_stage_n(bool rk, const StageArgs& a, int num_sms, cudaStream_t s, int shape);
 
 template <int N>
 cudaError_t launch_tc_stage_n(bool rk, const StageArgs& a, int num_sms, cudaStream_t s);
@@ -40,17 +40,18 @@ cudaError_t launch_tc_stage(int N, bool rk, const StageArgs& a, int num_sms, cud
   }
 }
 
-cudaError_t launch_stage(int N, bool rk, const StageArgs& a, int num_sms, cudaStream_t s) {
+cudaError_t launch_stage(int N, bool rk, const StageArgs& a, int num_sms, cudaStream_t s,
+                         int shape) {
   switch (N) {
-    case 1: return launch_stage_n<1>(rk, a, num_sms, s);
-    case 2: return launch_stage_n<2>(rk, a, num_sms, s);
-    case 3: return launch_stage_n<3>(rk, a, num_sms, s);
-    case 4: return launch_stage_n<4>(rk, a, num_sms, s);
-    case 5: return launch_stage_n<5>(rk, a, num_sms, s);
-    case 6: return launch_stage_n<6>(rk, a, num_sms, s);
-    case 7: return launch_stage_n<7>(rk, a, num_sms, s);
-    case 8: return launch_stage_n<8>(rk, a, num_sms, s);
-    case 9: return launch_stage_n<9>(rk, a, num_sms, s);
+    case 1: return launch_stage_n<1>(rk, a, num_sms, s, shape);
+    case 2: return launch_stage_n<2>(rk, a, num_sms, s, shape);
+    case 3: return launch_stage_n<3>(rk, a, num_sms, s, shape);
+    case 4: return launch_stage_n<4>(rk, a, num_sms, s, shape);
+    case 5: return launch_stage_n<5>(rk, a, num_sms, s, shape);
+    case 6: return launch_stage_n<6>(rk, a, num_sms, s, shape);
+    case 7: return launch_stage_n<7>(rk, a, num_sms, s, shape);
+    case 8: return launch_stage_n<8>(rk, a, num_sms, s, shape);
+    case 9: return launch_stage_n<9>(rk, a, num_sms, s, shape);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -689,7 +690,7 @@ static dgdev::StageArgs stage_args(dg_mesh* m, bool tc) {
   a.perm = d->perm;
   a.K = static_cast<int>(d->K);
   a.alpha = static_cast<float>(m->alpha);
-  const int E = tc ? dgdev::tc_tile_elems(d->N) : dgdev::stage_tile_elems(d->N);
+  const int E = tc ? dgdev::tc_tile_elems(d->N) : dgdev::stage_tile_elems(d->N, m->stage_shape);
   a.num_tiles = static_cast<int>((d->K + E - 1) / E);
   return a;
 }
@@ -704,7 +705,8 @@ int device_rhs(dg_mesh* m, const float* u, float* rhs, void* stream, std::string
   a.rhs = rhs;
   DG_CUDA(traced(m, s, tc ? 5 : 1, [&] {
             return tc ? dgdev::launch_tc_stage(m->N, false, a, m->dev->num_sms, s)
-                             : dgdev::launch_stage(m->N, false, a, m->dev->num_sms, s);
+                             : dgdev::launch_stage(m->N, false, a, m->dev->num_sms, s,
+                                                   m->stage_shape);
           }), "stage kernel launch");
   m->last_launches = 1;
   return DG_OK;
@@ -741,7 +743,7 @@ static int step_impl(dg_mesh* m, float* u, float* res, double dt, int nsteps, cu
       a.b = static_cast<float>(kRkB[i]);
       DG_CUDA(traced(m, s, tc ? 4 : 0, [&] {
                 return tc ? dgdev::launch_tc_stage(m->N, true, a, d->num_sms, s)
-                          : dgdev::launch_stage(m->N, true, a, d->num_sms, s);
+                          : dgdev::launch_stage(m->N, true, a, d->num_sms, s, m->stage_shape);
               }), "stage kernel launch");
       ++launches;
       float* nsrc = dst;
@@ -772,7 +774,7 @@ int device_stage(dg_mesh* m, const float* u_in, float* u_out, float* res, int st
   a.b = static_cast<float>(kRkB[stage]);
   DG_CUDA(traced(m, s, tc ? 4 : 0, [&] {
             return tc ? dgdev::launch_tc_stage(m->N, true, a, d->num_sms, s)
-                      : dgdev::launch_stage(m->N, true, a, d->num_sms, s);
+                      : dgdev::launch_stage(m->N, true, a, d->num_sms, s, m->stage_shape);
           }), "stage kernel launch");
   m->last_launches = 1;
   return DG_OK;

@@ -28,10 +28,15 @@ constexpr unsigned kAbsorbingCode = 0xFFu;
 constexpr int kMatVecs = 5;
 
 // Stage-kernel tiling per order N: tile of E tetrahedra, G row groups (threads
-// = E * G).  Chosen so a thread holds at most 7 rows and the shared tiles of
-// one CTA stay near 100 KB.
-__host__ __device__ constexpr int stage_tile_elems(int N) {
-  return N <= 5 ? 32 : N == 6 ? 12 : N == 7 ? 16 : 8;     // N = 6: room for its operators
+// = E * G).  Shape 0 (the default) chosen so a thread holds at most 7 rows and
+// the shared tiles of one CTA stay near 100 KB; shape 1 halves the elements
+// per tile (twice the CTAs of a small mesh, half the shared tiles) with the
+// same rows per thread.  The autotuner of the serving loop picks per order
+// and size (dg_set_stage_shape).
+constexpr int kStageShapes = 2;
+__host__ __device__ constexpr int stage_tile_elems(int N, int shape = 0) {
+  return shape == 0 ? (N <= 5 ? 32 : N == 6 ? 12 : N == 7 ? 16 : 8)   // N = 6: room for its operators
+                    : (N <= 5 ? 16 : N == 6 ? 6 : N == 7 ? 8 : 4);
 }
 __host__ __device__ constexpr int stage_row_groups(int N) {
   // 3 (N = 5..7) or 4 (N = 8, 9) matrix rows per thread: measured fastest on GB300
@@ -111,7 +116,8 @@ cudaError_t launch_tt_mixed(const MixedArgs& m, int grid, cudaStream_t s);
 
 // Launches one RK stage (rk = true: res <- a res + dt rhs, u_out <- u_in + b res)
 // or one bare right-hand-side evaluation (rk = false: rhs <- rhs(u_in)).
-cudaError_t launch_stage(int N, bool rk, const StageArgs& a, int num_sms, cudaStream_t s);
+cudaError_t launch_stage(int N, bool rk, const StageArgs& a, int num_sms, cudaStream_t s,
+                         int shape = 0);
 cudaError_t launch_tc_stage(int N, bool rk, const StageArgs& a, int num_sms, cudaStream_t s);
 
 struct EnergyArgs {

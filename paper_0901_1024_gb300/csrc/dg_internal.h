@@ -69,6 +69,7 @@ struct dg_mesh {
   int64_t last_launches = 0;
   bool trace = false;
   int stage_impl = DG_STAGE_AUTO;
+  int stage_shape = 0;            // FP32 stage tile shape (dg_set_stage_shape)
   double energy_check = -1.0;     // dg_step_host energy-growth limit (< 0: off)
 };
 

@@ -35,11 +35,11 @@
 
 namespace dgdev {
 
-template <int N> struct StageDims {
+template <int N, int S = 0> struct StageDims {
   static constexpr int Np = (N + 1) * (N + 2) * (N + 3) / 6;
   static constexpr int Nfp = (N + 1) * (N + 2) / 2;
   static constexpr int NF = 4 * Nfp;
-  static constexpr int E = stage_tile_elems(N), G = stage_row_groups(N);
+  static constexpr int E = stage_tile_elems(N, S), G = stage_row_groups(N);
   static constexpr int T = E * G;
   static constexpr int R = (Np + G - 1) / G;
   static constexpr int US = Np | 1;                          // odd element stride
@@ -72,9 +72,9 @@ template <int N> struct StageDims {
 
 // EXT: meshes with materials (A.mat) or absorbing faces; the vacuum
 // instantiation compiles without any of that code.
-template <int N, bool RK, bool EXT>
-__global__ void __launch_bounds__(StageDims<N>::T) stage_kernel(const StageArgs A) {
-  using D = StageDims<N>;
+template <int N, bool RK, bool EXT, int S>
+__global__ void __launch_bounds__(StageDims<N, S>::T) stage_kernel(const StageArgs A) {
+  using D = StageDims<N, S>;
   constexpr int E = D::E, G = D::G, Np = D::Np, Nfp = D::Nfp, NF = D::NF, R = D::R;
   constexpr int US = D::US, FS = D::FS;
   extern __shared__ float4 smem4[];
@@ -386,17 +386,17 @@ __global__ void __launch_bounds__(StageDims<N>::T) stage_kernel(const StageArgs 
   }
 }
 
-template <int N>
-cudaError_t launch_stage_n(bool rk, const StageArgs& a, int num_sms, cudaStream_t s) {
-  using D = StageDims<N>;
+template <int N, int S>
+cudaError_t launch_stage_shape(bool rk, const StageArgs& a, int num_sms, cudaStream_t s) {
+  using D = StageDims<N, S>;
   static int occ[2][2][16] = {};        // [rk][ext][device]: CTAs per SM
   int dev = 0;
   cudaError_t err = cudaGetDevice(&dev);
   if (err != cudaSuccess) return err;
   dev &= 15;
   const bool ext = a.mat || a.absorbing;
-  auto kern = rk ? (ext ? stage_kernel<N, true, true> : stage_kernel<N, true, false>)
-                 : (ext ? stage_kernel<N, false, true> : stage_kernel<N, false, false>);
+  auto kern = rk ? (ext ? stage_kernel<N, true, true, S> : stage_kernel<N, true, false, S>)
+                 : (ext ? stage_kernel<N, false, true, S> : stage_kernel<N, false, false, S>);
   int& o = occ[rk ? 1 : 0][ext ? 1 : 0][dev];
   if (o == 0) {
     err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -411,9 +411,15 @@ cudaError_t launch_stage_n(bool rk, const StageArgs& a, int num_sms, cudaStream_
   return launch_pdl(kern, grid, D::T, int(D::smem_bytes), s, a);
 }
 
+template <int N>
+cudaError_t launch_stage_n(bool rk, const StageArgs& a, int num_sms, cudaStream_t s, int shape) {
+  return shape == 1 ? launch_stage_shape<N, 1>(rk, a, num_sms, s)
+                    : launch_stage_shape<N, 0>(rk, a, num_sms, s);
+}
+
 }  // namespace dgdev
 
 #define DG_INSTANTIATE_STAGE(NN)                                                          \
   namespace dgdev {                                                                        \
-  template cudaError_t launch_stage_n<NN>(bool, const StageArgs&, int, cudaStream_t);      \
+  template cudaError_t launch_stage_n<NN>(bool, const StageArgs&, int, cudaStream_t, int); \
   }

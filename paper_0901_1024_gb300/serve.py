@@ -93,7 +93,7 @@ class _Live:
 class _Pack:
     """The live solves of one order, packed; fields in state = (u, res, work)."""
 
-    def __init__(self, torch, N, solves, old, padding, impl, graphs, stream):
+    def __init__(self, torch, N, solves, old, padding, impl, graphs, stream, shape=0):
         self.N, self.solves = N, list(solves)
         self.alive = len(self.solves)
         self.built_at = 0
@@ -105,7 +105,8 @@ class _Pack:
             npad += 1
         self.mesh = Mesh.pack(meshes + [padding] * npad)
         self.mesh.set_stage_impl(impl)
-        self.impl = impl
+        self.mesh.set_stage_shape(shape)
+        self.impl, self.shape = impl, shape
         self.K, self.Np = self.mesh.K, Np
         dev = "cuda"
         shape = (6, self.K, Np)
@@ -233,7 +234,7 @@ class Server:
         # retiring (energy, copy-out); and how many packs were built
         self.stats = {}
 
-    _tuned = {}                        # (device, N, decade of K) -> stage implementation
+    _tuned = {}                        # (device, N, decade of K) -> (stage implementation, tile shape)
     _cost = {}                         # (device, N, decade of K) -> ms per tile on one SM
 
     # ---- stage implementation per (N, K) ---------------------------------
@@ -248,12 +249,12 @@ class Server:
         return (self.torch.cuda.current_device(), N,
                 min(3, int(math.log10(max(K, 1))) - 2))     # <1e3, <1e4, <1e5, more
 
-    def _time_impl(self, N, solves, impl):
-        """Milliseconds of 3 steps of a scratch pack of `solves` on `impl`; the
-        pack is released before returning."""
+    def _time_impl(self, N, solves, impl, shape=0):
+        """Milliseconds of 3 steps of a scratch pack of `solves` on `impl` with
+        tile shape `shape`; the pack is released before returning."""
         torch = self.torch
         self._charge(sum(s.bytes for s in solves))
-        p = _Pack(torch, N, solves, None, self._pad_mesh(N), impl, False, self.stream)
+        p = _Pack(torch, N, solves, None, self._pad_mesh(N), impl, False, self.stream, shape)
         for _ in range(2):                       # warm-up
             p.step()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -273,14 +274,18 @@ class Server:
         return ms
 
     def _choose_impl(self, N, solves):
+        """(stage implementation, FP32 tile shape) of a pack: without autotuning
+        the server's `impl` and the default shape; with it, the fastest of the
+        tensor-core stage (orders <= 6) and the FP32 stage in each tile shape,
+        timed on a scratch pack once per (device, order, decade of K)."""
         if not self.autotune:
-            return self.impl
-        if N > 6:
-            return Mesh.STAGE_FP32
+            return self.impl, 0
         key = self._tune_key(N, solves)
         if key not in self._tuned:
-            times = {impl: self._time_impl(N, solves, impl)
-                     for impl in (Mesh.STAGE_TC, Mesh.STAGE_FP32)}
+            cands = [(Mesh.STAGE_FP32, 0), (Mesh.STAGE_FP32, 1)]
+            if N <= 6:
+                cands.insert(0, (Mesh.STAGE_TC, 0))
+            times = {c: self._time_impl(N, solves, *c) for c in cands}
             self._tuned[key] = min(times, key=times.get)
         return self._tuned[key]
 
@@ -308,8 +313,9 @@ class Server:
 
     def _new_pack(self, N, members, carry, impl):
         self._charge(sum(s.bytes for s in members))
+        impl, shape = impl
         p = _Pack(self.torch, N, members, carry, self._pad_mesh(N), impl,
-                  self.graphs and not self.mixed, self.stream)
+                  self.graphs and not self.mixed, self.stream, shape)
         if self.mixed:
             p.set_parity(self._gparity)
             p.cost = self._cost.get(self._tune_key(N, members))

@@ -7,7 +7,8 @@ the one-RHS tests; these tests run the stage instantiations themselves, each
 for 100 LSERK4 steps on a 48-tetrahedron cavity (Section 6's time stepper),
 element by element against `oracle.lserk4_run` at relative L2 <= 1e-4:
 
-  * impl: FP32 CUDA cores (all orders) and tensor cores (every order that has a
+  * impl: FP32 CUDA cores (all orders; tile shape 0, and shape 1 -- half the
+    tetrahedra per tile -- in vacuum) and tensor cores (every order that has a
     tensor-core stage);
   * kind: vacuum, or per-element eps, mu with a random mix of perfect-conductor
     and characteristic absorbing boundary faces (the EXT instantiation).
@@ -26,6 +27,7 @@ pytestmark = pytest.mark.gpu
 
 STEP_TOL = 1e-4
 FP32, TC = 1, 2
+FP32_S1 = 11                                   # FP32 stage in tile shape 1 (test-local code)
 KIND_FP32_STAGE, KIND_TC_STAGE = 0, 4          # dg_trace_read kinds of a fused RK stage
 TC_ORDERS = range(1, 7)
 
@@ -50,6 +52,8 @@ def _cases():
     for kind in ("vacuum", "ext"):
         for N in range(1, 10):
             out.append(pytest.param(FP32, N, kind, id=f"fp32-N{N}-{kind}"))
+            if kind == "vacuum":
+                out.append(pytest.param(FP32_S1, N, kind, id=f"fp32shape1-N{N}-{kind}"))
         for N in TC_ORDERS:
             out.append(pytest.param(TC, N, kind, id=f"tc-N{N}-{kind}"))
     return out
@@ -62,6 +66,8 @@ def _materials(K, seed):
 
 
 def _run(torch, mesh, u0, dt, nsteps, impl):
+    mesh.set_stage_shape(1 if impl == FP32_S1 else 0)
+    impl = FP32 if impl == FP32_S1 else impl
     mesh.set_stage_impl(impl)
     u = torch.from_numpy(u0).cuda()
     res = torch.zeros_like(u)
@@ -70,6 +76,7 @@ def _run(torch, mesh, u0, dt, nsteps, impl):
     torch.cuda.synchronize()
     _, kinds = mesh.trace_read()
     mesh.set_stage_impl(0)
+    mesh.set_stage_shape(0)
     mesh.trace_enable(0)
     return u.cpu().numpy(), res.cpu().numpy(), set(int(k) for k in kinds)
 
