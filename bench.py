@@ -622,6 +622,7 @@ def run_serve(args):
                                          if shared else None),
             "speedup_vs_same_kernels": ours["solves_per_s"] / base["solves_per_s"],
             "speedup_vs_plain": ours["solves_per_s"] / plain["solves_per_s"],
+            "autotuner_choices": Server.tuned_choices(),
             "max_rel_l2_vs_same_kernels": worst(served, same),
             "max_rel_l2_vs_plain_fp32": worst(served, plain_res)}
     print(json.dumps(line), flush=True)
@@ -646,8 +647,9 @@ def run_sweep(args):
         mesh = dg.Mesh(verts, tets, N)
         x = mesh.nodes()
         u0 = gaussian_pulse(x[0], x[1], x[2], 0.2, pulse_center(1)).astype(np.float32)
-        for impl in ([0, 1] if 2 <= N <= 6 else [0]):
+        for impl, shape in ([(0, 0), (1, 0), (1, 1)] if 2 <= N <= 6 else [(0, 0), (1, 1)]):
             mesh.set_stage_impl(impl)
+            mesh.set_stage_shape(shape)
             u = torch.from_numpy(u0).cuda()
             res = torch.zeros_like(u)
             mesh.step(u, res, mesh.dt_cfl, 3)
@@ -666,7 +668,8 @@ def run_sweep(args):
             gbs = stage_bytes_per_elem(Np) * K / stage / 1e9
             tf = flops_per_elem_stage(N, Np, Nfp) * K / stage / 1e12
             rows.append({"N": N, "n": n, "K": K, "Np": Np, "dofs": 6 * K * Np,
-                         "kernel": "tensor cores (FP16x3)" if 4 in kinds else "FP32 CUDA cores",
+                         "kernel": ("tensor cores (FP16x3)" if 4 in kinds
+                                    else f"FP32 CUDA cores, tile shape {shape}"),
                          "stage_us": stage * 1e6, "dof_updates_per_s": 6 * K * Np / stage,
                          "hbm_gbs": gbs, "hbm_frac": gbs / peaks["hbm_gbs"],
                          "tflops": tf, "fp32_frac": tf / fp32_peak})

@@ -29,14 +29,15 @@ constexpr int kMatVecs = 5;
 
 // Stage-kernel tiling per order N: tile of E tetrahedra, G row groups (threads
 // = E * G).  Shape 0 (the default) chosen so a thread holds at most 7 rows and
-// the shared tiles of one CTA stay near 100 KB; shape 1 halves the elements
-// per tile (twice the CTAs of a small mesh, half the shared tiles) with the
+// the shared tiles of one CTA stay near 100 KB (sizes measured fastest on the
+// order sweep's meshes of ~1.7e7 DOFs); shape 1 halves the elements per tile (twice the CTAs of a small mesh, half the shared tiles) with the
 // same rows per thread.  The autotuner of the serving loop picks per order
 // and size (dg_set_stage_shape).
 constexpr int kStageShapes = 2;
 __host__ __device__ constexpr int stage_tile_elems(int N, int shape = 0) {
-  return shape == 0 ? (N <= 5 ? 32 : N == 6 ? 12 : N == 7 ? 16 : 8)   // N = 6: room for its operators
-                    : (N <= 5 ? 16 : N == 6 ? 6 : N == 7 ? 8 : 4);
+  // N = 1: 16 per tile by default (measured 16 % faster than 32 on 705 894 tets)
+  return shape == 0 ? (N == 1 ? 16 : N <= 5 ? 32 : N == 6 ? 12 : N == 7 ? 16 : 8)  // N = 6: room for its operators
+                    : (N == 1 ? 8 : N <= 5 ? 16 : N == 6 ? 6 : N == 7 ? 8 : 4);
 }
 __host__ __device__ constexpr int stage_row_groups(int N) {
   // 3 (N = 5..7) or 4 (N = 8, 9) matrix rows per thread: measured fastest on GB300

@@ -289,6 +289,13 @@ class Server:
             self._tuned[key] = min(times, key=times.get)
         return self._tuned[key]
 
+    @classmethod
+    def tuned_choices(cls):
+        """The autotuner's picks so far: "device/N/decade" -> "tc" or "fp32/shape"."""
+        names = {Mesh.STAGE_TC: "tc", Mesh.STAGE_FP32: "fp32", Mesh.STAGE_AUTO: "auto"}
+        return {f"{d}/{N}/{k}": (names[i] if i == Mesh.STAGE_TC else f"{names[i]}/{sh}")
+                for (d, N, k), (i, sh) in sorted(cls._tuned.items())}
+
     # ---- device-memory accounting (a model of what the loop allocates) ------
     def _charge(self, nbytes):
         m = self.stats
