@@ -86,6 +86,25 @@ def test_rhs_parity_materials(env, N, impl, what):
     assert rel(got, want) < RHS_TOL
 
 
+@pytest.mark.parametrize("N", [1, 4, 7])
+def test_rhs_parity_materials_fp32_tile_shape_1(env, N):
+    """The FP32 stage in tile shape 1 (half the tetrahedra per tile) with random
+    eps, mu and absorbing faces: K = 162, ragged last tiles."""
+    torch, dg = env
+    verts, tets = kuhn_box_mesh(3, 0.15, 80 + N)
+    mesh, om, eps, mu, bc = _setup(dg, verts, tets, N, 90 + N)
+    u32 = random_fields(om.K, om.Np, 95 + N).astype(np.float32)
+    mesh.set_stage_impl(FP32)
+    mesh.set_stage_shape(1)
+    u = torch.from_numpy(u32).cuda()
+    out = torch.full_like(u, float("nan"))
+    mesh.rhs(u, out)
+    torch.cuda.synchronize()
+    mesh.set_stage_shape(0)
+    want = oracle.rhs(om, u32.astype(np.float64), 1.0, eps, mu, bc)
+    assert rel(out.cpu().numpy(), want) < RHS_TOL
+
+
 @pytest.mark.parametrize("alpha", [1.0, 0.0])
 @pytest.mark.parametrize("impl,N", [(FP32, 3), (TC, 3), (TC, 6)])
 def test_step_parity_materials(env, alpha, impl, N):
