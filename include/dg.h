@@ -238,6 +238,31 @@ int dg_rk_stage(dg_mesh* mesh, const float* u_in, float* u_out, float* res, int 
                 double dt, void* stream);
 
 /*
+ * dg_rk_stage for the elements [k0, k1) only; the others' u_out and res are
+ * not touched.  With the elements of a subdomain numbered interior first (no
+ * face to a ghost element), a stage can run on the interior while the ghosts'
+ * face values are exchanged, then on the rest (the one-mesh decomposition of
+ * Section 6's multi-GPU outlook; paper_0901_1024_gb300/domain.py): every
+ * element's result is bit for bit that of dg_rk_stage, provided the elements
+ * of the first call read no value written between the two calls.
+ *   k0, k1 : multiples of the stage kernel's tile (dg_stage_tile), or k1 = K.
+ * Asynchronous on `stream`.  Errors: as dg_rk_stage; DG_ERR_ARG for a range
+ * outside 0 <= k0 < k1 <= K or not on tile boundaries.
+ */
+int dg_rk_stage_range(dg_mesh* mesh, const float* u_in, float* u_out, float* res, int stage,
+                      double dt, int64_t k0, int64_t k1, void* stream);
+
+/*
+ * Tetrahedra per tile of the stage kernel that runs on these buffers (the
+ * tensor-core kernels need 16-byte aligned buffers; NULL pointers count as
+ * aligned): the granularity of dg_rk_stage_range.  Uploads the mesh to the
+ * current device if needed.  Errors: DG_ERR_ARG (NULL tile), DG_ERR_STATE
+ * (no order), DG_ERR_CUDA.
+ */
+int dg_stage_tile(dg_mesh* mesh, const float* u_in, const float* u_out, const float* res,
+                  int* tile);
+
+/*
  * dg_rk_stage with a time step per element: element k's update uses
  * dt_elem[k] in place of dt.
  *   dt_elem : device, [K] FP32, read; positive.

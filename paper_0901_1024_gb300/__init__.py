@@ -199,6 +199,23 @@ class Mesh:
         check(self._lib.dg_rk_stage(self._h, _devptr(u_in), _devptr(u_out), _devptr(res),
                                     int(stage), float(dt), _stream_handle(stream)), "dg_rk_stage")
 
+    def rk_stage_range(self, u_in, u_out, res, stage: int, dt: float, k0: int, k1: int,
+                       stream=None):
+        """dg_rk_stage_range: one LSERK4 stage for the elements [k0, k1) only (tile
+        boundaries of `stage_tile`, or k1 = K)."""
+        check(self._lib.dg_rk_stage_range(self._h, _devptr(u_in), _devptr(u_out), _devptr(res),
+                                          int(stage), float(dt), int(k0), int(k1),
+                                          _stream_handle(stream)), "dg_rk_stage_range")
+
+    def stage_tile(self, u_in=None, u_out=None, res=None) -> int:
+        """dg_stage_tile: tetrahedra per tile of the stage kernel these buffers run
+        (None: aligned buffers)."""
+        t = C.c_int()
+        ptr = lambda x: None if x is None else _devptr(x)  # noqa: E731
+        check(self._lib.dg_stage_tile(self._h, ptr(u_in), ptr(u_out), ptr(res), C.byref(t)),
+              "dg_stage_tile")
+        return t.value
+
     def rk_stage_elem(self, u_in, u_out, res, stage: int, dt_elem, stream=None):
         """dg_rk_stage_elem: one LSERK4 stage with the per-element steps dt_elem
         (a device FP32 tensor of K entries)."""

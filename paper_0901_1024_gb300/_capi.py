@@ -38,6 +38,9 @@ SIGNATURES = {
     "dg_step": (C.c_int, [_vp, _vp, _vp, C.c_double, C.c_int, _vp]),
     "dg_rk_stage": (C.c_int, [_vp, _vp, _vp, _vp, C.c_int, C.c_double, _vp]),
     "dg_rk_stage_elem": (C.c_int, [_vp, _vp, _vp, _vp, C.c_int, _vp, _vp]),
+    "dg_rk_stage_range": (C.c_int, [_vp, _vp, _vp, _vp, C.c_int, C.c_double, C.c_int64, C.c_int64,
+                                    _vp]),
+    "dg_stage_tile": (C.c_int, [_vp, _vp, _vp, _vp, _intp]),
     "dg_rk_stage_multi": (C.c_int, [C.POINTER(_vp), C.c_int, C.POINTER(_vp), C.POINTER(_vp),
                                     C.POINTER(_vp), C.POINTER(_vp), C.c_int, C.c_double,
                                     C.POINTER(C.c_double), _vp]),

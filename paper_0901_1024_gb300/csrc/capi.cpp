@@ -375,6 +375,29 @@ int dg_rk_stage(dg_mesh* m, const float* u_in, float* u_out, float* res, int sta
   return DG_OK;
 }
 
+int dg_rk_stage_range(dg_mesh* m, const float* u_in, float* u_out, float* res, int stage,
+                      double dt, int64_t k0, int64_t k1, void* stream) {
+  if (int rc = check_mesh(m, true)) return rc;
+  if (!u_in || !u_out || !res) return fail(DG_ERR_ARG, "u_in, u_out or res is NULL");
+  if (u_in == u_out || res == u_in || res == u_out)
+    return fail(DG_ERR_ARG, "u_in, u_out and res must be three different buffers");
+  if (stage < 0 || stage > 4) return fail(DG_ERR_ARG, "stage must be 0..4");
+  if (!(dt > 0.0) || !std::isfinite(dt)) return fail(DG_ERR_ARG, "dt must be positive and finite");
+  if (k0 < 0 || k1 <= k0 || k1 > m->K) return fail(DG_ERR_ARG, "need 0 <= k0 < k1 <= K");
+  std::string err;
+  if (int rc = dg::device_stage(m, u_in, u_out, res, stage, dt, nullptr, stream, err, k0, k1))
+    return fail(rc, err);
+  return DG_OK;
+}
+
+int dg_stage_tile(dg_mesh* m, const float* u_in, const float* u_out, const float* res, int* tile) {
+  if (int rc = check_mesh(m, true)) return rc;
+  if (!tile) return fail(DG_ERR_ARG, "tile is NULL");
+  std::string err;
+  if (int rc = dg::device_stage_tile(m, u_in, u_out, res, tile, err)) return fail(rc, err);
+  return DG_OK;
+}
+
 int dg_rk_stage_elem(dg_mesh* m, const float* u_in, float* u_out, float* res, int stage,
                      const float* dt_elem, void* stream) {
   if (int rc = check_mesh(m, true)) return rc;

@@ -757,14 +757,33 @@ static int step_impl(dg_mesh* m, float* u, float* res, double dt, int nsteps, cu
   return DG_OK;
 }
 
+int device_stage_tile(dg_mesh* m, const float* u_in, const float* u_out, const float* res,
+                      int* tile, std::string& err) {
+  int rc = ensure_device(m, err);
+  if (rc) return rc;
+  *tile = use_tc(m, {u_in, u_out, res}) ? dgdev::tc_tile_elems(m->N)
+                                        : dgdev::stage_tile_elems(m->N, m->stage_shape);
+  return DG_OK;
+}
+
 int device_stage(dg_mesh* m, const float* u_in, float* u_out, float* res, int stage, double dt,
-                 const float* dt_elem, void* stream, std::string& err) {
+                 const float* dt_elem, void* stream, std::string& err, int64_t k0, int64_t k1) {
   int rc = ensure_device(m, err);
   if (rc) return rc;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   DeviceState* d = m->dev;
   const bool tc = use_tc(m, {u_in, u_out, res});
   dgdev::StageArgs a = stage_args(m, tc);
+  if (k1 >= 0) {                        // elements [k0, k1): whole tiles of the kernel that runs
+    const int E = tc ? dgdev::tc_tile_elems(m->N) : dgdev::stage_tile_elems(m->N, m->stage_shape);
+    if (k0 < 0 || k1 <= k0 || k1 > m->K || k0 % E != 0 || (k1 % E != 0 && k1 != m->K)) {
+      err = "the element range must be [k0, k1) with k0 and k1 multiples of the stage's tile of " +
+            std::to_string(E) + " tetrahedra (or k1 = K), 0 <= k0 < k1 <= K";
+      return DG_ERR_ARG;
+    }
+    a.tile0 = static_cast<int>(k0 / E);
+    a.num_tiles = static_cast<int>((k1 + E - 1) / E - k0 / E);
+  }
   a.u_in = u_in;
   a.u_out = u_out;
   a.res = res;

@@ -55,7 +55,8 @@ struct StageArgs {
   const unsigned char* fmask;  // [4][Nfp]
   const unsigned char* perm;   // [4][24][Nfp]
   int K;
-  int num_tiles;
+  int num_tiles;           // tiles of this launch: tile0, tile0 + 1, ..., tile0 + num_tiles - 1
+  int tile0;               // first tile (0: the whole mesh; dg_rk_stage_range: a sub-range)
   float a, b, dt, alpha;
   const float* dt_elem;    // RK mode: per-element time step [K], or null for dt
   const float4* mat;       // [K][kMatVecs] material record, or null (vacuum)

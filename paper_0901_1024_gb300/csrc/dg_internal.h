@@ -88,8 +88,13 @@ void greedy_partition_order(const std::vector<int32_t>& nbr, int64_t K, int64_t 
                             int64_t* perm);
 // device.cu (stream = cudaStream_t)
 int device_rhs(dg_mesh* m, const float* u, float* rhs, void* stream, std::string& err);
+// k1 >= 0: only the elements [k0, k1), whole tiles of the stage kernel that runs
 int device_stage(dg_mesh* m, const float* u_in, float* u_out, float* res, int stage, double dt,
-                 const float* dt_elem, void* stream, std::string& err);
+                 const float* dt_elem, void* stream, std::string& err, int64_t k0 = 0,
+                 int64_t k1 = -1);
+// tetrahedra per tile of the stage kernel these buffers would run
+int device_stage_tile(dg_mesh* m, const float* u_in, const float* u_out, const float* res,
+                      int* tile, std::string& err);
 int device_step(dg_mesh* m, float* u, float* res, double dt, int nsteps, void* stream,
                 std::string& err);
 int device_stage_multi(dg_mesh* const* ms, int n, const float* const* u_in, float* const* u_out,

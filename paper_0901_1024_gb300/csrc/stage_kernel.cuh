@@ -120,7 +120,8 @@ __global__ void __launch_bounds__(StageDims<N, S>::T) stage_kernel(const StageAr
   };
   pdl_wait();        // the previous kernel's fields are complete (operators are constant)
 
-  for (int tile = blockIdx.x; tile < A.num_tiles; tile += gridDim.x) {
+  for (int tt = blockIdx.x; tt < A.num_tiles; tt += gridDim.x) {
+    const int tile = A.tile0 + tt;
     const int k0 = tile * E;
     const int Ev = min(E, K - k0);
     // the first operator chunk flies while the tile is staged and its fluxes formed

@@ -480,7 +480,7 @@ __device__ __forceinline__ void tc_flux_items(const uint32_t (&item)[NI], const 
 // EXT: meshes with materials (A.mat) or absorbing faces; the vacuum instantiation
 // has none of that arithmetic.
 // The stage as run by one CTA: `cta` of `ncta` CTAs that share the tiles of A
-// (tile cta, cta + ncta, ...).  The kernels below run it as CTA cta of
+// (tile tile0 + cta, tile0 + cta + ncta, ...).  The kernels below run it as CTA cta of
 // the grid; the mixed-order kernel runs it for the group its CTA belongs to.
 template <int N, bool RK, bool EXT>
 __device__ __forceinline__ void tc_stage_body(const StageArgs& A, const int cta, const int ncta) {
@@ -496,6 +496,7 @@ __device__ __forceinline__ void tc_stage_body(const StageArgs& A, const int cta,
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int K = A.K;
   const int ntiles = (A.num_tiles - cta + ncta - 1) / ncta;
+  const int base = A.tile0 + cta;                  // this CTA's first tile of the mesh
   if (ntiles <= 0) return;
 
   float* sU = reinterpret_cast<float*>(smem + D::OFF_U);
@@ -537,9 +538,9 @@ __device__ __forceinline__ void tc_stage_body(const StageArgs& A, const int cta,
     const uint32_t lane_off = uint32_t(warp * 32) << 16;
     if (warp == 0 && tc::elect_one()) {   // first loads: fields of tiles 0..NSU-2, res of tile 0
       for (int t = 0; t < D::NSU - 1 && t < ntiles; ++t)
-        tc_load_u<N>(A, cta + t * ncta, sU + t * D::U_FLOATS, sG + t * D::G_FLOATS,
+        tc_load_u<N>(A, base + t * ncta, sU + t * D::U_FLOATS, sG + t * D::G_FLOATS,
                      &s_u_full[t]);
-      if (RK) tc_load_res<N>(A, cta, sR, &s_r_full[0]);
+      if (RK) tc_load_res<N>(A, base, sR, &s_r_full[0]);
     }
     __syncwarp();
     // Flux items of elements E0 .. E-1 (warps 1..3), computed one tile ahead
@@ -554,7 +555,7 @@ __device__ __forceinline__ void tc_stage_body(const StageArgs& A, const int cta,
     auto epilogue_fluxes = [&](int t) {
       if (warp != 0) {
         const int slot = t % D::NSU;
-        const int k0t = (cta + t * ncta) * E, Evt = min(E, K - k0t);
+        const int k0t = (base + t * ncta) * E, Evt = min(E, K - k0t);
         wait_or_flag(&s_u_full[slot], (t / D::NSU) & 1, A.status);
         tc_flux_items<N, EXT, D::EITEMS>(eitem, A, k0t, Evt, sU + slot * D::U_FLOATS,
                                          sG + slot * D::G_FLOATS, sF2 + (t & 1) * D::F2_FLOATS,
@@ -595,7 +596,7 @@ __device__ __forceinline__ void tc_stage_body(const StageArgs& A, const int cta,
       }
       if (j >= 1) {                                  // epilogue of tile t = j - 1
         const int t = j - 1, buf = t & 1;
-        const int tile = cta + t * ncta;
+        const int tile = base + t * ncta;
         const int k0 = tile * E, Ev = min(E, K - k0);
         float* su = sU + (t % D::NSU) * D::U_FLOATS;
         float* sr = sR + (t % D::NSR) * D::U_FLOATS;
@@ -710,7 +711,7 @@ __device__ __forceinline__ void tc_stage_body(const StageArgs& A, const int cta,
 #pragma unroll
     for (int q = 0; q < D::ITEMS; ++q) item[q] = tc_item<N>(pt + q * D::PRODUCERS, D::E0, sFmask);
     for (int t = 0; t < ntiles; ++t) {
-      const int tile = cta + t * ncta;
+      const int tile = base + t * ncta;
       const int k0 = tile * E, Ev = min(E, K - k0);
       const int slot = t % D::NSU, buf = t & 1;
       const float* su = sU + slot * D::U_FLOATS;

@@ -134,7 +134,7 @@ __device__ __forceinline__ void lds8(const float* p, float* v) {
 // EXT: meshes with materials (A.mat) or absorbing faces; the vacuum instantiation
 // has none of that arithmetic.
 // The stage as run by one CTA: `cta` of `ncta` CTAs that share the tiles of A
-// (tile cta, cta + ncta, ...).  The kernels below run it as CTA cta of
+// (tile tile0 + cta, tile0 + cta + ncta, ...).  The kernels below run it as CTA cta of
 // the grid; the mixed-order kernel runs it for the group its CTA belongs to.
 template <int N, bool RK, bool EXT>
 __device__ __forceinline__ void tt_stage_body(const StageArgs& A, const int cta, const int ncta) {
@@ -149,6 +149,7 @@ __device__ __forceinline__ void tt_stage_body(const StageArgs& A, const int cta,
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int K = A.K;
   const int ntiles = (A.num_tiles - cta + ncta - 1) / ncta;
+  const int base = A.tile0 + cta;                  // this CTA's first tile of the mesh
   if (ntiles <= 0) return;
 
   unsigned char* sXhi = smem + D::OFF_X;
@@ -234,16 +235,16 @@ __device__ __forceinline__ void tt_stage_body(const StageArgs& A, const int cta,
     const uint32_t lane_off = uint32_t(warp * 32) << 16;
     if (warp == 3 && tc::elect_one()) {   // first loads: fields of tiles 0..NSU-2, res of tile 0
       for (int t = 0; t < D::NSU - 1 && t < ntiles; ++t)
-        tt_load_u<N>(A, cta + t * ncta, sU + t * D::U_FLOATS, sG + t * D::G_FLOATS,
+        tt_load_u<N>(A, base + t * ncta, sU + t * D::U_FLOATS, sG + t * D::G_FLOATS,
                      &s_u_full[t]);
-      if (RK) tt_load_res<N>(A, cta, sR, &s_r_full[0]);
+      if (RK) tt_load_res<N>(A, base, sR, &s_r_full[0]);
     }
     __syncwarp();
     constexpr uint32_t IDESC = tc::idesc_f16(128, D::NN);
     constexpr uint32_t LBO = (D::NN / 8) * 128;
     for (int j = 0; j <= ntiles; ++j) {
       const int t = j - 1, buf = t & 1;               // tile whose update runs in iteration j
-      const int tile = cta + t * ncta;
+      const int tile = base + t * ncta;
       const int k0 = tile * E, Ev = min(E, K - k0);
       if (warp == 3) {
         if (j < ntiles) {                              // MMAs of tile j into accumulator j & 1
@@ -379,7 +380,7 @@ __device__ __forceinline__ void tt_stage_body(const StageArgs& A, const int cta,
     }
     float* F = sF;
     for (int t = 0; t < ntiles; ++t) {
-      const int tile = cta + t * ncta;
+      const int tile = base + t * ncta;
       const int k0 = tile * E, Ev = min(E, K - k0);
       const int slot = t % D::NSU;
       const float* su = sU + slot * D::U_FLOATS;

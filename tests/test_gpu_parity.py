@@ -569,6 +569,81 @@ def test_subdomains_in_lockstep_match_the_single_mesh(env, impl):
         assert np.array_equal(u.cpu().numpy()[:, :p.n_owned], full[:, p.owned])
 
 
+@pytest.mark.parametrize("impl,N", [(FP32, 4), (TC, 4), (TC, 6), (FP32, 7)])
+def test_overlapped_subdomains_match_the_single_mesh(env, impl, N):
+    """The overlapped stage of a subdomain: plans ordered interior first
+    (build_plans with the stage kernel's tile), each stage run as
+    dg_rk_stage_range over the interior tiles while the ghosts still hold NaN
+    (so an interior element that read a ghost would poison its result), then the
+    trace copy, then the range over the remaining owned and ghost elements.
+    Every owned element is bit-identical to the single-mesh run."""
+    torch, dg = env
+    from paper_0901_1024_gb300.domain import build_plans
+    verts, tets = kuhn_box_mesh(6 if N < 7 else 4, 0.15, 4)
+    glob = dg.Mesh(verts, tets, N)
+    glob.set_stage_impl(impl)
+    tile = glob.stage_tile()
+    plans = build_plans(glob, tets, 3, tile=tile)
+    u0 = random_fields(glob.K, glob.Np, 22).astype(np.float32)
+    dt = glob.dt_cfl
+    ug, rg = torch.from_numpy(u0).cuda(), torch.zeros(u0.shape, device="cuda")
+    glob.step(ug, rg, dt, 2)
+    meshes, us, works, ress = [], [], [], []
+    for p in plans:
+        assert 0 < p.n_interior < p.n_owned and p.n_interior % tile == 0
+        m = dg.Mesh(verts, p.tets, N)
+        m.set_stage_impl(impl)
+        meshes.append(m)
+        us.append(torch.from_numpy(np.ascontiguousarray(u0[:, np.concatenate([p.owned, p.ghosts])])).cuda())
+        works.append(torch.empty_like(us[-1]))
+        ress.append(torch.zeros_like(us[-1]))
+        assert m.stage_tile(us[-1], works[-1], ress[-1]) == tile
+    idx = [{q: torch.as_tensor(v, device="cuda") for q, v in p.send.items()} for p in plans]
+    ridx = [{q: torch.as_tensor(v, device="cuda") for q, v in p.recv.items()} for p in plans]
+    src, dst = us, works
+    for _ in range(2):
+        for i in range(5):
+            for r, p in enumerate(plans):
+                src[r][:, p.n_owned:, :] = float("nan")
+                meshes[r].trace_enable(2)
+                meshes[r].rk_stage_range(src[r], dst[r], ress[r], i, dt, 0, p.n_interior)
+            for p, u in zip(plans, src):
+                u[:, p.n_owned:, :] = 0
+            for r, p in enumerate(plans):
+                for q, ix in idx[r].items():
+                    src[q].view(6, -1).index_copy_(1, ridx[q][r], src[r].view(6, -1).index_select(1, ix))
+            for r, p in enumerate(plans):
+                ress[r][:, p.n_owned:, :] = 0
+                meshes[r].rk_stage_range(src[r], dst[r], ress[r], i, dt, p.n_interior, p.n_local)
+                assert _stage_kinds(meshes[r]) == ({4} if impl == TC else {0})
+            src, dst = dst, src
+    torch.cuda.synchronize()
+    glob.set_stage_impl(0)
+    full = ug.cpu().numpy()
+    for p, u in zip(plans, src):
+        assert np.array_equal(u.cpu().numpy()[:, :p.n_owned], full[:, p.owned])
+
+
+def test_range_stage_argument_errors(env):
+    torch, dg = env
+    mesh = dg.Mesh(*kuhn_box_mesh(4, 0.1, 3), 4)
+    u = torch.zeros((6, mesh.K, mesh.Np), device="cuda")
+    out, res = torch.empty_like(u), torch.zeros_like(u)
+    E = mesh.stage_tile(u, out, res)
+    assert E == 20                                            # the tensor-core tile at N = 4
+    mesh.rk_stage_range(u, out, res, 0, 0.01, 0, mesh.K)     # the whole mesh
+    mesh.rk_stage_range(u, out, res, 0, 0.01, E, 3 * E)
+    for k0, k1 in ((-E, E), (E, E), (3, E), (0, 7), (0, mesh.K + 1), (2 * E, E)):
+        with pytest.raises(dg.DGError):
+            mesh.rk_stage_range(u, out, res, 0, 0.01, k0, k1)
+    mesh.set_stage_impl(FP32)
+    assert mesh.stage_tile() == 32                             # FP32 tile shape 0 at N = 4
+    mesh.set_stage_shape(1)
+    assert mesh.stage_tile() == 16
+    mesh.set_stage_shape(0)
+    mesh.set_stage_impl(0)
+
+
 @pytest.mark.parametrize("N", [2, 4, 7])
 def test_packed_mesh_stages_and_range_energies(env, N):
     """dg_mesh_pack of two meshes: a packed stage with per-element steps
