@@ -107,7 +107,7 @@ def load_peaks():
 KERNEL_SOURCES = {
     "tc": ("tc_stage.cuh", "tcgen05.cuh", "launch.cuh", "device.h"),      # tensor cores, N <= 4
     "tt": ("tc_stage_t.cuh", "tc_stage.cuh", "tcgen05.cuh", "launch.cuh",
-           "device.h"),                                                   # tensor cores, N = 5, 6
+           "device.h"),                                                   # tensor cores, N = 5..7
     "fp32": ("stage_kernel.cuh", "tcgen05.cuh", "launch.cuh", "device.h"),  # CUDA cores
 }
 
@@ -647,7 +647,7 @@ def run_sweep(args):
         mesh = dg.Mesh(verts, tets, N)
         x = mesh.nodes()
         u0 = gaussian_pulse(x[0], x[1], x[2], 0.2, pulse_center(1)).astype(np.float32)
-        for impl, shape in ([(0, 0), (1, 0), (1, 1)] if 2 <= N <= 6 else [(0, 0), (1, 1)]):
+        for impl, shape in ([(0, 0), (1, 0), (1, 1)] if 2 <= N <= 7 else [(0, 0), (1, 1)]):
             mesh.set_stage_impl(impl)
             mesh.set_stage_shape(shape)
             u = torch.from_numpy(u0).cuda()

@@ -36,6 +36,7 @@ cudaError_t launch_tc_stage(int N, bool rk, const StageArgs& a, int num_sms, cud
     case 4: return launch_tc_stage_n<4>(rk, a, num_sms, s);
     case 5: return launch_tt_stage_n<5>(rk, a, num_sms, s);
     case 6: return launch_tt_stage_n<6>(rk, a, num_sms, s);
+    case 7: return launch_tt_stage_n<7>(rk, a, num_sms, s);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -469,7 +470,7 @@ static int order_ops(const dg_mesh* m, int dev, OrderOps& out, std::string& err)
   std::vector<unsigned char> pm(m->ops.perm.begin(), m->ops.perm.end());
   if ((rc = upload(&o.perm, pm, err))) return rc;
   if (m->N > 4 && m->N <= dgdev::kTcMaxOrder) {
-    // Orders 5, 6: Op = [Dr Ds Dt LIFT] (Np x KT, each derivative block padded
+    // Orders 5..7: Op = [Dr Ds Dt LIFT] (Np x KT, each derivative block padded
     // to KB columns, zero padded), scaled by 2^p, split into FP16 hi + lo, as
     // tensor-memory rows: [piece][lane = node, 128][KT / 2] words, word p of a
     // row holding columns 2p (low half) and 2p + 1.
@@ -841,7 +842,7 @@ int device_stage_multi(dg_mesh* const* ms, int n, const float* const* u_in, floa
       err = "every mesh of one call must be on the same device";
       return DG_ERR_ARG;
     }
-    if (use_tc(ms[i], {u_in[i], u_out[i], res[i]})) fam[i] = ms[i]->N <= 4 ? 1 : 2;
+    if (use_tc(ms[i], {u_in[i], u_out[i], res[i]})) fam[i] = ms[i]->N <= 4 ? 1 : ms[i]->N <= 6 ? 2 : 0;
   }
   for (int i = 0; i < n; ++i)
     if (fam[i] == 0) {

@@ -64,14 +64,14 @@ struct StageArgs {
   const float* tcgeo;       // per tile: [kTcGeoWords][tc_tile_elems(N)] word-major geometry
   int tc_geo_stride;        // floats per tile block
   const void* tcB;          // FP16 [Dr Ds Dt LIFT] hi/lo pieces: orders <= 4 in the canonical
-                            // K-major shared-memory layout, orders 5, 6 as tensor-memory rows
+                            // K-major shared-memory layout, orders 5..7 as tensor-memory rows
   float tc_inv_bscale;      // 1 / (power-of-two scale applied to [Dr Ds Dt LIFT])
   int* status;              // set to 1 if an MMA completion wait timed out
   int absorbing;            // 1 if any boundary face is absorbing (code kAbsorbingCode)
 };
 
 // Tensor-core stage: elements per tile.  Orders <= 4: 6 * 20 = 120 of the 128
-// MMA rows (fields are the A operand); orders 5, 6: 6 * 8 = 48 MMA columns
+// MMA rows (fields are the A operand); orders 5..7: 6 * 8 = 48 MMA columns
 // (fields are the B operand, the operator sits in tensor memory).
 constexpr int kTcTileElems = 20;
 constexpr int kTtTileElems = 8;
@@ -80,13 +80,13 @@ __host__ __device__ constexpr int tc_tile_elems(int N) { return N <= 4 ? kTcTile
 // neighbour codes, 10 + 4f .. 13 + 4f normal and Fscale of face f, 26 + f
 // neighbour element of face f.
 constexpr int kTcGeoWords = 30;
-constexpr int kTcMaxOrder = 6;
+constexpr int kTcMaxOrder = 7;
 // Floats of one tile's geometry block: kTcGeoWords x E words, then E * 4 Nfp
 // neighbour-node bytes (a multiple of 16 bytes), E = tc_tile_elems(N).
 __host__ __device__ constexpr int tc_geo_floats(int N) {
   return kTcGeoWords * tc_tile_elems(N) + tc_tile_elems(N) * 4 * ((N + 1) * (N + 2) / 2) / 4;
 }
-// Orders 5, 6: [Dr Ds Dt LIFT] columns (K) with each derivative block padded to
+// Orders 5..7: [Dr Ds Dt LIFT] columns (K) with each derivative block padded to
 // whole 8-value chunks, and tensor-memory columns of one FP16 operator piece.
 __host__ __device__ constexpr int tt_kb(int N) { return (((N + 1) * (N + 2) * (N + 3) / 6) + 7) & ~7; }
 __host__ __device__ constexpr int tt_kt(int N) { return (3 * tt_kb(N) + 4 * ((N + 1) * (N + 2) / 2) + 15) & ~15; }

@@ -58,15 +58,26 @@ template <int N> struct TtDims {
   static constexpr int CG = KB / 8;                   // chunks per mu block
   static constexpr int CF = KG / 8;                   // first flux chunk
   static constexpr int ACOLS = tt_acols(N);           // tensor-memory columns per Op piece
-  static constexpr int ACC0 = 2 * ACOLS;              // first accumulator column
+  // Nodes reach tensor-memory lanes 96..127 (N = 7): all four lane quarters
+  // update (warp 3 also issues the MMAs and copies), the accumulator is single
+  // buffered, and the k-steps of Op_lo that do not fit tensor memory beside
+  // Op_hi and the accumulator are the MMA's A operand from shared memory.
+  static constexpr bool W4 = Np > 96;
+  static constexpr int NACC = W4 ? 1 : 2;             // accumulator buffers
+  static constexpr int LCOLS = W4 ? 512 - ACOLS - NN : ACOLS;   // Op_lo columns in tensor memory
+  static constexpr int LSTEPS = LCOLS / 8;            // k-steps of Op_lo read from tensor memory
+  static constexpr int ACC0 = ACOLS + LCOLS;          // first accumulator column
   static constexpr int PRODUCERS = 384;               // a multiple of ROWS
-  static constexpr int THREADS = 128 + PRODUCERS;     // 4 epilogue warps + producer warps
+  static constexpr int THREADS = 128 + PRODUCERS;     // 4 MMA/epilogue warps + producer warps
   static constexpr int QR = PRODUCERS / ROWS;         // producers per X row
   static constexpr int CPT = (KCH + QR - 1) / QR;     // X chunks per producer
   static constexpr int ITEMS = (E * NF + PRODUCERS - 1) / PRODUCERS;   // flux items per producer
   static constexpr int FSTR = ((NF / 4) | 1) * 4;     // flux row stride: 16-byte row reads of
                                                       // 8 consecutive rows are conflict-free
-  static constexpr int NSU = 5, NSR = 2;              // ring slots: fields+geometry, RK register
+  // ring slots: fields+geometry, RK register (W4: the update reads and writes
+  // global memory directly, the fields' slots serve the producers only)
+  static constexpr int NSU = W4 ? 3 : 5, NSR = W4 ? 0 : 2;
+  static constexpr int NSR1 = NSR ? NSR : 1;          // array size and modulus
   // shared memory (bytes)
   static constexpr int U_FLOATS = 6 * E * Np;
   static constexpr int G_FLOATS = tc_geo_floats(N);
@@ -79,12 +90,15 @@ template <int N> struct TtDims {
   static constexpr int OFF_BND = OFF_F + ROWS * FSTR * 4;    // [QR][ROWS] partial row maxima
   static constexpr int OFF_SC = OFF_BND + QR * ROWS * 4;     // [4][ROWS] column factors
   static constexpr int OFF_TAB = OFF_SC + 4 * ROWS * 4;      // face-node table (NF bytes)
-  static constexpr int SMEM = OFF_TAB + ((NF + 15) & ~15);
+  // Op_lo k-steps LSTEPS.. as A operand: [k-step][2 chunks][128 rows][16 bytes]
+  static constexpr int OFF_TAIL = (OFF_TAB + NF + 127) & ~127;
+  static constexpr int TAIL_CH = (KSTEPS - LSTEPS) * 2;      // 8-value chunks
+  static constexpr int SMEM = W4 ? OFF_TAIL + TAIL_CH * 128 * 16 : OFF_TAB + ((NF + 15) & ~15);
   static_assert(NN % 16 == 0 && NN <= 256, "MMA N");
   static_assert(PRODUCERS % ROWS == 0 && PRODUCERS % 32 == 0 && CPT * QR >= KCH, "X chunk split");
-  static_assert(ACC0 + 2 * NN <= 512, "tensor-memory budget");
-  static_assert(ACOLS % 16 == 0, "operator columns are written 16 at a time");
-  static_assert(Np <= 128 && NF < 128 && Np < 128 && E <= 32, "item encoding");
+  static_assert(ACC0 + NACC * NN <= 512, "tensor-memory budget");
+  static_assert(ACOLS % 16 == 0 && LCOLS % 16 == 0 && LCOLS <= ACOLS, "operator columns are written 16 at a time");
+  static_assert(Np <= 128 && NF < 256 && E <= 32, "item encoding");
   static_assert((E * Np * 4) % 16 == 0 && (U_FLOATS * 4) % 16 == 0 && (G_FLOATS * 4) % 16 == 0,
                 "bulk-copy alignment");
   static_assert((Np * 4) % 16 == 0 && (FSTR * 4) % 16 == 0, "16-byte row chunks");
@@ -95,7 +109,7 @@ template <int N> struct TtDims {
   // a warp are conflict-free) in the X / U region, before the ring starts
   static constexpr int OPW = ACOLS + 4;               // staged row stride (words)
   static constexpr int OP_VEC = 128 * ACOLS / 4;      // 16-byte words of one piece
-  static_assert(128 * OPW * 4 <= OFF_R, "operator staging area");
+  static_assert(128 * OPW * 4 <= OFF_R && (!W4 || 128 * OPW * 4 <= OFF_TAIL), "operator staging area");
 };
 
 // One thread: bulk copies of tile `tile`'s fields and geometry block.
@@ -123,6 +137,16 @@ __device__ __forceinline__ void tt_load_res(const StageArgs& A, int tile, float*
     tc::bulk_g2s(sr + c * D::E * D::Np, A.res + (size_t(c) * K + k0) * D::Np, fb, bar);
 }
 
+// One thread: L2 prefetch of tile `tile`'s RK register (read by the update
+// warps straight from global memory).
+template <int N>
+__device__ __forceinline__ void tt_prefetch_res(const StageArgs& A, int tile) {
+  using D = TtDims<N>;
+  const int K = A.K, k0 = tile * D::E, Ev = min(D::E, K - k0);
+  const uint32_t fb = uint32_t(Ev) * D::Np * 4;
+  for (int c = 0; c < 6; ++c) tc::bulk_prefetch_l2(A.res + (size_t(c) * K + k0) * D::Np, fb);
+}
+
 // 8 consecutive floats from a 16-byte aligned shared address.
 __device__ __forceinline__ void lds8(const float* p, float* v) {
   const float4 a = reinterpret_cast<const float4*>(p)[0];
@@ -143,8 +167,8 @@ __device__ __forceinline__ void tt_stage_body(const StageArgs& A, const int cta,
   extern __shared__ __align__(1024) unsigned char smem[];
   __shared__ uint32_t s_tmem;
   __shared__ __align__(8) uint64_t s_u_full[D::NSU];
-  __shared__ __align__(8) uint64_t s_r_full[D::NSR];
-  __shared__ __align__(8) uint64_t s_x_full, s_mma_done[2];
+  __shared__ __align__(8) uint64_t s_r_full[D::NSR1];
+  __shared__ __align__(8) uint64_t s_x_full, s_mma_done[2], s_acc_free;
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int K = A.K;
@@ -170,6 +194,7 @@ __device__ __forceinline__ void tt_stage_body(const StageArgs& A, const int cta,
     for (int i = 0; i < D::NSR; ++i) tc::mbar_init(&s_r_full[i], 1);
     tc::mbar_init(&s_x_full, D::PRODUCERS);        // every producer thread stores X chunks
     for (int i = 0; i < 2; ++i) tc::mbar_init(&s_mma_done[i], 1);
+    tc::mbar_init(&s_acc_free, 4);                 // W4: one arrival per epilogue warp
     tc::fence_mbar_init();
   }
   tc::fence_before_sync();
@@ -203,7 +228,7 @@ __device__ __forceinline__ void tt_stage_body(const StageArgs& A, const int cta,
       const uint4* row = stage + (warp * 32 + lane) * (D::OPW / 4);
       const uint32_t trow = tbase + (uint32_t(warp * 32) << 16) + piece * D::ACOLS;
 #pragma unroll 1
-      for (int c0 = 0; c0 < D::ACOLS; c0 += 16) {
+      for (int c0 = 0; c0 < (piece ? D::LCOLS : D::ACOLS); c0 += 16) {
         uint32_t v[16];
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
@@ -213,6 +238,16 @@ __device__ __forceinline__ void tt_stage_body(const StageArgs& A, const int cta,
         tc::tmem_st<16>(trow + c0, v);
       }
       tc::tmem_st_wait();
+    }
+    if (D::W4 && piece == 1) {
+      // Op_lo columns LCOLS.. into the canonical K-major A layout: chunk c of
+      // row r (8 K values, 16 bytes) at (c * 128 + r) * 16
+      uint4* tail = reinterpret_cast<uint4*>(smem + D::OFF_TAIL);
+      for (int i = tid; i < D::TAIL_CH * 128; i += D::THREADS) {
+        const int c = i >> 7, r = i & 127;
+        tail[i] = stage[r * (D::OPW / 4) + D::LCOLS / 4 + c];
+      }
+      tc::fence_proxy_async_smem();                 // generic stores -> tensor-core reads
     }
     tc::fence_before_sync();
     __syncthreads();                                 // staging area free again
@@ -224,81 +259,99 @@ __device__ __forceinline__ void tt_stage_body(const StageArgs& A, const int cta,
 
   if (warp < 4) {
     // ======================= MMA issue + epilogue warps ========================
-    // Nodes i < Np <= 84 sit in tensor-memory lanes 0..95, so warp 3 (lanes
-    // 96..127) holds none: it issues the MMAs and all bulk copies while warps
-    // 0..2 apply the RK update.  Named barrier 1 (these 128 threads) closes
-    // iteration j: the update of tile j-1 is done (its tiles may be stored and
-    // its accumulator reused), and warp 3 has acquired X(j) -- which carries
-    // tile j's column factors to warps 0..2.
-    static_assert(Np <= 96, "warp 3 holds no node");
+    // Warp 3 issues the MMAs and all bulk copies; lane i of warp w updates node
+    // 32 w + i.  Orders 5, 6: nodes i < Np <= 84 sit in tensor-memory lanes
+    // 0..95, so warp 3 holds none and only issues, while warps 0..2 update from
+    // and into the shared-memory tiles.  Order 7 (W4): all four warps read the
+    // single accumulator first (freeing it for the next tile's MMAs), warp 3
+    // then issues, and the update reads and writes global memory directly.
+    // Named barrier 1 (these 128 threads) closes iteration j: the update of
+    // tile j-1 is done (its tiles may be stored and, with two accumulators, its
+    // accumulator reused), and warp 3 has acquired X(j) -- which carries tile
+    // j's column factors to the updating warps.
+    static_assert(D::W4 || Np <= 96, "warp 3 holds no node");
     const int node = warp * 32 + lane;
     const uint32_t lane_off = uint32_t(warp * 32) << 16;
-    if (warp == 3 && tc::elect_one()) {   // first loads: fields of tiles 0..NSU-2, res of tile 0
-      for (int t = 0; t < D::NSU - 1 && t < ntiles; ++t)
-        tt_load_u<N>(A, base + t * ncta, sU + t * D::U_FLOATS, sG + t * D::G_FLOATS,
-                     &s_u_full[t]);
-      if (RK) tt_load_res<N>(A, base, sR, &s_r_full[0]);
+    if (warp == 3 && tc::elect_one()) {
+      if constexpr (D::W4) {            // first loads: fields of tiles 0..NSU-1
+        for (int t = 0; t < D::NSU && t < ntiles; ++t) {
+          tt_load_u<N>(A, base + t * ncta, sU + t * D::U_FLOATS, sG + t * D::G_FLOATS,
+                       &s_u_full[t]);
+          if (RK) tt_prefetch_res<N>(A, base + t * ncta);
+        }
+      } else {                          // fields of tiles 0..NSU-2, res of tile 0
+        for (int t = 0; t < D::NSU - 1 && t < ntiles; ++t)
+          tt_load_u<N>(A, base + t * ncta, sU + t * D::U_FLOATS, sG + t * D::G_FLOATS,
+                       &s_u_full[t]);
+        if (RK) tt_load_res<N>(A, base, sR, &s_r_full[0]);
+      }
     }
     __syncwarp();
     constexpr uint32_t IDESC = tc::idesc_f16(128, D::NN);
     constexpr uint32_t LBO = (D::NN / 8) * 128;
+    // warp 3: the 3 x KSTEPS MMAs of tile j (passes hi.hi, hi.lo, lo.hi)
+    auto issue_mmas = [&](int j) {
+      wait_or_flag(&s_x_full, j & 1, A.status);
+      if (D::W4 && j >= 1) wait_or_flag(&s_acc_free, (j - 1) & 1, A.status);
+      tc::fence_after_sync();
+      const uint32_t d_acc = tbase + D::ACC0 + (D::NACC == 2 ? (j & 1) * D::NN : 0);
+      const uint64_t b_hi = tc::smem_desc(tc::smem_u32(sXhi), LBO, 128);
+      const uint64_t b_lo = b_hi + uint64_t(D::X_BYTES >> 4);
+      const uint64_t a_tail = tc::smem_desc(tc::smem_u32(smem + D::OFF_TAIL), 128 * 16, 128);
+      // fully unrolled: warp-uniform operands (base + constant) issue cheaply
+#pragma unroll
+      for (int i = 0; i < 3 * D::KSTEPS; ++i) {
+        const int p = i / D::KSTEPS, ks = i - p * D::KSTEPS;
+        const uint64_t bd = (p == 1 ? b_lo : b_hi) + uint64_t((ks * 2 * LBO) >> 4);
+        if (p == 2 && ks >= D::LSTEPS) {               // Op_lo k-step from shared memory
+          const uint64_t ad = a_tail + uint64_t(((ks - D::LSTEPS) * 2 * 128 * 16) >> 4);
+          tc::mma_f16_ss_warp(d_acc, ad, bd, IDESC, 1u);
+        } else {
+          const uint32_t ad = tbase + (p == 2 ? D::ACOLS : 0) + ks * 8;
+          tc::mma_f16_ts_warp(d_acc, ad, bd, IDESC, i > 0 ? 1u : 0u);
+        }
+      }
+      tc::mma_commit_warp(&s_mma_done[j & 1]);
+    };
     for (int j = 0; j <= ntiles; ++j) {
       const int t = j - 1, buf = t & 1;               // tile whose update runs in iteration j
       const int tile = base + t * ncta;
       const int k0 = tile * E, Ev = min(E, K - k0);
-      if (warp == 3) {
-        if (j < ntiles) {                              // MMAs of tile j into accumulator j & 1
-          wait_or_flag(&s_x_full, j & 1, A.status);
-          tc::fence_after_sync();
-          const uint32_t d_acc = tbase + D::ACC0 + (j & 1) * D::NN;
-          const uint64_t b_hi = tc::smem_desc(tc::smem_u32(sXhi), LBO, 128);
-          const uint64_t b_lo = b_hi + uint64_t(D::X_BYTES >> 4);
-          // fully unrolled: warp-uniform operands (base + constant) issue cheaply
-#pragma unroll
-          for (int i = 0; i < 3 * D::KSTEPS; ++i) {
-            const int p = i / D::KSTEPS, ks = i - p * D::KSTEPS;   // passes: hi.hi, hi.lo, lo.hi
-            const uint64_t bd = (p == 1 ? b_lo : b_hi) + uint64_t((ks * 2 * LBO) >> 4);
-            const uint32_t ad = tbase + (p == 2 ? D::ACOLS : 0) + ks * 8;
-            tc::mma_f16_ts_warp(d_acc, ad, bd, IDESC, i > 0 ? 1u : 0u);
-          }
-          tc::mma_commit_warp(&s_mma_done[j & 1]);
-        }
-        if (j >= 1 && tc::elect_one()) {
-          // the slots of tile t-1 (stored in the previous iteration) take tiles
-          // t+NSU-1 and t+1 now, while warps 0..2 update tile t
-          asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
-          tc::fence_proxy_async_smem();
-          if (t + D::NSU - 1 < ntiles) {
-            const int s = (t + D::NSU - 1) % D::NSU;
-            tt_load_u<N>(A, tile + (D::NSU - 1) * ncta, sU + s * D::U_FLOATS,
-                         sG + s * D::G_FLOATS, &s_u_full[s]);
-          }
-          if (RK && t + 1 < ntiles) {
-            const int s = (t + 1) % D::NSR;
-            tt_load_res<N>(A, tile + ncta, sR + s * D::U_FLOATS, &s_r_full[s]);
-          }
-        }
-        __syncwarp();
-      } else if (j >= 1) {                             // RK update of tile t = j - 1
-        float* su = sU + (t % D::NSU) * D::U_FLOATS;
-        float* sr = sR + (t % D::NSR) * D::U_FLOATS;
-        wait_or_flag(&s_mma_done[buf], (t >> 1) & 1, A.status);
-        if (RK) wait_or_flag(&s_r_full[t % D::NSR], (t / D::NSR) & 1, A.status);
-        tc::fence_after_sync();
+      if constexpr (D::W4) {
         uint32_t acc[D::NN];
-        tmem_load_cols<D::NN>(tbase + lane_off + D::ACC0 + buf * D::NN, acc);
-        tc::tmem_ld_wait();
-        tc::fence_before_sync();
-        if (node < Np) {
+        if (j >= 1) {                                  // accumulator of tile t -> registers
+          wait_or_flag(&s_mma_done[buf], (t >> 1) & 1, A.status);
+          tc::fence_after_sync();
+          tmem_load_cols<D::NN>(tbase + lane_off + D::ACC0, acc);
+          tc::tmem_ld_wait();
+          tc::fence_before_sync();
+          __syncwarp();
+          if (lane == 0) tc::mbar_arrive(&s_acc_free);
+        }
+        if (warp == 3) {
+          if (j < ntiles) {
+            issue_mmas(j);
+            if (tc::elect_one()) {
+              // the producers are done with tile j's slot: it takes tile j + NSU
+              tc::fence_proxy_async_smem();
+              if (j + D::NSU < ntiles) {
+                const int jt = base + (j + D::NSU) * ncta, s = j % D::NSU;
+                tt_load_u<N>(A, jt, sU + s * D::U_FLOATS, sG + s * D::G_FLOATS, &s_u_full[s]);
+                if (RK) tt_prefetch_res<N>(A, jt);
+              }
+            }
+          }
+          __syncwarp();
+        }
+        if (j >= 1 && node < Np) {
+          // RK update of tile t: column n = (c, e) is node `node` of field c of
+          // element k0 + e, so a warp reads and writes 32 consecutive floats
           const float* scl = sScale + (t & 3) * ROWS;
           float dte[E];
 #pragma unroll
           for (int e = 0; e < E; ++e)
             dte[e] = RK && A.dt_elem && e < Ev ? __ldg(A.dt_elem + k0 + e) : A.dt;
-          // column n = (c, e) is the tile row n * Np + node; u and res share one
-          // shared array, so every batch is loaded before any of its stores;
-          // columns are paired (n, n + 1) for packed FP32x2 arithmetic
-          constexpr int CH = 12;
+          constexpr int CH = 16;
           static_assert(ROWS % CH == 0 && E % 2 == 0, "epilogue batches");
 #pragma unroll
           for (int n0 = 0; n0 < ROWS; n0 += CH) {
@@ -306,13 +359,16 @@ __device__ __forceinline__ void tt_stage_body(const StageArgs& A, const int cta,
             if (RK) {
 #pragma unroll
               for (int q = 0; q < CH; ++q) {
-                rv[q] = sr[(n0 + q) * Np + node];
-                uv[q] = su[(n0 + q) * Np + node];
+                const int n = n0 + q, c = n / E, e = n - (n / E) * E;
+                const size_t g = (size_t(c) * K + k0 + e) * Np + node;
+                rv[q] = e < Ev ? A.res[g] : 0.f;
+                uv[q] = e < Ev ? __ldg(A.u_in + g) : 0.f;
               }
             }
 #pragma unroll
             for (int q = 0; q < CH; q += 2) {
-              const int n = n0 + q, e = n % E;           // e even: e + 1 < E
+              const int n = n0 + q, c = n / E, e = n - (n / E) * E;   // e even: e + 1 < E
+              const size_t g = (size_t(c) * K + k0 + e) * Np + node;
               const float2 r = __fmul2_rn(
                   make_float2(__uint_as_float(acc[n]), __uint_as_float(acc[n + 1])),
                   make_float2(scl[n], scl[n + 1]));
@@ -321,39 +377,116 @@ __device__ __forceinline__ void tt_stage_body(const StageArgs& A, const int cta,
                                              __fmul2_rn(make_float2(dte[e], dte[e + 1]), r));
                 const float2 un = __ffma2_rn(f2(A.b), rn, make_float2(uv[q], uv[q + 1]));
                 if (e < Ev) {
-                  sr[n * Np + node] = rn.x;
-                  su[n * Np + node] = un.x;
+                  A.res[g] = rn.x;
+                  A.u_out[g] = un.x;
                 }
                 if (e + 1 < Ev) {
-                  sr[(n + 1) * Np + node] = rn.y;
-                  su[(n + 1) * Np + node] = un.y;
+                  A.res[g + Np] = rn.y;
+                  A.u_out[g + Np] = un.y;
                 }
               } else {
-                if (e < Ev) sr[n * Np + node] = r.x;
-                if (e + 1 < Ev) sr[(n + 1) * Np + node] = r.y;
+                if (e < Ev) A.rhs[g] = r.x;
+                if (e + 1 < Ev) A.rhs[g + Np] = r.y;
               }
             }
           }
         }
-        tc::fence_proxy_async_smem();                  // tile stores -> bulk-copy reads
-      }
-      named_sync(1, 128);
-      if (warp == 3 && j >= 1 && tc::elect_one()) {
-        float* su = sU + (t % D::NSU) * D::U_FLOATS;
-        float* sr = sR + (t % D::NSR) * D::U_FLOATS;
-        const uint32_t fb = uint32_t(Ev) * Np * 4;
-        for (int c = 0; c < 6; ++c) {
-          const size_t g = (size_t(c) * K + k0) * Np;
-          if (RK) {
-            tc::bulk_s2g(A.u_out + g, su + c * E * Np, fb);
-            tc::bulk_s2g(A.res + g, sr + c * E * Np, fb);
-          } else {
-            tc::bulk_s2g(A.rhs + g, sr + c * E * Np, fb);
+        named_sync(1, 128);
+      } else {
+        if (warp == 3) {
+          if (j < ntiles) issue_mmas(j);               // into accumulator j & 1
+          if (j >= 1 && tc::elect_one()) {
+            // the slots of tile t-1 (stored in the previous iteration) take tiles
+            // t+NSU-1 and t+1 now, while warps 0..2 update tile t
+            asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+            tc::fence_proxy_async_smem();
+            if (t + D::NSU - 1 < ntiles) {
+              const int s = (t + D::NSU - 1) % D::NSU;
+              tt_load_u<N>(A, tile + (D::NSU - 1) * ncta, sU + s * D::U_FLOATS,
+                           sG + s * D::G_FLOATS, &s_u_full[s]);
+            }
+            if (RK && t + 1 < ntiles) {
+              const int s = (t + 1) % D::NSR1;
+              tt_load_res<N>(A, tile + ncta, sR + s * D::U_FLOATS, &s_r_full[s]);
+            }
           }
+          __syncwarp();
+        } else if (j >= 1) {                           // RK update of tile t = j - 1
+          float* su = sU + (t % D::NSU) * D::U_FLOATS;
+          float* sr = sR + (t % D::NSR1) * D::U_FLOATS;
+          wait_or_flag(&s_mma_done[buf], (t >> 1) & 1, A.status);
+          if (RK) wait_or_flag(&s_r_full[t % D::NSR1], (t / D::NSR1) & 1, A.status);
+          tc::fence_after_sync();
+          uint32_t acc[D::NN];
+          tmem_load_cols<D::NN>(tbase + lane_off + D::ACC0 + buf * D::NN, acc);
+          tc::tmem_ld_wait();
+          tc::fence_before_sync();
+          if (node < Np) {
+            const float* scl = sScale + (t & 3) * ROWS;
+            float dte[E];
+#pragma unroll
+            for (int e = 0; e < E; ++e)
+              dte[e] = RK && A.dt_elem && e < Ev ? __ldg(A.dt_elem + k0 + e) : A.dt;
+            // column n = (c, e) is the tile row n * Np + node; u and res share one
+            // shared array, so every batch is loaded before any of its stores;
+            // columns are paired (n, n + 1) for packed FP32x2 arithmetic
+            constexpr int CH = 12;
+            static_assert(ROWS % CH == 0 && E % 2 == 0, "epilogue batches");
+#pragma unroll
+            for (int n0 = 0; n0 < ROWS; n0 += CH) {
+              float rv[CH], uv[CH];
+              if (RK) {
+#pragma unroll
+                for (int q = 0; q < CH; ++q) {
+                  rv[q] = sr[(n0 + q) * Np + node];
+                  uv[q] = su[(n0 + q) * Np + node];
+                }
+              }
+#pragma unroll
+              for (int q = 0; q < CH; q += 2) {
+                const int n = n0 + q, e = n % E;           // e even: e + 1 < E
+                const float2 r = __fmul2_rn(
+                    make_float2(__uint_as_float(acc[n]), __uint_as_float(acc[n + 1])),
+                    make_float2(scl[n], scl[n + 1]));
+                if (RK) {
+                  const float2 rn = __ffma2_rn(f2(A.a), make_float2(rv[q], rv[q + 1]),
+                                               __fmul2_rn(make_float2(dte[e], dte[e + 1]), r));
+                  const float2 un = __ffma2_rn(f2(A.b), rn, make_float2(uv[q], uv[q + 1]));
+                  if (e < Ev) {
+                    sr[n * Np + node] = rn.x;
+                    su[n * Np + node] = un.x;
+                  }
+                  if (e + 1 < Ev) {
+                    sr[(n + 1) * Np + node] = rn.y;
+                    su[(n + 1) * Np + node] = un.y;
+                  }
+                } else {
+                  if (e < Ev) sr[n * Np + node] = r.x;
+                  if (e + 1 < Ev) sr[(n + 1) * Np + node] = r.y;
+                }
+              }
+            }
+          }
+          tc::fence_proxy_async_smem();                // tile stores -> bulk-copy reads
         }
-        tc::bulk_commit();
+        named_sync(1, 128);
+        if (warp == 3 && j >= 1 && tc::elect_one()) {
+          float* su = sU + (t % D::NSU) * D::U_FLOATS;
+          float* sr = sR + (t % D::NSR1) * D::U_FLOATS;
+          const uint32_t fb = uint32_t(Ev) * Np * 4;
+          for (int c = 0; c < 6; ++c) {
+            const size_t g = (size_t(c) * K + k0) * Np;
+            if (RK) {
+              tc::bulk_s2g(A.u_out + g, su + c * E * Np, fb);
+              tc::bulk_s2g(A.res + g, sr + c * E * Np, fb);
+            } else {
+              tc::bulk_s2g(A.rhs + g, sr + c * E * Np, fb);
+            }
+          }
+          tc::bulk_commit();
+        }
+        __syncwarp();
       }
-      __syncwarp();
     }
     if (warp == 3 && tc::elect_one()) tc::bulk_wait_all();
     __syncwarp();
@@ -368,14 +501,14 @@ __device__ __forceinline__ void tt_stage_body(const StageArgs& A, const int cta,
     const int fb = xc < 3 ? 3 + (o + 1) % 3 : (o + 1) % 3;
     const float sgn = xc < 3 ? 1.f : -1.f;
     // Item idx = pt + q * PRODUCERS is face node m of element e (idx = e * NF + m).
-    // Tile-independent decode: e | m << 5 | f << 12 | idM << 14, bit 31 past the end.
+    // Tile-independent decode: e | m << 5 | f << 13 | idM << 15, bit 31 past the end.
     uint32_t item[D::ITEMS];
 #pragma unroll
     for (int q = 0; q < D::ITEMS; ++q) {
       const int idx = pt + q * D::PRODUCERS;
       const int e = idx / NF, m = idx - e * NF;
-      item[q] = idx < E * NF ? uint32_t(e) | uint32_t(m) << 5 | uint32_t(m / Nfp) << 12 |
-                                   uint32_t(sFmask[m]) << 14
+      item[q] = idx < E * NF ? uint32_t(e) | uint32_t(m) << 5 | uint32_t(m / Nfp) << 13 |
+                                   uint32_t(sFmask[m]) << 15
                              : 0x80000000u;
     }
     float* F = sF;
@@ -395,7 +528,7 @@ __device__ __forceinline__ void tt_stage_body(const StageArgs& A, const int cta,
 #pragma unroll
       for (int q = 0; q < D::ITEMS; ++q) {
         const uint32_t it = item[q];
-        const int e = it & 31, m = (it >> 5) & 127, f = (it >> 12) & 3, idM = (it >> 14) & 127;
+        const int e = it & 31, m = (it >> 5) & 255, f = (it >> 13) & 3, idM = (it >> 15) & 127;
         const bool ok = !(it >> 31) && e < Ev;
         const int ec = ok ? e : 0;
         const unsigned code = (__float_as_uint(sg[9 * E + ec]) >> (8 * f)) & 0xffu;
@@ -426,8 +559,8 @@ __device__ __forceinline__ void tt_stage_body(const StageArgs& A, const int cta,
 #pragma unroll
         for (int q = 0; q < D::ITEMS; ++q) {
           const uint32_t it = item[q], kind = info[q] & 3u;
-          const int e = kind ? int(it & 31) : 0, m = (it >> 5) & 127, f = (it >> 12) & 3;
-          const int idM = (it >> 14) & 127;
+          const int e = kind ? int(it & 31) : 0, m = (it >> 5) & 255, f = (it >> 13) & 3;
+          const int idM = (it >> 15) & 127;
           const float* pp = kind == 3u ? F + e * FSTR + m
                                        : su + (EXT ? (info[q] >> 2) & 0x1FFFFFFFu : info[q] >> 2);
           const int ps = kind == 3u ? E * FSTR : E * Np;
@@ -473,7 +606,7 @@ __device__ __forceinline__ void tt_stage_body(const StageArgs& A, const int cta,
           fl[3] = fmaf(-al, dHx, fmaf(nx, aH, yp * fmaf(-nz, dEy, ny * dEz)));
           fl[4] = fmaf(-al, dHy, fmaf(ny, aH, yp * fmaf(-nx, dEz, nz * dEx)));
           fl[5] = fmaf(-al, dHz, fmaf(nz, aH, yp * fmaf(-ny, dEx, nx * dEy)));
-          float* fr = F + int(item[q] & 31) * FSTR + int((item[q] >> 5) & 127);
+          float* fr = F + int(item[q] & 31) * FSTR + int((item[q] >> 5) & 255);
 #pragma unroll
           for (int c = 0; c < 6; ++c) fr[c * E * FSTR] = (c < 3 ? scE : scH) * fl[c];
         }

@@ -131,6 +131,14 @@ __device__ __forceinline__ void mma_f16_ts_warp(uint32_t d_tmem, uint32_t a_tmem
       " @P tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, Q;\n}"
       :: "r"(d_tmem), "r"(a_tmem), "l"(b_desc), "r"(idesc), "r"(accumulate) : "memory");
 }
+// D[tmem] (+)= A[smem desc] * B[smem desc], issued like mma_f16_ts_warp.
+__device__ __forceinline__ void mma_f16_ss_warp(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc,
+                                                uint32_t idesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred P, Q;\n elect.sync _|P, 0xffffffff;\n setp.ne.b32 Q, %4, 0;\n"
+      " @P tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, Q;\n}"
+      :: "r"(d_tmem), "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate) : "memory");
+}
 __device__ __forceinline__ void mma_commit_warp(uint64_t* mbar) {
   asm volatile(
       "{\n .reg .pred P;\n elect.sync _|P, 0xffffffff;\n"
@@ -220,6 +228,10 @@ __device__ __forceinline__ void bulk_g2s(void* smem, const void* gmem, uint32_t 
 __device__ __forceinline__ void bulk_s2g(void* gmem, const void* smem, uint32_t bytes) {
   asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;"
                :: "l"(gmem), "r"(smem_u32(smem)), "r"(bytes) : "memory");
+}
+// L2 prefetch of `bytes` (a multiple of 16) from a 16-byte aligned address.
+__device__ __forceinline__ void bulk_prefetch_l2(const void* gmem, uint32_t bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" :: "l"(gmem), "r"(bytes) : "memory");
 }
 __device__ __forceinline__ void bulk_commit() {
   asm volatile("cp.async.bulk.commit_group;" ::: "memory");

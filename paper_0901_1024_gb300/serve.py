@@ -264,7 +264,7 @@ class Server:
         e1.record(self.stream)
         e1.synchronize()
         ms = e0.elapsed_time(e1)
-        if impl == Mesh.STAGE_TC and N <= 6:
+        if impl == Mesh.STAGE_TC and N <= 7:
             # one tile's cost on one SM: stage time x CTAs in use / tiles
             tiles = -(-p.K // (20 if N <= 4 else 8))
             sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
@@ -276,14 +276,14 @@ class Server:
     def _choose_impl(self, N, solves):
         """(stage implementation, FP32 tile shape) of a pack: without autotuning
         the server's `impl` and the default shape; with it, the fastest of the
-        tensor-core stage (orders <= 6) and the FP32 stage in each tile shape,
+        tensor-core stage (orders <= 7) and the FP32 stage in each tile shape,
         timed on a scratch pack once per (device, order, decade of K)."""
         if not self.autotune:
             return self.impl, 0
         key = self._tune_key(N, solves)
         if key not in self._tuned:
             cands = [(Mesh.STAGE_FP32, 0), (Mesh.STAGE_FP32, 1)]
-            if N <= 6:
+            if N <= 7:
                 cands.insert(0, (Mesh.STAGE_TC, 0))
             times = {c: self._time_impl(N, solves, *c) for c in cands}
             self._tuned[key] = min(times, key=times.get)

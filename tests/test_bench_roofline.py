@@ -68,7 +68,7 @@ def test_stage_profiles_are_machine_readable(workload, family):
 
 
 def test_kernel_family_of_each_stage_path():
-    assert [bench.kernel_family(N, True) for N in range(1, 7)] == ["tc"] * 4 + ["tt"] * 2
+    assert [bench.kernel_family(N, True) for N in range(1, 8)] == ["tc"] * 4 + ["tt"] * 3
     assert {bench.kernel_family(N, False) for N in range(1, 10)} == {"fp32"}
     for files in bench.KERNEL_SOURCES.values():
         for f in files:

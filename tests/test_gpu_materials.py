@@ -78,7 +78,7 @@ def test_rhs_parity_materials(env, N, impl, what):
     out = torch.full_like(u, float("nan"))
     mesh.rhs(u, out)
     torch.cuda.synchronize()
-    tc_ran = impl == TC and N <= 6 and (om.K * om.Np) % 4 == 0
+    tc_ran = impl == TC and N <= 7 and (om.K * om.Np) % 4 == 0
     assert _kinds(mesh) == ({5} if tc_ran else {1})
     want = oracle.rhs(om, u32.astype(np.float64), 1.0, eps, mu, bc)
     got = out.cpu().numpy()

@@ -4,7 +4,8 @@ of several orders (the batched form of the paper's element-local stage).
 Every mesh's fields must be bit for bit those of its own per-mesh stage
 (dg_rk_stage_elem / dg_rk_stage): a packed element does the same arithmetic
 whichever CTA of the shared grid runs it.  Orders 1..4 share one launch, 5..6
-another, FP32-path meshes (order 7 here) launch alone; the trace shows it.
+another, the rest (order 7 here: the tensor-core kernel with part of its
+operator in shared memory) launch alone; the trace shows it.
 """
 import numpy as np
 import pytest

@@ -29,7 +29,7 @@ STEP_TOL = 1e-4
 FP32, TC = 1, 2
 FP32_S1 = 11                                   # FP32 stage in tile shape 1 (test-local code)
 KIND_FP32_STAGE, KIND_TC_STAGE = 0, 4          # dg_trace_read kinds of a fused RK stage
-TC_ORDERS = range(1, 7)
+TC_ORDERS = range(1, 8)
 
 
 @pytest.fixture(scope="module")
@@ -105,7 +105,7 @@ def test_100_steps_every_stage_instantiation(env, impl, N, kind):
 
 @pytest.mark.parametrize("N", TC_ORDERS)
 def test_several_tiles_per_cta_10_steps(env, N):
-    """K = 10 368 (orders 1..4: 519 tiles of 20) or 3 072 (orders 5, 6: 384
+    """K = 10 368 (orders 1..4: 519 tiles of 20) or 3 072 (orders 5..7: 384
     tiles of 8) on 152 SMs: every CTA runs two or more tiles through its rings."""
     torch, dg = env
     n = 12 if N <= 4 else 8
