@@ -171,17 +171,19 @@ int dg_set_boundary(dg_mesh* mesh, const int8_t* kind);
 /*
  * Implementation of the RK-stage operator (the paper notes that each operator
  * part may need its own strategy on the GPU, Section 4):
- *   DG_STAGE_AUTO   tensor cores for N = 2..6, FP32 CUDA cores for N = 1 and
- *                   above 6 (the faster kernel of each order on GB300; default);
+ *   DG_STAGE_AUTO   tensor cores for N = 2..7, FP32 CUDA cores for N = 1 and
+ *                   above 7 (the faster kernel of each order on GB300; default);
  *   DG_STAGE_FP32   FP32 CUDA cores for every order;
  *   DG_STAGE_TC     tensor cores (tcgen05): the volume and lifting contractions
  *                   as one GEMM per tile with three FP16 products
  *                   (A_hi B_hi + A_hi B_lo + A_lo B_hi, power-of-two row
- *                   scaling, FP32 accumulation), FP32 elsewhere; orders 1..6
- *                   (orders 5, 6 with [Dr Ds Dt LIFT] held in tensor memory).
- *                   Its tiles move by bulk copies, so it also needs K*Np to
- *                   be a multiple of 4 and 16-byte aligned field buffers;
- *                   otherwise (and for N > 6) the call runs DG_STAGE_FP32.
+ *                   scaling, FP32 accumulation), FP32 elsewhere; orders 1..7
+ *                   (orders 5..7 with [Dr Ds Dt LIFT] held in tensor memory,
+ *                   at order 7 the last k-steps of its low piece in shared
+ *                   memory).  Its tiles move by bulk copies, so it also needs
+ *                   K*Np to be a multiple of 4 and 16-byte aligned field
+ *                   buffers; otherwise (and for N > 7) the call runs
+ *                   DG_STAGE_FP32.
  * Host only.  Errors: DG_ERR_ARG for an unknown value.
  */
 #define DG_STAGE_AUTO 0
@@ -281,8 +283,9 @@ int dg_rk_stage_elem(dg_mesh* mesh, const float* u_in, float* u_out, float* res,
  * 1..4 share one persistent launch, those at orders 5, 6 another; each launch
  * splits its CTAs (one per SM) among the meshes in proportion to their tiles x
  * tile_cost, so all of them advance side by side on the GPU.  Meshes on the
- * FP32 CUDA-core stage (orders >= 7, forced FP32, unaligned sizes) get their own
- * launch.  For mesh i the result is bit for bit that of
+ * tensor-core stage at order 7 and those on the FP32 CUDA-core stage (orders
+ * >= 8, forced FP32, unaligned sizes) get their own launch.  For mesh i the
+ * result is bit for bit that of
  *   dg_rk_stage_elem(meshes[i], u_in[i], u_out[i], res[i], stage, dt_elem[i])
  * (or of dg_rk_stage with dt where dt_elem or dt_elem[i] is NULL): the paper's
  * element-local work (Section 5) assigned across solves.

@@ -835,7 +835,7 @@ int device_stage_multi(dg_mesh* const* ms, int n, const float* const* u_in, floa
                        const double* tile_cost, void* stream, std::string& err) {
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   int64_t launches = 0;
-  std::vector<int> fam(n, 0);        // 0: its own launch, 1: orders 1..4, 2: orders 5, 6
+  std::vector<int> fam(n, 0);        // 0: its own launch (order 7, FP32), 1: orders 1..4, 2: orders 5, 6
   for (int i = 0; i < n; ++i) {
     if (int rc = ensure_device(ms[i], err)) return rc;
     if (ms[i]->dev->device != ms[0]->dev->device) {

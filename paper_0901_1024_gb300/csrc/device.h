@@ -112,7 +112,8 @@ struct MixedArgs {
   int ngroups;
 };
 // Fused RK stages of groups of orders 1..4 (tensor cores, one 640-thread CTA
-// per SM) or of orders 5, 6 (tensor cores, operator in tensor memory).
+// per SM) or of orders 5, 6 (tensor cores, operator in tensor memory); order 7
+// always launches alone.
 cudaError_t launch_tc_mixed(const MixedArgs& m, int grid, cudaStream_t s);
 cudaError_t launch_tt_mixed(const MixedArgs& m, int grid, cudaStream_t s);
 

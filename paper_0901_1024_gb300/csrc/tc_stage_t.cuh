@@ -1,4 +1,4 @@
-// Tensor-core RK stage for orders 5 and 6: the operator lives in tensor memory.
+// Tensor-core RK stage for orders 5..7: the operator lives in tensor memory.
 //
 // The same contraction as the order <= 4 kernel (tc_stage.cuh), transposed:
 //     rhs^T[i, (c,e)] = sum_k Op[i, k] X[(c,e), k],
@@ -19,7 +19,18 @@
 // warps owns node i of every (c,e) of the tile -- the shared-memory order of
 // the RK update.
 //
-// One persistent 512-thread CTA per SM:
+// Order 7 (Np = 120, KT = 512): the two pieces take all 512 columns, so the
+// accumulator is single buffered (48 columns, freed as soon as the four
+// epilogue warps have read it into registers), Op_lo keeps its first 26
+// k-steps (208 columns) in tensor memory and its last 6 k-steps (24 KB) sit in
+// shared memory as the MMA's A operand (canonical K-major layout).  Nodes fill
+// lanes 0..119, so warp 3 updates as well as issuing; the shared-memory ring
+// then has room for three field slots and no RK register, and the update reads
+// res and u and writes res and u_out straight from and to global memory (a
+// warp touches 32 consecutive floats per column; res is prefetched into L2
+// with the fields' bulk copy).
+//
+// One persistent 512-thread CTA per SM (orders 5, 6):
 //   * producer warps (12): the fluxes of tile t (Alg. 3: face-node gathers by
 //     4-byte cp.async, upwind flux with the PEC ghost state), then, after a
 //     named barrier, the 48 x KT values of X(t) -- producer p builds the 8-value
