@@ -355,10 +355,12 @@ __device__ __forceinline__ void tt_stage_body(const StageArgs& A, const int cta,
         const bool upd = j >= 1 && node < Np;
         if (mma) mma_begin(j);
         const float* scl = sScale + (t & 3) * ROWS;
+        // per-element steps of tile t (only when an update runs: at j = 0 there
+        // is no tile t, and k0 would lie before the mesh)
         float dte[E];
 #pragma unroll
         for (int e = 0; e < E; ++e)
-          dte[e] = RK && A.dt_elem && e < Ev ? __ldg(A.dt_elem + k0 + e) : A.dt;
+          dte[e] = RK && upd && A.dt_elem && e < Ev ? __ldg(A.dt_elem + k0 + e) : A.dt;
         constexpr int CH = 16;
         static_assert(ROWS == 3 * CH && E % 2 == 0, "epilogue batches");
         // RK update of tile t, columns n0 .. n0 + 15: column n = (c, e) is node
