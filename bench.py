@@ -611,7 +611,7 @@ def run_serve(args):
                 "Gaussian pulse, jitter 0.1h, seeded")
     line = {"metric": "served solves/s", "value": ours["solves_per_s"], "unit": "solves/s",
             "higher_is_better": True, "n_gpus": 1,
-            "dtype": "f32 fields (FP16x3 tensor-core contractions for N = 2..6)",
+            "dtype": "f32 fields (FP16x3 tensor-core contractions for N = 2..7)",
             "data": "synthetic", "mode": "serve", "serve_config": args.serve_config,
             "config": {"workload": workload,
                        "server": "continuous batching: one packed launch per RK stage and order, "
