@@ -533,6 +533,16 @@ __device__ __forceinline__ void tt_stage_body(const StageArgs& A, const int cta,
     const int fa = xc < 3 ? 3 + (o + 2) % 3 : (o + 2) % 3;
     const int fb = xc < 3 ? 3 + (o + 1) % 3 : (o + 1) % 3;
     const float sgn = xc < 3 ? 1.f : -1.f;
+    // X chunks of this producer: its j-chunks jc = xq + QR i (i < nj, 8 nodes
+    // each) give the chunks of all three g^mu blocks from one load of U_a and
+    // U_b; flux chunks fill the rest of its CPT chunks, producer xq taking flux
+    // chunks f0 .. f0 + CPT - 3 nj - 1
+    constexpr int NJ = D::CG, NJS = (NJ + D::QR - 1) / D::QR;   // j-chunk slots
+    static_assert(3 * NJS <= D::CPT, "g chunks per producer");
+    const int nj = xq < NJ ? (NJ - 1 - xq) / D::QR + 1 : 0;
+    const int ng = 3 * nj;
+    int f0 = 0;
+    for (int p = 0; p < xq; ++p) f0 += D::CPT - 3 * (p < NJ ? (NJ - 1 - p) / D::QR + 1 : 0);
     // Item idx = pt + q * PRODUCERS is face node m of element e (idx = e * NF + m).
     // Tile-independent decode: e | m << 5 | f << 13 | idM << 15, bit 31 past the end.
     uint32_t item[D::ITEMS];
@@ -645,43 +655,52 @@ __device__ __forceinline__ void tt_stage_body(const StageArgs& A, const int cta,
         }
       }
       named_sync(2, D::PRODUCERS);                     // the flux buffer is complete
-      // ---- X(t): row xn, chunks xq + QR q (8 values each), and the row maximum
+      // ---- X(t): row xn, this producer's chunks (8 values each), row maximum
       const bool live = xe < Ev;
       float x[D::CPT][8];
-      float xmax = 0.f;
+      float ca[3], cb[3];
 #pragma unroll
-      for (int q = 0; q < D::CPT; ++q) {
-        const int ch = xq + D::QR * q;
-        float v[8];
-        if (ch >= D::KCH) {                            // past the row (uneven split)
+      for (int mu = 0; mu < 3; ++mu) {
+        ca[mu] = sgn * sg[(3 * mu + (o + 1) % 3) * E + xe];
+        cb[mu] = -sgn * sg[(3 * mu + (o + 2) % 3) * E + xe];
+      }
 #pragma unroll
-          for (int j = 0; j < 8; ++j) v[j] = 0.f;
-        } else if (ch < D::CF) {                       // g^mu, nodes j0 .. j0 + 7
-          const int mu = ch / D::CG, j0 = (ch - mu * D::CG) * 8;
-          const float ca = sgn * sg[(3 * mu + (o + 1) % 3) * E + xe];
-          const float cb = -sgn * sg[(3 * mu + (o + 2) % 3) * E + xe];
-          float va[8], vb[8];
+      for (int i = 0; i < NJS; ++i) {                  // g^mu, nodes j0 .. j0 + 7, mu = 0..2
+        const int j0 = (xq + D::QR * i) * 8;
+        float va[8], vb[8];
+        if (i < nj) {
           lds8(su + (fa * E + xe) * Np + j0, va);
           lds8(su + (fb * E + xe) * Np + j0, vb);
+        }
 #pragma unroll
-          for (int j = 0; j < 8; ++j) v[j] = j0 + j < Np ? fmaf(ca, va[j], cb * vb[j]) : 0.f;
-        } else {                                       // flux, face nodes m0 .. m0 + 7
-          const int m0 = (ch - D::CF) * 8;
+        for (int mu = 0; mu < 3; ++mu)
+#pragma unroll
+          for (int j = 0; j < 8; ++j)
+            x[3 * i + mu][j] = i < nj && j0 + j < Np ? fmaf(ca[mu], va[j], cb[mu] * vb[j]) : 0.f;
+      }
+#pragma unroll
+      for (int q = 0; q < D::CPT; ++q) {               // flux, face nodes m0 .. m0 + 7
+        if (q >= ng) {
+          const int m0 = (f0 + q - ng) * 8;
+          float v[8];
           if (m0 < NF) {
             lds8(F + xn * FSTR + m0, v);
 #pragma unroll
-            for (int j = 0; j < 8; ++j) v[j] = m0 + j < NF ? v[j] : 0.f;
+            for (int j = 0; j < 8; ++j) x[q][j] = m0 + j < NF ? v[j] : 0.f;
           } else {
 #pragma unroll
-            for (int j = 0; j < 8; ++j) v[j] = 0.f;
+            for (int j = 0; j < 8; ++j) x[q][j] = 0.f;
           }
         }
+      }
+      float xmax = 0.f;
+#pragma unroll
+      for (int q = 0; q < D::CPT; ++q)
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
-          x[q][j] = live ? v[j] : 0.f;
+          x[q][j] = live ? x[q][j] : 0.f;
           xmax = fmaxf(xmax, fabsf(x[q][j]));
         }
-      }
       sBound[xq * ROWS + xn] = xmax;
       named_sync(2, D::PRODUCERS);                     // row maxima published
       float rmax = 0.f;
@@ -702,8 +721,8 @@ __device__ __forceinline__ void tt_stage_body(const StageArgs& A, const int cta,
       if (t >= 1) wait_or_flag(&s_mma_done[(t - 1) & 1], ((t - 1) >> 1) & 1, A.status);
 #pragma unroll
       for (int q = 0; q < D::CPT; ++q) {
-        const int ch = xq + D::QR * q;
-        if (ch >= D::KCH) break;
+        const int ch = q < ng ? (q % 3) * NJ + xq + D::QR * (q / 3) : D::CF + f0 + q - ng;
+        if (ch >= D::KCH) continue;                   // past the row (uneven split)
         uint32_t hi[4], lo[4];
 #pragma unroll
         for (int p = 0; p < 4; ++p) {
