@@ -591,11 +591,13 @@ def run_serve(args):
         return res, summary(res, time.perf_counter() - t0, srv)
 
     served, ours = timed(Server(batch=True, graphs=not args.serve_no_graphs, autotune=True,
-                                rebuild_every=args.rebuild_every, mixed=False))
+                                rebuild_every=args.rebuild_every, mixed=False,
+                                dead_fraction=args.dead_fraction))
     shared = None
     if args.serve_shared:
         _, shared = timed(Server(batch=True, graphs=not args.serve_no_graphs, autotune=True,
-                                 rebuild_every=args.rebuild_every, mixed=True))
+                                 rebuild_every=args.rebuild_every, mixed=True,
+                                 dead_fraction=args.dead_fraction))
     same, base = timed(Server(hbm_budget=1.0, batch=False, graphs=False, autotune=False))
     plain_res, plain = timed(Server(hbm_budget=1.0, batch=False, graphs=False, autotune=False,
                                     impl=Mesh.STAGE_FP32))
@@ -632,8 +634,8 @@ def run_sweep(args):
     """Roofline curve over the order: for N = 1..9 a pulse workload on a box mesh
     with n chosen so that 6 K Np is about 1.7e7, timed per stage launch (CUDA
     events around back-to-back steps, divided by the stage count) after warm-up,
-    for the default stage kernel (tensor cores for N = 2..6, FP32 CUDA cores
-    otherwise) and, for N = 2..6, the FP32 kernel as well."""
+    for the default stage kernel (tensor cores for N = 2..7, FP32 CUDA cores
+    otherwise) and the FP32 kernel in both tile shapes."""
     import torch
     import paper_0901_1024_gb300 as dg
     peaks, _ = load_peaks()
@@ -697,6 +699,8 @@ def main():
     ap.add_argument("--rebuild-every", type=int, default=32,
                     help="serve mode: steps a pack runs before waiting solves join it")
     ap.add_argument("--serve-no-graphs", action="store_true")
+    ap.add_argument("--dead-fraction", type=float, default=0.15,
+                    help="serve: rebuild an aged pack once finished solves hold this share of it")
     ap.add_argument("--serve-shared", action="store_true",
                     help="serve mode: also time the server with shared launches of all orders")
     ap.add_argument("--rate", type=float, default=200.0)

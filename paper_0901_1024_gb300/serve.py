@@ -206,6 +206,11 @@ class Server:
     autotune   : pick each pack's stage implementation by timing; else `impl`.
     keep_fields: return every solve's final fields (host FP32) in its Result.
     rebuild_every: steps a pack runs before waiting solves may join it.
+    dead_fraction: share of a pack's elements held by finished solves (which
+                 keep stepping, unread) at which an aged pack is rebuilt
+                 without them.  On GB300, 200-request stream: 1.0 (only when
+                 every solve is done) 2.12 solves/s, 0.5 3.19, 0.3 3.49, 0.15
+                 3.62 (64 pack builds, 5.6 s of host time).
     mixed      : (with batch) advance all packs, of every order, with one
                  dg_rk_stage_multi call per RK stage -- one shared persistent
                  launch for orders 1..4 and one for 5, 6 -- its CTAs split by
@@ -218,7 +223,7 @@ class Server:
 
     def __init__(self, hbm_budget: float = 150e9, batch: bool = True, graphs: bool = True,
                  autotune: bool = True, impl: int = Mesh.STAGE_AUTO, keep_fields: bool = True,
-                 rebuild_every: int = 32, mixed: bool = False):
+                 rebuild_every: int = 32, mixed: bool = False, dead_fraction: float = 0.15):
         import torch
         self.torch = torch
         self.budget, self.batch, self.graphs = hbm_budget, batch, graphs
@@ -226,6 +231,7 @@ class Server:
         self._gparity = 0              # ping-pong parity shared by the packs (mixed)
         self._gcache = {}              # (pack ids, parity) -> captured graph, or None: seen once
         self.rebuild_every = rebuild_every
+        self.dead_fraction = dead_fraction
         self.autotune, self.impl, self.keep = autotune, impl, keep_fields
         self.stream = torch.cuda.Stream()
         self._padding = {}
@@ -401,13 +407,20 @@ class Server:
     def _device_context(self):
         return self.torch.cuda.stream(self.stream)
 
+    def _dead_weight(self, pack) -> bool:
+        """Finished solves hold at least `dead_fraction` of the pack's elements
+        (they keep stepping, unread, until a rebuild drops them)."""
+        dead = sum(s.K for s in pack.solves if s.finished)
+        return dead > 0 and dead >= self.dead_fraction * sum(s.K for s in pack.solves)
+
     def run(self, requests, max_iterations: int | None = None):
         """Serve `requests` (arriving at their `arrival` times) to completion;
         returns their Results in rid order.
 
         A pack of order N is rebuilt when solves of that order wait to join it
         and it has run at least `rebuild_every` steps since it was built (at once
-        when there is no pack), or when most of its solves have finished.  A
+        when there is no pack), or, after as many steps, when finished solves
+        hold `dead_fraction` of its elements.  A
         finished solve's fields and energy are taken at its last step; its
         elements keep stepping, unread, until its pack is rebuilt; a pack with
         no unfinished solve is dropped at the start of the next iteration.
@@ -455,8 +468,7 @@ class Server:
                         old = next((p for p in packs if p.N == N), None)
                         new = [s for s in waiting if s.req.N == N]
                         aged = old is not None and it - old.built_at >= every
-                        if old is not None and not new and not (old.alive * 2 <= len(old.solves)
-                                                                 and aged):
+                        if old is not None and not new and not (aged and self._dead_weight(old)):
                             continue
                         if old is not None and new and not aged:
                             continue

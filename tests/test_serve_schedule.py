@@ -38,8 +38,9 @@ class FakePack:
 
 
 class FakeServer(serve.Server):
-    def __init__(self, budget=1e18, batch=True, rebuild_every=4):
+    def __init__(self, budget=1e18, batch=True, rebuild_every=4, dead_fraction=0.5):
         self.budget, self.batch, self.rebuild_every = budget, batch, rebuild_every
+        self.dead_fraction = dead_fraction
         self.graphs, self.autotune, self.keep, self.mixed = False, False, False, False
         self.stats, self.live_log = {}, []
 
@@ -159,3 +160,29 @@ def test_rebuild_peak_stays_within_the_budget(every):
     assert srv.carried > 0 and max(srv.live_log) > 1
     assert 0 < srv.stats["model_peak"] <= budget
     assert srv.stats["model_now"] == 0                # everything released at the end
+
+
+@pytest.mark.parametrize("frac", [0.2, 0.5, 1.0])
+def test_dead_weight_rebuilds(frac):
+    """A pack is rebuilt without its finished solves once they hold `frac` of
+    its elements (after rebuild_every steps); every solve still finishes with
+    its exact step count, and a lower threshold never builds fewer packs."""
+    reqs = requests(count=30, seed=3)
+    srv = FakeServer(rebuild_every=2, dead_fraction=frac)
+    res = srv.run(reqs, max_iterations=10_000)
+    assert sorted(r.rid for r in res) == list(range(30))
+    base = FakeServer(rebuild_every=2, dead_fraction=1.0)
+    base.run(requests(count=30, seed=3), max_iterations=10_000)
+    assert srv.stats["packs_built"] >= base.stats["packs_built"]
+
+
+def test_dead_weight_counts_elements_not_solves():
+    srv = FakeServer(dead_fraction=0.5)
+    small = [FakeLive(serve.Request(i, None, np.zeros((10, 4)), 2, 3.0, None), 0.0) for i in range(3)]
+    big = FakeLive(serve.Request(9, None, np.zeros((100, 4)), 2, 3.0, None), 0.0)
+    p = FakePack(2, small + [big], 0)
+    for s in small:
+        s.finished = True                     # 3 of 4 solves, 30 of 130 elements
+    assert not srv._dead_weight(p)
+    big.finished, small[0].finished = True, False
+    assert srv._dead_weight(p)                # 120 of 130 elements
