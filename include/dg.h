@@ -255,6 +255,23 @@ int dg_rk_stage_range(dg_mesh* mesh, const float* u_in, float* u_out, float* res
                       double dt, int64_t k0, int64_t k1, void* stream);
 
 /*
+ * Self-test of failure detection in the tensor-core stages: every mbarrier
+ * wait of those kernels is bounded and, when it runs out, sets the mesh's
+ * pipeline status word, which dg_energy, dg_energy_range and dg_step_host read
+ * (and clear) after their synchronisation and report as DG_ERR_CUDA.  This
+ * call runs the same bounded wait, limited to `polls` polls, in a one-warp
+ * kernel on an mbarrier that nothing arrives at (nothing else is in flight,
+ * so no GPU fault or hang is involved), then makes the same check.
+ *   polls   : 1 .. 2^24.
+ *   seconds : host, out, may be NULL: GPU time the bounded wait took.
+ * Synchronous (default stream).  Returns DG_ERR_CUDA with the stage kernels'
+ * timeout message -- the expected outcome -- and leaves the status word
+ * clear, so the mesh stays usable; DG_ERR_STATE if the wait did not time
+ * out; DG_ERR_ARG for polls out of range.
+ */
+int dg_check_wait_timeout(dg_mesh* mesh, uint32_t polls, double* seconds);
+
+/*
  * Tetrahedra per tile of the stage kernel that runs on these buffers (the
  * tensor-core kernels need 16-byte aligned buffers; NULL pointers count as
  * aligned): the granularity of dg_rk_stage_range.  Uploads the mesh to the

@@ -207,6 +207,14 @@ class Mesh:
                                           int(stage), float(dt), int(k0), int(k1),
                                           _stream_handle(stream)), "dg_rk_stage_range")
 
+    def check_wait_timeout(self, polls: int):
+        """dg_check_wait_timeout: (status code, message, seconds) of the stage
+        kernels' bounded wait run out on purpose (expected: DG_ERR_CUDA)."""
+        sec = C.c_double(-1.0)
+        rc = self._lib.dg_check_wait_timeout(self._h, int(polls), C.byref(sec))
+        msg = self._lib.dg_last_error().decode() if rc else ""
+        return rc, msg, sec.value
+
     def stage_tile(self, u_in=None, u_out=None, res=None) -> int:
         """dg_stage_tile: tetrahedra per tile of the stage kernel these buffers run
         (None: aligned buffers)."""

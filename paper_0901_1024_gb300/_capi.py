@@ -41,6 +41,7 @@ SIGNATURES = {
     "dg_rk_stage_range": (C.c_int, [_vp, _vp, _vp, _vp, C.c_int, C.c_double, C.c_int64, C.c_int64,
                                     _vp]),
     "dg_stage_tile": (C.c_int, [_vp, _vp, _vp, _vp, _intp]),
+    "dg_check_wait_timeout": (C.c_int, [_vp, C.c_uint32, _dp]),
     "dg_rk_stage_multi": (C.c_int, [C.POINTER(_vp), C.c_int, C.POINTER(_vp), C.POINTER(_vp),
                                     C.POINTER(_vp), C.POINTER(_vp), C.c_int, C.c_double,
                                     C.POINTER(C.c_double), _vp]),

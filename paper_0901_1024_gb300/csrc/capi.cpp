@@ -390,6 +390,14 @@ int dg_rk_stage_range(dg_mesh* m, const float* u_in, float* u_out, float* res, i
   return DG_OK;
 }
 
+int dg_check_wait_timeout(dg_mesh* m, uint32_t polls, double* seconds) {
+  if (int rc = check_mesh(m, true)) return rc;
+  if (polls < 1 || polls > (1u << 24)) return fail(DG_ERR_ARG, "polls outside 1 .. 2^24");
+  std::string err;
+  if (int rc = dg::device_wait_selftest(m, polls, seconds, err)) return fail(rc, err);
+  return fail(DG_ERR_STATE, "bounded wait self-test: the wait did not time out");
+}
+
 int dg_stage_tile(dg_mesh* m, const float* u_in, const float* u_out, const float* res, int* tile) {
   if (int rc = check_mesh(m, true)) return rc;
   if (!tile) return fail(DG_ERR_ARG, "tile is NULL");

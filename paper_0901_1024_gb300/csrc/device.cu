@@ -919,6 +919,18 @@ static int check_status(dg_mesh* m, std::string& err) {
   return DG_OK;
 }
 
+int device_wait_selftest(dg_mesh* m, uint32_t polls, double* seconds, std::string& err) {
+  int rc = ensure_device(m, err);
+  if (rc) return rc;
+  DeviceState* d = m->dev;
+  auto* ns = reinterpret_cast<unsigned long long*>(d->result);   // 8-byte scratch word
+  DG_CUDA(dgdev::launch_wait_selftest(d->status, polls, ns, nullptr), "self-test launch");
+  unsigned long long h = 0;
+  DG_CUDA(cudaMemcpy(&h, ns, sizeof(h), cudaMemcpyDeviceToHost), "cudaMemcpy D2H");
+  if (seconds) *seconds = static_cast<double>(h) * 1e-9;
+  return check_status(m, err);
+}
+
 static int energy_impl(dg_mesh* m, const float* u, double* out, cudaStream_t s,
                        std::string& err, int64_t k0 = 0, int64_t k1 = -1) {
   DeviceState* d = m->dev;

@@ -122,6 +122,10 @@ cudaError_t launch_tt_mixed(const MixedArgs& m, int grid, cudaStream_t s);
 cudaError_t launch_stage(int N, bool rk, const StageArgs& a, int num_sms, cudaStream_t s,
                          int shape = 0);
 cudaError_t launch_tc_stage(int N, bool rk, const StageArgs& a, int num_sms, cudaStream_t s);
+// One warp waits (bounded by `polls`) on an mbarrier nothing arrives at: the
+// timeout sets *status as in the tensor-core stages; *ns = the wait's duration.
+cudaError_t launch_wait_selftest(int* status, uint32_t polls, unsigned long long* ns,
+                                 cudaStream_t s);
 
 struct EnergyArgs {
   const float* u;      // [6][K][Np]

@@ -93,6 +93,7 @@ int device_stage(dg_mesh* m, const float* u_in, float* u_out, float* res, int st
                  const float* dt_elem, void* stream, std::string& err, int64_t k0 = 0,
                  int64_t k1 = -1);
 // tetrahedra per tile of the stage kernel these buffers would run
+int device_wait_selftest(dg_mesh* m, uint32_t polls, double* seconds, std::string& err);
 int device_stage_tile(dg_mesh* m, const float* u_in, const float* u_out, const float* res,
                       int* tile, std::string& err);
 int device_step(dg_mesh* m, float* u, float* res, double dt, int nsteps, void* stream,

@@ -182,11 +182,16 @@ __device__ __forceinline__ void named_arrive(int id, int nthreads) {
   asm volatile("bar.arrive %0, %1;" :: "r"(id), "r"(nthreads) : "memory");
 }
 
-constexpr uint32_t kWaitLimit = 1u << 26;
+// Polls of a bounded mbarrier wait.  A poll that finds the phase incomplete
+// suspends for the hardware's time limit, measured at ~4 us on GB300 (the
+// self-test of dg_check_wait_timeout), so 2^18 polls give up after about a
+// second; the pipeline's real waits last microseconds.
+constexpr uint32_t kWaitLimit = 1u << 18;
 
 // Bounded mbarrier wait; on timeout records the failure in *status.
-__device__ __forceinline__ void wait_or_flag(uint64_t* bar, uint32_t parity, int* status) {
-  if (!tc::mbar_wait_bounded(bar, parity, kWaitLimit) && status) atomicExch(status, 1);
+__device__ __forceinline__ void wait_or_flag(uint64_t* bar, uint32_t parity, int* status,
+                                             uint32_t limit = kWaitLimit) {
+  if (!tc::mbar_wait_bounded(bar, parity, limit) && status) atomicExch(status, 1);
 }
 
 // One thread: bulk copies of tile `tile`'s fields and geometry block.

@@ -9,6 +9,12 @@ DG_ERR_UNSTABLE (-6).
 The premise of the growth test is pinned on the CPU by the oracle: on the same
 48-tetrahedron mesh at N = 2 the energy decays at the CFL step and grows by
 more than 10^6 in five steps at three times it.
+
+A third failure path is a tensor-core stage whose bounded mbarrier wait runs
+out (a lost MMA completion, say): dg_check_wait_timeout runs that bounded wait
+on a barrier nothing arrives at, in a kernel with nothing else in flight, and
+the mesh reports DG_ERR_CUDA (-4) through the same status word, then stays
+usable.
 """
 import numpy as np
 import pytest
@@ -16,7 +22,7 @@ import pytest
 import oracle
 from workloads import kuhn_box_mesh, random_fields
 
-UNSTABLE = -6
+UNSTABLE, CUDA_ERR, ARG_ERR = -6, -4, -1
 N = 2
 FACTOR, UNSTABLE_STEPS = 3.0, 5
 
@@ -93,3 +99,24 @@ def test_energy_growth_check_flags_a_too_large_step(env):
     want, _ = oracle.lserk4_run(om, u32.astype(np.float64), FACTOR * mesh.dt_cfl, UNSTABLE_STEPS)
     assert np.linalg.norm(u - want) < 1e-3 * np.linalg.norm(want)
     mesh.set_energy_check(-1.0)
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("polls", [1, 1000, 100000])
+def test_a_wait_that_runs_out_is_reported_and_cleared(env, polls):
+    torch, dg = env
+    verts, tets, om, u0 = _mesh_and_fields()
+    mesh = dg.Mesh(verts, tets, N)
+    rc, msg, sec = mesh.check_wait_timeout(polls)
+    assert rc == CUDA_ERR and "timed out" in msg
+    assert 0.0 <= sec < 5.0
+    # the status word was cleared: the stage and the energy run normally after it
+    u = torch.from_numpy(u0.astype(np.float32)).cuda()
+    res = torch.zeros_like(u)
+    mesh.step(u, res, mesh.dt_cfl, 2)
+    ue, _ = oracle.lserk4_run(om, u0, mesh.dt_cfl, 2)
+    assert np.linalg.norm(u.cpu().numpy() - ue) / np.linalg.norm(ue) < 1e-5
+    assert mesh.energy(u) > 0
+    with pytest.raises(dg.DGError) as ei:            # polls outside 1 .. 2^24
+        dg.check(mesh._lib.dg_check_wait_timeout(mesh._h, 0, None), "dg_check_wait_timeout")
+    assert ei.value.code == ARG_ERR
