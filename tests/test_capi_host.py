@@ -111,6 +111,9 @@ def test_error_codes(dg):
     assert lib.dg_set_flux(m._h, C.c_double(float("nan"))) == -1
     assert b"dt must be" in lib.dg_last_error() or b"alpha" in lib.dg_last_error()
     assert lib.dg_mesh_create(None, 0, None, 0, None) == -1
+    assert lib.dg_check_wait_timeout(m._h, 0, None) == -1          # polls outside 1 .. 2^24
+    assert lib.dg_check_wait_timeout(m._h, (1 << 24) + 1, None) == -1
+    assert b"polls" in lib.dg_last_error()
     lib.dg_mesh_destroy(None)
 
 
