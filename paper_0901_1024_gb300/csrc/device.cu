@@ -213,6 +213,114 @@ __global__ void __launch_bounds__(kEnergyRows) energy_rows_kernel(const EnergyAr
   }
 }
 
+// Orders 7..9: M in shared memory (row j padded to NP8 floats; M symmetric,
+// so row j is also column j), each thread takes RPT field rows (c, k) of a pass,
+// staged by 4-byte cp.async copies with an odd row stride (conflict-free 4-byte
+// reads), and forms u^T M u by output chunks of 8: s_i = sum_j M_ji u_j for the
+// chunk's i (row j of M read as two broadcast 16-byte loads, used for all RPT
+// rows of the thread), then e += sum_i u_i s_i.  FP32 products, FP64 sums of
+// the weighted rows.
+template <int NP, int THREADS, int RPT>
+struct EnergyWideShape {
+  static constexpr int NP8 = (NP + 7) & ~7, RS = NP | 1, ROWS = THREADS * RPT;
+  static constexpr int BYTES = (NP * NP8 + ROWS * RS) * 4;
+  static_assert(BYTES <= 226 * 1024, "shared memory");
+};
+
+template <int NP, int THREADS, int RPT>
+__global__ void __launch_bounds__(THREADS) energy_wide_kernel(const EnergyArgs A) {
+  using S = EnergyWideShape<NP, THREADS, RPT>;
+  constexpr int NP8 = S::NP8, RS = S::RS, ROWS = S::ROWS;
+  extern __shared__ __align__(16) float esm[];
+  float* sM = esm;                       // [NP][NP8], zero padded
+  float* sU = esm + NP * NP8;            // [ROWS][RS]
+  __shared__ int64_t sRow[ROWS];
+  for (int i = threadIdx.x; i < NP * NP8; i += THREADS) {
+    const int r = i / NP8, c = i - r * NP8;
+    sM[i] = c < NP ? __ldg(A.M + r * NP + c) : 0.f;
+  }
+  const int64_t Kr = A.k1 - A.k0, rows = 6 * Kr;
+  double acc = 0.0;
+  for (int64_t r0 = int64_t(blockIdx.x) * ROWS; r0 < rows; r0 += int64_t(gridDim.x) * ROWS) {
+    float w[RPT];                        // J_k (times eps_k or mu_k), or 0: no row
+#pragma unroll
+    for (int q = 0; q < RPT; ++q) {
+      const int lr = threadIdx.x + q * THREADS;
+      const int64_t g = r0 + lr;
+      w[q] = 0.f;
+      if (g < rows) {
+        const int64_t c = g / Kr, k = A.k0 + (g - c * Kr);
+        sRow[lr] = (c * A.K + k) * NP;
+        const float J = __ldg(reinterpret_cast<const float*>(A.geo) + k * kGeoWords + 9);
+        w[q] = J;
+        if (A.mat) {
+          const float4 m = __ldg(A.mat + k * kMatVecs);
+          w[q] = J * (c < 3 ? m.z : m.w);
+        }
+      }
+    }
+    __syncthreads();                     // row offsets visible; the previous pass is consumed
+    const int nr = int(rows - r0 < ROWS ? rows - r0 : ROWS);
+    for (int i = threadIdx.x; i < nr * NP; i += THREADS) {
+      const int r = i / NP, j = i - r * NP;
+      tc::cp_async4(sU + r * RS + j, A.u + sRow[r] + j);
+    }
+    tc::cp_async_commit();
+    tc::cp_async_wait_all();
+    __syncthreads();
+    if (threadIdx.x < nr) {
+      const float* u0 = sU + threadIdx.x * RS;
+      float e[RPT];
+#pragma unroll
+      for (int q = 0; q < RPT; ++q) e[q] = 0.f;
+#pragma unroll 1
+      for (int i0 = 0; i0 < NP; i0 += 8) {
+        float sacc[RPT][8];
+#pragma unroll
+        for (int q = 0; q < RPT; ++q)
+#pragma unroll
+          for (int ii = 0; ii < 8; ++ii) sacc[q][ii] = 0.f;
+#pragma unroll 4
+        for (int j = 0; j < NP; ++j) {
+          const float4 m0 = *reinterpret_cast<const float4*>(sM + j * NP8 + i0);
+          const float4 m1 = *reinterpret_cast<const float4*>(sM + j * NP8 + i0 + 4);
+#pragma unroll
+          for (int q = 0; q < RPT; ++q) {
+            const float uj = u0[q * THREADS * RS + j];
+            sacc[q][0] = fmaf(m0.x, uj, sacc[q][0]);
+            sacc[q][1] = fmaf(m0.y, uj, sacc[q][1]);
+            sacc[q][2] = fmaf(m0.z, uj, sacc[q][2]);
+            sacc[q][3] = fmaf(m0.w, uj, sacc[q][3]);
+            sacc[q][4] = fmaf(m1.x, uj, sacc[q][4]);
+            sacc[q][5] = fmaf(m1.y, uj, sacc[q][5]);
+            sacc[q][6] = fmaf(m1.z, uj, sacc[q][6]);
+            sacc[q][7] = fmaf(m1.w, uj, sacc[q][7]);
+          }
+        }
+#pragma unroll
+        for (int q = 0; q < RPT; ++q)
+#pragma unroll
+          for (int ii = 0; ii < 8; ++ii)
+            if (i0 + ii < NP) e[q] = fmaf(u0[q * THREADS * RS + i0 + ii], sacc[q][ii], e[q]);
+      }
+#pragma unroll
+      for (int q = 0; q < RPT; ++q)
+        if (threadIdx.x + q * THREADS < nr) acc += double(w[q]) * double(e[q]);
+    }
+  }
+  tc::cp_async_wait_all();
+  __shared__ double sw[(THREADS + 31) / 32];
+#pragma unroll
+  for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) sw[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (THREADS + 31) / 32; ++w) t += sw[w];
+    A.partials[blockIdx.x] = t;
+  }
+}
+
 // Any order: one warp per element, lane i forms (M u_c)_i (M symmetric, read
 // column-wise = coalesced) and u_i (M u_c)_i in FP32, scaled by J_k in FP64.
 __global__ void __launch_bounds__(kEnergyThreads) energy_kernel(const EnergyArgs A) {
@@ -275,6 +383,23 @@ static cudaError_t launch_energy_rows(const EnergyArgs& a, int grid, cudaStream_
   return cudaGetLastError();
 }
 
+template <int NP, int THREADS, int RPT>
+static cudaError_t launch_energy_wide(const EnergyArgs& a, int grid, cudaStream_t s) {
+  constexpr int bytes = EnergyWideShape<NP, THREADS, RPT>::BYTES;
+  auto kern = energy_wide_kernel<NP, THREADS, RPT>;
+  static bool attr[16] = {};
+  int dev = 0;
+  cudaError_t err = cudaGetDevice(&dev);
+  if (err != cudaSuccess) return err;
+  if (!attr[dev & 15]) {
+    err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (err != cudaSuccess) return err;
+    attr[dev & 15] = true;
+  }
+  kern<<<grid, THREADS, bytes, s>>>(a);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_energy_partials(const EnergyArgs& a, int grid, cudaStream_t s) {
   switch (a.Np) {
     case 4: return launch_energy_rows<4>(a, grid, s);
@@ -283,6 +408,9 @@ cudaError_t launch_energy_partials(const EnergyArgs& a, int grid, cudaStream_t s
     case 35: return launch_energy_rows<35>(a, grid, s);
     case 56: return launch_energy_rows<56>(a, grid, s);
     case 84: return launch_energy_rows<84>(a, grid, s);
+    case 120: return launch_energy_wide<120, 128, 2>(a, grid, s);
+    case 165: return launch_energy_wide<165, 64, 2>(a, grid, s);
+    case 220: return launch_energy_wide<220, 32, 1>(a, grid, s);
     default:
       energy_kernel<<<grid, kEnergyThreads, 0, s>>>(a);
       return cudaGetLastError();

@@ -53,7 +53,8 @@ def test_headline_workload_bytes():
     assert bench.stage_bytes_per_elem(Np) * 82944 == 289_640_448
 
 
-@pytest.mark.parametrize("workload,family", [("pulse_n24_N4", "tc"), ("cavity_n16_N6", "tt")])
+@pytest.mark.parametrize("workload,family", [("pulse_n24_N4", "tc"), ("cavity_n16_N6", "tt"),
+                                             ("pulse_n16_N7", "tt")])
 def test_stage_profiles_are_machine_readable(workload, family):
     """The committed ncu summary of each benchmark workload carries the source
     digest of the kernel family it measured and the DRAM bytes per launch; the

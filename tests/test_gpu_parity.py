@@ -354,10 +354,11 @@ def test_golden_cavity_run_fp64_config(env):
     assert e1 <= e0 * (1 + 1e-6)
 
 
-@pytest.mark.parametrize("N,n", [(N, 2) for N in range(1, 10)] + [(4, 6), (6, 5)])
+@pytest.mark.parametrize("N,n", [(N, 2) for N in range(1, 10)] + [(4, 6), (6, 5), (7, 5), (8, 4)])
 def test_energy_parity(env, N, n):
-    """Every order (1..6: row-staged kernel, 7..9: warp per element); n = 6 and
-    5 give 7776 and 4500 field rows: many 128-row passes with a ragged last one."""
+    """Every order (1..6: row-staged kernel, 7..9: operator in shared memory,
+    256 / 128 / 32 rows per pass); n = 6, 5 and 4 give 7776, 4500 and 2304
+    field rows: many passes with a ragged last one."""
     torch, dg = env
     verts, tets = kuhn_box_mesh(n, 0.15, 1)
     mesh, om = _setup(dg, verts, tets, N)
