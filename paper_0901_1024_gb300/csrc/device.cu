@@ -213,13 +213,14 @@ __global__ void __launch_bounds__(kEnergyRows) energy_rows_kernel(const EnergyAr
   }
 }
 
-// Orders 7..9: M in shared memory (row j padded to NP8 floats; M symmetric,
-// so row j is also column j), each thread takes RPT field rows (c, k) of a pass,
-// staged by 4-byte cp.async copies with an odd row stride (conflict-free 4-byte
-// reads), and forms u^T M u by output chunks of 8: s_i = sum_j M_ji u_j for the
-// chunk's i (row j of M read as two broadcast 16-byte loads, used for all RPT
-// rows of the thread), then e += sum_i u_i s_i.  FP32 products, FP64 sums of
-// the weighted rows.
+// Orders 7..9: M (symmetric) in shared memory as its weighted upper triangle,
+// T_ji = M_ij for j = i, 2 M_ij for j > i, 0 below (row j padded to NP8 floats),
+// so u^T M u = sum_i u_i s_i with s_i = sum_{j >= i} T_ji u_j.  Each thread takes
+// RPT field rows (c, k) of a pass, staged by 4-byte cp.async copies with an odd
+// row stride (conflict-free 4-byte reads), and forms s_i for 8 outputs i0..i0+7
+// at a time over j >= i0 (row j of T read as two broadcast 16-byte loads, used
+// for all RPT rows of the thread), then e += sum_i u_i s_i.  FP32 products,
+// FP64 sums of the weighted rows.
 template <int NP, int THREADS, int RPT>
 struct EnergyWideShape {
   static constexpr int NP8 = (NP + 7) & ~7, RS = NP | 1, ROWS = THREADS * RPT;
@@ -232,12 +233,12 @@ __global__ void __launch_bounds__(THREADS) energy_wide_kernel(const EnergyArgs A
   using S = EnergyWideShape<NP, THREADS, RPT>;
   constexpr int NP8 = S::NP8, RS = S::RS, ROWS = S::ROWS;
   extern __shared__ __align__(16) float esm[];
-  float* sM = esm;                       // [NP][NP8], zero padded
+  float* sM = esm;                       // T: [NP][NP8], zero padded
   float* sU = esm + NP * NP8;            // [ROWS][RS]
   __shared__ int64_t sRow[ROWS];
   for (int i = threadIdx.x; i < NP * NP8; i += THREADS) {
-    const int r = i / NP8, c = i - r * NP8;
-    sM[i] = c < NP ? __ldg(A.M + r * NP + c) : 0.f;
+    const int r = i / NP8, c = i - r * NP8;              // T_rc
+    sM[i] = c < NP && r >= c ? (r > c ? 2.f : 1.f) * __ldg(A.M + r * NP + c) : 0.f;
   }
   const int64_t Kr = A.k1 - A.k0, rows = 6 * Kr;
   double acc = 0.0;
@@ -281,7 +282,7 @@ __global__ void __launch_bounds__(THREADS) energy_wide_kernel(const EnergyArgs A
 #pragma unroll
           for (int ii = 0; ii < 8; ++ii) sacc[q][ii] = 0.f;
 #pragma unroll 4
-        for (int j = 0; j < NP; ++j) {
+        for (int j = i0; j < NP; ++j) {
           const float4 m0 = *reinterpret_cast<const float4*>(sM + j * NP8 + i0);
           const float4 m1 = *reinterpret_cast<const float4*>(sM + j * NP8 + i0 + 4);
 #pragma unroll
