@@ -213,7 +213,7 @@ __global__ void __launch_bounds__(kEnergyRows) energy_rows_kernel(const EnergyAr
   }
 }
 
-// Orders 7..9: M (symmetric) in shared memory as its weighted upper triangle,
+// Orders 4 and 6..9: M (symmetric) in shared memory as its weighted upper triangle,
 // T_ji = M_ij for j = i, 2 M_ij for j > i, 0 below (row j padded to NP8 floats),
 // so u^T M u = sum_i u_i s_i with s_i = sum_{j >= i} T_ji u_j.  Each thread takes
 // RPT field rows (c, k) of a pass, staged by 4-byte cp.async copies with an odd
@@ -406,9 +406,9 @@ cudaError_t launch_energy_partials(const EnergyArgs& a, int grid, cudaStream_t s
     case 4: return launch_energy_rows<4>(a, grid, s);
     case 10: return launch_energy_rows<10>(a, grid, s);
     case 20: return launch_energy_rows<20>(a, grid, s);
-    case 35: return launch_energy_rows<35>(a, grid, s);
+    case 35: return launch_energy_wide<35, 256, 2>(a, grid, s);
     case 56: return launch_energy_rows<56>(a, grid, s);
-    case 84: return launch_energy_rows<84>(a, grid, s);
+    case 84: return launch_energy_wide<84, 256, 2>(a, grid, s);
     case 120: return launch_energy_wide<120, 128, 2>(a, grid, s);
     case 165: return launch_energy_wide<165, 64, 2>(a, grid, s);
     case 220: return launch_energy_wide<220, 32, 1>(a, grid, s);

@@ -148,11 +148,11 @@ def test_tensor_cores_agree_with_fp32_on_a_large_material_mesh(env):
     assert rel(out[0], out[1].astype(np.float64)) < RHS_TOL
 
 
-@pytest.mark.parametrize("N", [2, 6, 7, 9])
+@pytest.mark.parametrize("N", [2, 5, 6, 7, 9])
 def test_energy_parity_materials(env, N):
-    """Energy weighted by eps (E) and mu (H): the row-staged kernel (N <= 6),
-    the shared-memory operator kernel (N = 7..9) and the allocation-free entry
-    point."""
+    """Energy weighted by eps (E) and mu (H): the row-staged kernel (N = 2, 5),
+    the shared-memory triangle kernel (N = 6, 7, 9) and the allocation-free
+    entry point."""
     torch, dg = env
     verts, tets = kuhn_box_mesh(3, 0.15, 2)
     mesh, om, eps, mu, _ = _setup(dg, verts, tets, N, 21, with_bc=False)

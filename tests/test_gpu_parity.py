@@ -356,9 +356,10 @@ def test_golden_cavity_run_fp64_config(env):
 
 @pytest.mark.parametrize("N,n", [(N, 2) for N in range(1, 10)] + [(4, 6), (6, 5), (7, 5), (8, 4)])
 def test_energy_parity(env, N, n):
-    """Every order (1..6: row-staged kernel, 7..9: operator in shared memory,
-    256 / 128 / 32 rows per pass); n = 6, 5 and 4 give 7776, 4500 and 2304
-    field rows: many passes with a ragged last one."""
+    """Every order (1, 2, 3, 5: row-staged kernel; 4, 6..9: the weighted upper
+    triangle of M in shared memory, 512 / 512 / 256 / 128 / 32 rows per pass);
+    n = 6, 5 and 4 give 7776, 4500 and 2304 field rows: many passes with a
+    ragged last one."""
     torch, dg = env
     verts, tets = kuhn_box_mesh(n, 0.15, 1)
     mesh, om = _setup(dg, verts, tets, N)
