@@ -47,9 +47,11 @@ template <int N, int S = 0> struct StageDims {
   static constexpr int UT = 6 * E * US;
   static constexpr int FT = 6 * E * (FS > US ? FS : US);     // flux tile, reused for rhs
   static constexpr int GT = E * kGeoWords;
-  // orders 5 and 6: Dr/Ds/Dt (float4 rows) and LIFT staged in shared memory once
-  // per CTA, next to the tile (they fit there; above N = 6 they are read through L1)
-  static constexpr bool OPS_SMEM = N == 5 || N == 6;
+  // orders 3..6: Dr/Ds/Dt (float4 rows) and LIFT staged in shared memory once
+  // per CTA, next to the tile (they fit there; above N = 6 they are streamed or
+  // read through L1).  N = 3, 4: with more row groups, 24 and 28 % faster than
+  // reading them through L1; N = 1, 2 are faster through L1.
+  static constexpr bool OPS_SMEM = N >= 3 && N <= 6;
   static constexpr int OT = OPS_SMEM ? 4 * Np * Np + Np * NF : 0;
   // orders 7, 8: Dr/Ds/Dt (230, 436 KB) are streamed through shared memory in
   // chunks of JC columns, two buffers: the copy of chunk c+1 (16-byte
