@@ -39,11 +39,6 @@ __host__ __device__ constexpr int stage_tile_elems(int N, int shape = 0) {
   return shape == 0 ? (N == 1 ? 16 : N <= 5 ? 32 : N == 6 ? 12 : N == 7 ? 16 : 8)  // N = 6: room for its operators
                     : (N == 1 ? 8 : N <= 5 ? 16 : N == 6 ? 6 : N == 7 ? 8 : 4);
 }
-__host__ __device__ constexpr int stage_row_groups(int N) {
-  // 2 (N = 3), 3 (N = 4..7) or 4 (N = 8, 9) matrix rows per thread: measured
-  // fastest on GB300 (N = 4: 7 groups 476 us, 9 383, 12 343, 18 464 on 82 944 tets)
-  return N == 1 ? 4 : N == 2 ? 5 : N == 3 ? 10 : N == 4 ? 12 : N == 5 ? 19 : N == 6 ? 28 : N == 7 ? 40 : N == 8 ? 42 : 55;
-}
 
 struct StageArgs {
   const float* u_in;       // [6][K][Np]

@@ -35,11 +35,19 @@
 
 namespace dgdev {
 
+// Row groups G of the FP32 stage (a thread computes rows g, g + G, ... of the
+// operator products): 2 (N = 3), 3 (N = 4..7) or 4 (N = 8, 9) matrix rows per
+// thread, measured fastest on GB300 (N = 4: 7 groups 476 us, 9 383, 12 343, 18 464
+// on 82 944 tets).
+__host__ __device__ constexpr int fp32_row_groups(int N) {
+  return N == 1 ? 4 : N == 2 ? 5 : N == 3 ? 10 : N == 4 ? 12 : N == 5 ? 19 : N == 6 ? 28 : N == 7 ? 40 : N == 8 ? 42 : 55;
+}
+
 template <int N, int S = 0> struct StageDims {
   static constexpr int Np = (N + 1) * (N + 2) * (N + 3) / 6;
   static constexpr int Nfp = (N + 1) * (N + 2) / 2;
   static constexpr int NF = 4 * Nfp;
-  static constexpr int E = stage_tile_elems(N, S), G = stage_row_groups(N);
+  static constexpr int E = stage_tile_elems(N, S), G = fp32_row_groups(N);
   static constexpr int T = E * G;
   static constexpr int R = (Np + G - 1) / G;
   static constexpr int US = Np | 1;                          // odd element stride
