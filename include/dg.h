@@ -191,7 +191,7 @@ int dg_set_boundary(dg_mesh* mesh, const int8_t* kind);
 #define DG_STAGE_TC   2
 int dg_set_stage_impl(dg_mesh* mesh, int impl);
 
-/* Tile shape of the FP32 CUDA-core stage (orders 1 and >= 7 by default, any
+/* Tile shape of the FP32 CUDA-core stage (orders 1, 8 and 9 by default, any
  * order with DG_STAGE_FP32): 0 (default) the tile sizes measured fastest on
  * large meshes, 1 half the tetrahedra per tile with the same matrix rows per
  * thread (twice the CTAs of a small mesh, half the shared tiles).  The tile

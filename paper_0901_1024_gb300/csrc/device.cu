@@ -62,9 +62,9 @@ cudaError_t launch_stage(int N, bool rk, const StageArgs& a, int num_sms, cudaSt
 // (its threads' sums, added in a fixed order) and a one-warp kernel adds the
 // partials in a fixed order, so the result is deterministic.
 constexpr int kEnergyThreads = 256;
-constexpr int kEnergyRows = 128;      // field rows (c, k) per block pass, orders 1..6
+constexpr int kEnergyRows = 128;      // field rows (c, k) per block pass, row kernel
 
-// Orders 1..6: a block stages 128 consecutive field rows (c, k) in shared
+// Row kernel (orders 1, 2, 3, 5): a block stages 128 consecutive field rows (c, k) in shared
 // memory per pass (row stride NP | 1: conflict-free), thread r then keeps row r
 // in registers and forms u^T M u from M's rows, read as broadcast 16-byte loads.
 // The rows arrive by 4-byte cp.async copies (a pass's copies are all in flight

@@ -33,10 +33,12 @@
 // One persistent 512-thread CTA per SM (orders 5, 6):
 //   * producer warps (12): the fluxes of tile t (Alg. 3: face-node gathers by
 //     4-byte cp.async, upwind flux with the PEC ghost state), then, after a
-//     named barrier, the 48 x KT values of X(t) -- producer p builds the 8-value
-//     chunks p / 48 + 8 q of row p % 48 -- a second barrier publishes the row
-//     maxima (row scale), and once the MMAs of tile t-1 have read the single X
-//     buffer, the scaled values are split into FP16 hi/lo and stored;
+//     named barrier, the 48 x KT values of X(t) -- the 8 producers of a row
+//     share its 8-value chunks, producer q building the chunks of all three
+//     g^mu blocks at node chunks q, q + 8, ... from one load of the two curl
+//     fields, then flux chunks up to its share -- a second barrier publishes
+//     the row maxima (row scale), and once the MMAs of tile t-1 have read the
+//     single X buffer, the scaled values are split into FP16 hi/lo and stored;
 //   * MMA/epilogue warps (4): warp 3 (its tensor-memory lanes hold no node)
 //     issues the 3 x KT/16 MMAs of tile t into accumulator t & 1 and all bulk
 //     copies, while warps 0..2 read tile t-1's accumulator (tcgen05.ld), remove
