@@ -36,11 +36,13 @@
 namespace dgdev {
 
 // Row groups G of the FP32 stage (a thread computes rows g, g + G, ... of the
-// operator products): 2 (N = 3), 3 (N = 4..7) or 4 (N = 8, 9) matrix rows per
-// thread, measured fastest on GB300 (N = 4: 7 groups 476 us, 9 383, 12 343, 18 464
-// on 82 944 tets).
+// operator products): 2 (N = 3, 5, 6), 3 (N = 4, 7, 8) or 4 (N = 9) matrix rows
+// per thread, measured fastest on GB300 (sweep meshes, ~1.7e7 DOFs: N = 4 with 7
+// groups 476 us, 9 383, 12 343, 18 464; N = 6 with 21 groups 766, 28 730, 42 664;
+// N = 7 with 30 groups 725, 40 714, 60 760; N = 9 with 44 groups 1256, 55 1252,
+// 74 1317).
 __host__ __device__ constexpr int fp32_row_groups(int N) {
-  return N == 1 ? 4 : N == 2 ? 5 : N == 3 ? 10 : N == 4 ? 12 : N == 5 ? 19 : N == 6 ? 28 : N == 7 ? 40 : N == 8 ? 42 : 55;
+  return N == 1 ? 4 : N == 2 ? 5 : N == 3 ? 10 : N == 4 ? 12 : N == 5 ? 28 : N == 6 ? 42 : N == 7 ? 40 : N == 8 ? 55 : 55;
 }
 
 template <int N, int S = 0> struct StageDims {
