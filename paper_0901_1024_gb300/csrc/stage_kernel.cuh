@@ -76,6 +76,12 @@ template <int N, int S = 0> struct StageDims {
   static constexpr int NLC = NF / 4 / MC;
   static constexpr int CT = OPS_STREAM ? 2 * 4 * Np * JC : 0;  // floats of the two chunk buffers
   static constexpr size_t smem_bytes = size_t(UT + FT + GT + OT + CT) * sizeof(float);
+  // N = 4: keep two CTAs per SM (their shared tiles fit twice); without the
+  // bound the asynchronous tile staging let it grow to 100 registers, one CTA
+  // per SM and 440 us instead of 342.  Elsewhere 0 (no minimum): an explicit
+  // minimum of 1 or 2 changed the register allocation at N = 1..3 (72 -> 134
+  // registers at N = 1) and cost 10-50 %.
+  static constexpr int MIN_CTAS = N == 4 ? 2 : 0;
   static_assert(smem_bytes <= 227 * 1024, "shared memory budget");
   static_assert((UT % 4) == 0 && (FT % 4) == 0 && (GT % 4) == 0, "tiles must stay 16-byte aligned");
   static_assert(!OPS_STREAM || (Np % JC == 0 && NF / 4 % MC == 0 && MC <= JC),
@@ -85,7 +91,7 @@ template <int N, int S = 0> struct StageDims {
 // EXT: meshes with materials (A.mat) or absorbing faces; the vacuum
 // instantiation compiles without any of that code.
 template <int N, bool RK, bool EXT, int S>
-__global__ void __launch_bounds__(StageDims<N, S>::T) stage_kernel(const StageArgs A) {
+__global__ void __launch_bounds__(StageDims<N, S>::T, StageDims<N, S>::MIN_CTAS) stage_kernel(const StageArgs A) {
   using D = StageDims<N, S>;
   constexpr int E = D::E, G = D::G, Np = D::Np, Nfp = D::Nfp, NF = D::NF, R = D::R;
   constexpr int US = D::US, FS = D::FS;
@@ -140,17 +146,19 @@ __global__ void __launch_bounds__(StageDims<N, S>::T) stage_kernel(const StageAr
     // (buffer 0 was last read before the previous tile's final barriers)
     issue_chunk(0, 0);
 
-    // ---- 1. stage geometry and fields -------------------------------------
+    // ---- 1. stage geometry and fields (asynchronous copies, all in flight) --
     for (int idx = tid; idx < Ev * (kGeoWords / 4); idx += D::T)
-      reinterpret_cast<float4*>(sg)[idx] = __ldg(&A.geo[size_t(k0) * (kGeoWords / 4) + idx]);
+      tc::cp_async16(reinterpret_cast<float4*>(sg) + idx, &A.geo[size_t(k0) * (kGeoWords / 4) + idx]);
 #pragma unroll
     for (int c = 0; c < 6; ++c) {
       const float* src = A.u_in + (size_t(c) * K + k0) * Np;
       for (int idx = tid; idx < Ev * Np; idx += D::T) {
         const int ee = idx / Np, i = idx - ee * Np;
-        su[(c * E + ee) * US + i] = __ldg(src + idx);
+        tc::cp_async4(su + (c * E + ee) * US + i, src + idx);
       }
     }
+    tc::cp_async_commit();
+    tc::cp_async_wait_all();
     __syncthreads();
 
     // ---- 2. flux extraction -----------------------------------------------
