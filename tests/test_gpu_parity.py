@@ -83,10 +83,11 @@ def test_rhs_parity_both_implementations(env, N, impl):
     assert rel(got, oracle.rhs(om, u32.astype(np.float64))) < RHS_TOL
 
 
-@pytest.mark.parametrize("N", [5, 6])
+@pytest.mark.parametrize("N", [5, 6, 7])
 def test_tc_operator_in_tensor_memory_rhs_parity(env, N):
-    """Orders 5, 6 on the tensor cores (operator in tensor memory, tiles of 8):
-    K = 162 = 20 tiles + a ragged tile of 2, rows of very different scales."""
+    """Orders 5..7 on the tensor cores (operator in tensor memory, tiles of 8;
+    order 7 with the update straight to global memory): K = 162 = 20 tiles + a
+    ragged tile of 2, rows of very different scales."""
     torch, dg = env
     verts, tets = kuhn_box_mesh(3, 0.15, 40 + N)
     mesh, om = _setup(dg, verts, tets, N)

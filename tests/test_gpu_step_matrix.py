@@ -118,3 +118,26 @@ def test_several_tiles_per_cta_10_steps(env, N):
     ue, _ = oracle.lserk4_run(om, u0.astype(np.float64), dt, 10)
     assert np.isfinite(got).all()
     assert rel(got, ue) < STEP_TOL
+
+
+@pytest.mark.parametrize("N,kind", [(5, "vacuum"), (7, "vacuum"), (7, "ext")])
+def test_ragged_last_tile_10_steps(env, N, kind):
+    """K = 162 = 20 tiles of 8 + a ragged tile of 2 on the operator-in-tensor-
+    memory stages (order 7: the update's global stores are guarded per
+    element), per-element steps included via the materials case."""
+    torch, dg = env
+    verts, tets = kuhn_box_mesh(3, 0.15, 60 + N)
+    mesh, om = dg.Mesh(verts, tets, N), oracle.build_mesh(verts, tets, N)
+    kw = {}
+    if kind == "ext":
+        eps, mu, bc = _materials(om.K, 300 + N)
+        mesh.set_materials(eps, mu)
+        mesh.set_boundary(bc)
+        kw = dict(eps=eps, mu=mu, bc=bc)
+    u0 = random_fields(om.K, om.Np, 70 + N).astype(np.float32)
+    dt = mesh.dt_cfl
+    got, _, kinds = _run(torch, mesh, u0, dt, 10, TC)
+    assert kinds == {KIND_TC_STAGE}
+    ue, _ = oracle.lserk4_run(om, u0.astype(np.float64), dt, 10, **kw)
+    assert np.isfinite(got).all()
+    assert rel(got, ue) < STEP_TOL
