@@ -264,10 +264,12 @@ int dg_rk_stage_range(dg_mesh* mesh, const float* u_in, float* u_out, float* res
  * so no GPU fault or hang is involved), then makes the same check.
  *   polls   : 1 .. 2^24.
  *   seconds : host, out, may be NULL: GPU time the bounded wait took.
- * Synchronous (default stream).  Returns DG_ERR_CUDA with the stage kernels'
- * timeout message -- the expected outcome -- and leaves the status word
- * clear, so the mesh stays usable; DG_ERR_STATE if the wait did not time
- * out; DG_ERR_ARG for polls out of range.
+ * Synchronous (default stream); it uses the mesh's status word and energy
+ * result word, so it must not overlap other calls on the same mesh.  Returns
+ * DG_ERR_CUDA with the stage kernels' timeout message -- the expected
+ * outcome -- and leaves the status word clear, so the mesh stays usable;
+ * DG_ERR_STATE if the wait did not time out; DG_ERR_ARG for polls out of
+ * range.
  */
 int dg_check_wait_timeout(dg_mesh* mesh, uint32_t polls, double* seconds);
 
